@@ -1,0 +1,116 @@
+"""TEST INFRASTRUCTURE ONLY -- float64 oracle of the nowcasting aggregators.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this module; the CUDA path never does.
+
+The paper extrapolates wind from a context of past measurements with a
+kernel-weighted average (Eq. GKA, Sec. 3.2) and truncates the context to the
+few points that contribute most, i.e. the k nearest neighbours.  The
+aggregators written here are the readings used by this project:
+
+* features: for neighbour j of query q, the scaled offsets
+  (sqrt(sx)(x_j-x_q), sqrt(sy)(y_j-y_q), sqrt(sz)(z_j-z_q), sqrt(st)(t_j-t_q))
+  and the neighbour's measured wind (u_j, v_j); six channels per neighbour in
+  neighbour-rank order, standardised channel-wise with (mean, std), zero for
+  a missing neighbour.
+* IDW: s_hat = sum_j w_j s_j / sum_j w_j with w_j = 1 / (d2_j + eps) over the
+  valid neighbours; NaN when the context is empty.
+* MLP: Z = X W1 + b1, H = GELU(Z) (erf form), Y = H W2 + b2, mean squared
+  error over the B x 2 outputs, and its exact gradient.
+* AdamW: Adam's moment estimates with bias correction and decoupled weight
+  decay (w <- w - lr * (m_hat / (sqrt(v_hat) + eps) + wd * w)).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.special import erf
+
+N_FEAT = 6
+
+
+def features(pts, wind, queries, idx, sigma, mean=None, std=None):
+    """float64 features [m, k, 6] (see module doc)."""
+    pts = np.asarray(pts, dtype=np.float32)
+    wind = np.asarray(wind, dtype=np.float32)
+    queries = np.asarray(queries, dtype=np.float32)
+    idx = np.asarray(idx)
+    m, k = idx.shape
+    sq = np.sqrt(np.asarray(sigma, dtype=np.float64))
+    out = np.zeros((m, k, N_FEAT), dtype=np.float64)
+    valid = idx >= 0
+    j = np.where(valid, idx, 0)
+    nb = pts[j].astype(np.float64)
+    q = queries.astype(np.float64)[:, None, :]
+    off = (nb - q) * sq[None, None, :]
+    out[..., 0:4] = off
+    out[..., 4:6] = wind[j].astype(np.float64)
+    if mean is not None:
+        out = (out - np.asarray(mean, dtype=np.float64)) / np.asarray(std, dtype=np.float64)
+    out[~valid] = 0.0
+    return out
+
+
+def idw(d2, idx, wind, eps: float = 1e-6):
+    """Inverse-distance-weighted average of the neighbours' wind [m, 2]."""
+    d2 = np.asarray(d2, dtype=np.float64)
+    idx = np.asarray(idx)
+    wind = np.asarray(wind, dtype=np.float64)
+    valid = idx >= 0
+    w = np.where(valid, 1.0 / (np.where(valid, d2, 0.0) + eps), 0.0)
+    s = wind[np.where(valid, idx, 0)]
+    num = (w[..., None] * s).sum(axis=1)
+    den = w.sum(axis=1)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return num / den[:, None]
+
+
+def gelu(z):
+    return 0.5 * z * (1.0 + erf(z / math.sqrt(2.0)))
+
+
+def gelu_grad(z):
+    return 0.5 * (1.0 + erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
+
+
+def mlp_forward(X, W1, b1, W2, b2):
+    X = np.asarray(X, dtype=np.float64)
+    Z = X @ np.asarray(W1, np.float64) + np.asarray(b1, np.float64)
+    H = gelu(Z)
+    Y = H @ np.asarray(W2, np.float64) + np.asarray(b2, np.float64)
+    return Z, H, Y
+
+
+def mse(Y, T) -> float:
+    Y = np.asarray(Y, np.float64)
+    T = np.asarray(T, np.float64)
+    return float(np.mean((Y - T) ** 2))
+
+
+def mlp_grads(X, T, W1, b1, W2, b2):
+    """Loss and exact gradients of mean((Y - T)^2)."""
+    X = np.asarray(X, dtype=np.float64)
+    T = np.asarray(T, dtype=np.float64)
+    Z, H, Y = mlp_forward(X, W1, b1, W2, b2)
+    loss = float(np.mean((Y - T) ** 2))
+    dY = 2.0 * (Y - T) / Y.size
+    dW2 = H.T @ dY
+    db2 = dY.sum(axis=0)
+    dH = dY @ np.asarray(W2, np.float64).T
+    dZ = dH * gelu_grad(Z)
+    dW1 = X.T @ dZ
+    db1 = dZ.sum(axis=0)
+    return loss, dict(W1=dW1, b1=db1, W2=dW2, b2=db2)
+
+
+def adamw_step(w, g, m, v, t: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, wd=1e-2):
+    """One AdamW step (t counts from 1); returns new (w, m, v)."""
+    w = np.asarray(w, np.float64)
+    g = np.asarray(g, np.float64)
+    m = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    w = w - lr * (mhat / (np.sqrt(vhat) + eps) + wd * w)
+    return w, m, v

@@ -1,0 +1,89 @@
+"""Pins of the nowcast oracle: GELU against the standard normal CDF, the
+MLP gradient against central finite differences, AdamW against its closed
+form under a constant gradient, IDW special cases and a hand-worked
+feature row."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import nowcast as nc
+
+
+def test_gelu_known_values():
+    # GELU(z) = z * Phi(z); standard normal table values Phi(1) =
+    # 0.841344746068543, Phi(-1) = 0.158655253931457, Phi(6) = 1 - 9.8659e-10
+    z = np.array([0.0, 1.0, -1.0, 6.0])
+    np.testing.assert_allclose(nc.gelu(z), [0.0, 0.841344746068543, -0.158655253931457,
+                                            6.0 * (1.0 - 9.8659e-10)], rtol=1e-12, atol=1e-12)
+
+
+def test_mlp_gradient_matches_central_differences():
+    rng = np.random.default_rng(0)
+    B, din, dh = 7, 12, 9
+    X = rng.normal(size=(B, din))
+    T = rng.normal(size=(B, 2))
+    P = dict(W1=rng.normal(size=(din, dh)) * 0.4, b1=rng.normal(size=dh) * 0.1,
+             W2=rng.normal(size=(dh, 2)) * 0.4, b2=rng.normal(size=2) * 0.1)
+    loss, g = nc.mlp_grads(X, T, **P)
+    h = 1e-6
+    for name in P:
+        flat = P[name].reshape(-1)
+        for i in range(0, flat.size, max(1, flat.size // 11)):
+            old = flat[i]
+            flat[i] = old + h
+            lp = nc.mse(nc.mlp_forward(X, **P)[2], T)
+            flat[i] = old - h
+            lm = nc.mse(nc.mlp_forward(X, **P)[2], T)
+            flat[i] = old
+            fd = (lp - lm) / (2 * h)
+            assert g[name].reshape(-1)[i] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def test_adamw_constant_gradient_closed_form():
+    # With a constant gradient g, m_hat = g and v_hat = g^2 at every step, so
+    # w_{t+1} = (1 - lr wd) w_t - lr g / (|g| + eps): a geometric recursion
+    # with the closed form w_t = c^t w_0 - lr s (1 - c^t) / (1 - c).
+    lr, wd, eps = 1e-2, 0.1, 1e-8
+    g = np.array([0.5, -2.0, 3e-4])
+    w0 = np.array([1.0, -1.0, 0.25])
+    w, m, v = w0.copy(), np.zeros(3), np.zeros(3)
+    for t in range(1, 26):
+        w, m, v = nc.adamw_step(w, g, m, v, t, lr=lr, wd=wd, eps=eps)
+    c = 1.0 - lr * wd
+    s = g / (np.abs(g) + eps)
+    closed = c ** 25 * w0 - lr * s * (1 - c ** 25) / (1 - c)
+    np.testing.assert_allclose(w, closed, rtol=1e-9)
+
+
+def test_idw_special_cases():
+    wind = np.array([[3.0, 4.0], [3.0, 4.0], [3.0, 4.0], [-1.0, 2.0]])
+    # constant field -> that constant
+    out = nc.idw(np.array([[1.0, 2.0, 5.0]]), np.array([[0, 1, 2]]), wind)
+    np.testing.assert_allclose(out, [[3.0, 4.0]])
+    # a single neighbour -> its value; missing neighbours are ignored
+    out = nc.idw(np.array([[7.0, np.inf]]), np.array([[3, -1]]), wind)
+    np.testing.assert_allclose(out, [[-1.0, 2.0]])
+    # two neighbours at d2 = 1 and 3 (eps = 0): weights 1 and 1/3
+    out = nc.idw(np.array([[1.0, 3.0]]), np.array([[0, 3]]), wind, eps=0.0)
+    np.testing.assert_allclose(out, [[(3.0 - 1.0 / 3) / (4.0 / 3), (4.0 + 2.0 / 3) / (4.0 / 3)]])
+    # permutation invariance
+    a = nc.idw(np.array([[1.0, 2.0, 4.0]]), np.array([[0, 3, 1]]), wind)
+    b = nc.idw(np.array([[4.0, 1.0, 2.0]]), np.array([[1, 0, 3]]), wind)
+    np.testing.assert_allclose(a, b)
+    # empty context -> NaN
+    assert np.isnan(nc.idw(np.array([[np.inf]]), np.array([[-1]]), wind)).all()
+
+
+def test_features_hand_row():
+    pts = np.array([[10.0, 20.0, 9.0, 100.0], [12.0, 17.0, 10.0, 60.0]], np.float32)
+    wind = np.array([[1.0, 2.0], [5.0, -3.0]], np.float32)
+    q = np.array([[10.0, 20.0, 9.0, 100.0]], np.float32)
+    f = nc.features(pts, wind, q, np.array([[1, -1]]), (1.0, 4.0, 9.0, 0.01))
+    # offsets scaled by sqrt(sigma) = (1, 2, 3, 0.1): (2, -6, 3, -4), wind (5, -3)
+    np.testing.assert_allclose(f[0, 0], [2.0, -6.0, 3.0, -4.0, 5.0, -3.0], rtol=1e-7)
+    np.testing.assert_array_equal(f[0, 1], np.zeros(6))
+    g = nc.features(pts, wind, q, np.array([[1, -1]]), (1.0, 4.0, 9.0, 0.01),
+                    mean=np.ones(6), std=np.full(6, 2.0))
+    np.testing.assert_allclose(g[0, 0], [0.5, -3.5, 1.0, -2.5, 2.0, -2.0], rtol=1e-7)
+    np.testing.assert_array_equal(g[0, 1], np.zeros(6))
