@@ -1,0 +1,339 @@
+#!/usr/bin/env python3
+"""Exact causal k-NN contexts/s with TNN on one GB300 (and the linear-search
+comparator on the same inputs).
+
+A step is one pass of the search over every query of the workload:
+self-query of all points of the medium trajectory workload (2,000 synthetic
+flights x 200 samples = 400,000 points, k = 32, 20-point segments, scales
+(1, 1, 10, 0.01), mask t_j < t_i).  Inputs are resident in HBM; L2 is
+flushed (256 MiB write) before every timed step.  The JSON line follows the
+repository's benchmark contract.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "causal k-NN contexts/sec (exact, k=32) TNN vs GPU brute force on 1 GB300"
+UNIT = "contexts/s"
+# FP32 lane-operations per query-to-cylinder bound and per point distance
+# (instruction counts of seg_lb and of dist32 + mask + compare).
+OPS_PER_LB = 26
+OPS_PER_PAIR = 14
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["medium", "tiny", "precision"], default="medium")
+    ap.add_argument("--comparator-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _workload(name, rank):
+    from paper_2112_10408_gb300 import synth
+    if name == "tiny":
+        wl, k, K = synth.flights(200, 50, synth.SEED_TINY + 1000 * rank, name="tiny-10k"), 8, 10
+    elif name == "precision":
+        wl, k, K = synth.flights(20000, 200, synth.SEED_PRECISION + 1000 * rank,
+                                 name="precision-4M"), 32, 20
+    else:
+        wl, k, K = synth.flights(2000, 200, synth.SEED_MEDIUM + 1000 * rank,
+                                 name="medium-400k"), 32, 20
+    return wl, k, K
+
+
+def _config(wl, k, K, name):
+    desc = {"tiny": "200 synthetic flights x 50 samples = 10,000 points",
+            "medium": "2,000 synthetic flights x 200 samples = 400,000 points",
+            "precision": "20,000 synthetic flights x 200 samples = 4,000,000 points"}[name]
+    return {"workload": f"{wl.name}: {desc}, self-query of every point",
+            "k": k, "seg_len": K, "sigma": list((1.0, 1.0, 10.0, 0.01)), "lag_s": 0.0,
+            "queries_per_step": wl.n,
+            "generator": "routes of 3-5 waypoints, 4 s sampling, N(0,50 m) jitter, 2000x2000 km x 12 km x 6 h",
+            "l2": "flushed before every timed step (256 MiB write)"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.bus_id:
+                cmd += ["-i", self.bus_id]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _cpu_baseline(wl, k, n_sample, seed=0x5A00):
+    """The FP64 oracle as it stands on a bounded sample of the queries."""
+    import oracle
+    from paper_2112_10408_gb300 import synth
+    q = synth.query_sample(wl.n, n_sample, seed=seed)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.knn(wl.xyzt, k, (1.0, 1.0, 10.0, 0.01), lag=0.0, qsel=q, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": q.size / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{q.size} uniformly sampled self-queries of the same workload "
+                      f"(FP64 brute force, {cores} threads, {dt:.2f} s)"}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2112_10408_gb300 import synth
+    oracle.build()
+    wl, k, K = _workload(a.workload, 0)
+    cores = os.cpu_count() or 1
+    per_step = 64 if a.workload != "tiny" else 2048
+    for w in range(a.warmup):
+        oracle.knn(wl.xyzt, k, (1.0, 1.0, 10.0, 0.01), qsel=synth.query_sample(wl.n, per_step, seed=w),
+                   nthreads=cores)
+    t0 = time.perf_counter()
+    for s in range(a.steps):
+        q = synth.query_sample(wl.n, per_step, seed=0x1000 + s)
+        oracle.knn(wl.xyzt, k, (1.0, 1.0, 10.0, 0.01), qsel=q, nthreads=cores)
+    dt = time.perf_counter() - t0
+    value = a.steps * per_step / dt
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": 1e3 * dt / max(a.steps, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": _config(wl, k, K, a.workload), "impl": "reference",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"each step: {per_step} uniformly sampled self-queries "
+                                      f"(FP64 brute-force oracle, {cores} threads)"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2112_10408_gb300 import build as tb
+    if rank == 0:
+        tb.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2112_10408_gb300 import tnn
+    tnn.load_library()
+
+    wl, k, K = _workload(a.workload, rank)
+    sigma = (1.0, 1.0, 10.0, 0.01)
+    xyzt_d = torch.from_numpy(wl.xyzt).cuda()
+    ix = tnn.tnn_build_segments(xyzt_d, wl.traj_off, sigma, K)
+    tune = tnn.tnn_autotune(ix, k, 0.0, m_sample=8192)
+    m = wl.n
+    idx = torch.empty((m, k), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((m, k), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        tnn.tnn_knn(ix, k, 0.0, out=(idx, d2), **tune)
+
+    for _ in range(max(a.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(local).pci_bus_id
+    except Exception:
+        try:
+            p = torch.cuda.get_device_properties(local)
+            bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        except Exception:
+            bus = None
+    sampler = ClockSampler(bus)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    tnn.tnn_profile_read(reset=True)
+    tnn.tnn_profile_enable(True)
+    for s in range(a.steps):
+        flush.zero_()
+        ev[s][0].record()
+        step()
+        ev[s][1].record()
+    torch.cuda.synchronize()
+    tnn.tnn_profile_enable(False)
+    kern_ms, launches = tnn.tnn_profile_read(reset=True)
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / max(a.steps, 1)
+    value = world * m * a.steps / (total_ms / 1e3)
+
+    # executed and necessary work of one pass (outside the timed region)
+    _, _, st = tnn.tnn_knn(ix, k, 0.0, stats=True, out=(idx, d2), **tune)
+    nlb, npairs = tnn.tnn_knn_work(ix, k, d2, 0.0)
+    kern_avg_ms = kern_ms / max(launches, 1)
+    alg_ops = OPS_PER_LB * nlb + OPS_PER_PAIR * npairs
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = nsm * 128 * sm_max * 1e6 / 1e12  # T FP32 lane-ops/s
+    achieved = alg_ops / (kern_avg_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "T FP32 lane-ops/s",
+                "frac": achieved / alu_peak, "traffic": None, "kernel": "k_tnn_search",
+                "kernel_ms": kern_avg_ms,
+                "peak_note": f"{nsm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived, not measured)",
+                "work_per_launch": {"lb_needed": nlb, "pairs_needed": npairs,
+                                    "lb_executed": st["lb_evals"], "pairs_executed": st["pairs"],
+                                    "ops_per_lb": OPS_PER_LB, "ops_per_pair": OPS_PER_PAIR}}
+
+    # comparator: linear search on the same queries
+    comparator = None
+    if a.comparator_steps > 0:
+        bi = torch.empty_like(idx)
+        bd = torch.empty_like(d2)
+        tnn.tnn_knn_bruteforce(ix, k, 0.0, out=(bi, bd))
+        torch.cuda.synchronize()
+        cms = []
+        for _ in range(a.comparator_steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            tnn.tnn_knn_bruteforce(ix, k, 0.0, out=(bi, bd))
+            e1.record()
+            torch.cuda.synchronize()
+            cms.append(e0.elapsed_time(e1))
+        same = bool(torch.equal(bi, idx))
+        cmean = sum(cms) / len(cms)
+        comparator = {"impl": "linear search (k_linear_search, same FP32 ranking + FP64 settlement)",
+                      "value": m / (cmean / 1e3), "unit": UNIT, "ms_per_step": cmean,
+                      "tnn_speedup": cmean / ms_step, "identical_neighbours": same}
+
+    # end to end through the C ABI: pinned host points -> build -> search ->
+    # pinned host neighbour lists
+    h_x = torch.from_numpy(wl.xyzt).pin_memory()
+    h_i = torch.empty((m, k), dtype=torch.int32).pin_memory()
+    h_d = torch.empty((m, k), dtype=torch.float32).pin_memory()
+    d_x = torch.empty_like(xyzt_d)
+    e2e_ms = []
+    for s in range(max(a.e2e_steps, 1) + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        d_x.copy_(h_x, non_blocking=True)
+        ix2 = tnn.tnn_build_segments(d_x, wl.traj_off, sigma, K)
+        tnn.tnn_knn(ix2, k, 0.0, out=(idx, d2), **tune)
+        h_i.copy_(idx, non_blocking=True)
+        h_d.copy_(d2, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ix2.destroy()
+        if s > 0:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_avg = sum(e2e_ms) / len(e2e_ms)
+    e2e = {"value": world * m / (e2e_avg / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(h_x.numel() * 4), "d2h_bytes_per_step": int(m * k * 8),
+           "ms_per_step": e2e_avg, "includes": "H2D points, tnn_build_segments, tnn_knn, D2H results"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = _cpu_baseline(wl, k, 8192 if a.workload != "tiny" else wl.n)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": dict(_config(wl, k, K, a.workload), tuning=tune,
+                              parallelism=f"replicas x{world}: each rank its own window"),
+               "clocks": clocks, "e2e": e2e, "gpu_launches": 2 * a.steps,
+               "roofline": roofline, "cpu_baseline": cpu, "comparator": comparator,
+               "stats_per_step": st}
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

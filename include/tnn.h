@@ -1,0 +1,326 @@
+/*
+ * tnn.h -- C ABI of the exact Trajectory Nearest Neighbours (TNN) library.
+ *
+ * Method: "Efficient Wind Speed Nowcasting with GPU-Accelerated Nearest
+ * Neighbors Algorithm" (Pannatier, Picatoste, Fleuret), Sec. 3.
+ *
+ * Problem (Sec. 3.4): N measurements x_i = (x_i, y_i, z_i, t_i) grouped by
+ * trajectory; for a query at (x, y, z, t) find the k nearest points under the
+ * scalable metric
+ *     d2 = sx (dx)^2 + sy (dy)^2 + sz (dz)^2 + st (dt)^2
+ * among the points measured strictly more than `lag` (t_w) before it
+ * (Sec. 3.1, Eq. of the masked temporal part): valid iff t_j < t - lag.
+ * The result is exact: the ranking is that of the FP64 value
+ *     ((sx dx^2 + sy dy^2) + sz dz^2) + st dt^2    (dx = (double)x_j - (double)x)
+ * with ties broken by the smaller point index.
+ *
+ * Conventions for every entry point:
+ *  - Pointers prefixed d_ are device pointers (CUDA global memory on the
+ *    current device), h_ are host pointers.  The caller owns every buffer it
+ *    passes; the library never frees or retains caller memory beyond the call,
+ *    except where an object (tnn_index, tnn_batch, tnn_mlp) documents a copy.
+ *  - Points are float32 rows (x, y, z, t): x, y, z in km (any consistent
+ *    unit), t in s.  Rows of one trajectory are contiguous and sorted by
+ *    non-decreasing t.  N < 2^31.
+ *  - Every call is asynchronous on `stream` unless it says it synchronises;
+ *    outputs are valid once the stream reaches the call.  Errors are status
+ *    codes, never aborts; the message of the last failure on the calling
+ *    thread is returned by tnn_last_error().
+ *  - Output neighbour lists are rows of k entries sorted by (d2, index);
+ *    missing neighbours (fewer than k valid points) are index -1, d2 +inf.
+ */
+#ifndef TNN_H
+#define TNN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL means the legacy default stream. */
+typedef struct CUstream_st *tnn_stream_t;
+
+typedef enum {
+    TNN_OK = 0,
+    TNN_ERR_INVALID_ARG = 1, /* bad size, pointer, parameter or input value */
+    TNN_ERR_OOM = 2,         /* device allocation failed                    */
+    TNN_ERR_CUDA = 3,        /* a CUDA runtime call or kernel failed        */
+    TNN_ERR_TIMEOUT = 4,     /* reserved: a bounded device wait expired     */
+    TNN_ERR_UNSUPPORTED = 5  /* the device is not sm_103 or lacks a feature */
+} tnn_status;
+
+const char *tnn_status_string(tnn_status s);
+/* Message of the last failing call on this thread ("" if none). */
+const char *tnn_last_error(void);
+
+/* ------------------------------------------------------------------ index */
+
+typedef struct tnn_index tnn_index;
+
+typedef struct {
+    double sigma[4]; /* weights (sx, sy, sz, st) on squared differences,
+                        finite, 0 <= s <= 1e6 (Sec. 3.4, the scalable metric) */
+    int32_t seg_len; /* K, points per segment, 2..64 (Sec. 3.4)            */
+} tnn_build_params;
+
+typedef struct {
+    int64_t n_points;
+    int64_t n_traj;
+    int64_t n_segments;
+    int32_t seg_len;
+    float coord_max;   /* largest |sqrt(s) * coordinate| over x, y, z        */
+    float max_radius;  /* largest segment cylinder radius (scaled units)     */
+} tnn_index_info;
+
+/*
+ * Build the TNN index (Sec. 3.4 partitioning; Fig. 2 caption: segment
+ * matrices A, t_A, B, t_B, U, E).  Each trajectory is cut into consecutive
+ * sets of seg_len points (the last set keeps the remainder, no padding);
+ * every set becomes a segment from its first point A to its last point B in
+ * sqrt(sigma)-scaled space with U = AB / |AB|^2 and a cylinder radius r that
+ * bounds the distance of every member to the segment (computed in FP64 and
+ * rounded up).  Segments are then ordered by t_A.
+ *   d_xyzt      [n][4] float, device; copied into the index.
+ *   h_traj_off  [n_traj + 1] int64, host; 0 = off[0] <= ... <= off[n_traj] = n.
+ * Validates the input on the device (finite, |coordinate| <= 1e15, times
+ * sorted within each trajectory) and therefore SYNCHRONISES `stream`.
+ * On success *out owns device memory until tnn_index_destroy.
+ */
+tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
+                              const int64_t *h_traj_off, int64_t n_traj,
+                              const tnn_build_params *params,
+                              tnn_stream_t stream, tnn_index **out);
+
+void tnn_index_destroy(tnn_index *index);
+tnn_status tnn_index_get_info(const tnn_index *index, tnn_index_info *out);
+
+/*
+ * Copy the t_A-ordered segment table out of the index (for inspection and
+ * tests).  d_seg receives [n_segments][16] floats per segment:
+ *   0-2 A (scaled), 3 t_A, 4-6 U = AB/|AB|^2 (scaled), 7 t_B,
+ *   8-10 AB (scaled), 11 r, 12 first point (int32 bits), 13 count (int32
+ *   bits), 14 trajectory (int32 bits), 15 build-order id (int32 bits).
+ * d_pm (optional) receives [n_segments] floats, the running maximum of t_B
+ * in that order.
+ */
+tnn_status tnn_index_export(const tnn_index *index, float *d_seg, float *d_pm,
+                            tnn_stream_t stream);
+
+/* ------------------------------------------------------------------- k-NN */
+
+enum {
+    /* Output (float) of the FP64 distance for every neighbour (each one is
+       recomputed in FP64).  Without it, neighbours whose FP32 distance is
+       separated from their rank neighbours report the FP32 distance, which is
+       within 2^-20 relative of the FP64 value; the neighbour set and order
+       are exact either way. */
+    TNN_FLAG_EXACT_D2 = 1
+};
+
+typedef struct {
+    int32_t k;             /* neighbours per query, 1..64                    */
+    double lag;            /* t_w >= 0 (s): valid iff t_j < t_q - lag        */
+    int32_t seed_segments; /* F: segments scanned first, by lower bound,
+                              1..8 (0 = default 4)  (Algorithm 2, F)          */
+    int32_t seed_window;   /* most recent causal segments searched for those
+                              F (0 = default 64, max 256)                     */
+    int32_t extra;         /* candidate slots kept beyond k, 2..32 (0 = 8)   */
+    int32_t flags;         /* TNN_FLAG_*                                      */
+} tnn_knn_params;
+
+typedef struct {
+    uint64_t queries;          /* queries answered                           */
+    uint64_t lb_evals;         /* query-to-cylinder lower bounds evaluated   */
+    uint64_t pairs;            /* point distances computed ("comparisons",
+                                  Table 3)                                   */
+    uint64_t segs_scanned;     /* (query, segment) scans                     */
+    uint64_t fp64_rechecks;    /* distances recomputed in FP64               */
+    uint64_t fallback_queries; /* queries finished by the exact FP64 scan    */
+} tnn_stats;
+
+/*
+ * Exact causal k-NN with TNN (Algorithm 1 lower bounds, Algorithm 2 search
+ * and stop rule).  For every query: lower bounds to the cylinders of the
+ * causally valid segments, most recent first; a segment's points are scanned
+ * only while its bound does not exceed the current k-th candidate; the
+ * search stops once the running maximum of t_B certifies that every
+ * remaining segment is farther than that candidate.  Candidates are ranked
+ * in FP32 with a certified error bound; ranks the FP32 values cannot
+ * separate are settled in FP64 on the GPU.
+ *   d_q     [m][4] float queries (device), or NULL for self-query: every
+ *           indexed point is a query (m must equal n_points).
+ *   d_idx   [m][k] int32 out, d_d2 [m][k] float out (device).
+ *   h_stats optional; when non-NULL the call SYNCHRONISES `stream` and
+ *           fills the counters.
+ * Device scratch (a few bytes per query) is taken from the stream-ordered
+ * allocator and released on the stream.
+ */
+tnn_status tnn_knn(const tnn_index *index, const float *d_q, int64_t m,
+                   const tnn_knn_params *params, int32_t *d_idx, float *d_d2,
+                   tnn_stats *h_stats, tnn_stream_t stream);
+
+/*
+ * The comparator: the same exact causal k-NN by linear search (Sec. 3.6,
+ * Table 1 "Linear search"; Table 3 "Lin. Search") over the time-ordered
+ * copy of the points kept in the index, with the same FP32 ranking and FP64
+ * settlement.  Arguments as tnn_knn (seed_* fields are ignored).
+ */
+tnn_status tnn_knn_bruteforce(const tnn_index *index, const float *d_q,
+                              int64_t m, const tnn_knn_params *params,
+                              int32_t *d_idx, float *d_d2, tnn_stats *h_stats,
+                              tnn_stream_t stream);
+
+/*
+ * Lower bounds used by the search (Algorithm 1 with the cylinder reading of
+ * the exclusion criterion of Sec. 3.4): d_lb [m][n_segments] float (device),
+ * column j for the j-th segment of the t_A order; +inf where the segment
+ * holds no valid point.  Every valid point p of segment j satisfies
+ * lb <= the FP32 distance the search computes for p.
+ */
+tnn_status tnn_segment_lower_bounds(const tnn_index *index, const float *d_q,
+                                    int64_t m, double lag, float *d_lb,
+                                    tnn_stream_t stream);
+
+/*
+ * The work the search must do for each query once its k-th distance d_k is
+ * known (the "comparisons" of Table 3 reduced to the necessary ones):
+ *   h_work[0] = sum over queries of the segments whose temporal bound does
+ *               not exceed d_k (their cylinder bound has to be evaluated);
+ *   h_work[1] = sum over queries of the member points of the segments whose
+ *               cylinder bound does not exceed d_k (they have to be scanned).
+ * d_d2 [m][k] is the output of tnn_knn for the same queries (d_k = column
+ * k-1, +inf when fewer than k points are valid).  Synchronises `stream`.
+ */
+tnn_status tnn_knn_work(const tnn_index *index, const float *d_q, int64_t m,
+                        int32_t k, double lag, const float *d_d2,
+                        uint64_t *h_work, tnn_stream_t stream);
+
+/*
+ * Kernel timing for measurement tools.  While enabled, every launch of the
+ * search kernels (TNN or linear search) is bracketed by CUDA events recorded
+ * on the stream it is launched on.  tnn_profile_read synchronises on those
+ * events and returns the summed device time in ms and the number of
+ * launches since the last reset (reset != 0 clears them).
+ */
+tnn_status tnn_profile_enable(int32_t on);
+tnn_status tnn_profile_read(double *ms, int64_t *launches, int32_t reset);
+
+/* ---------------------------------------------------------------- batched */
+
+typedef struct tnn_batch tnn_batch;
+
+/*
+ * Many independent windows (each its own index, query set and k) answered by
+ * one persistent launch that pulls (window, query tile) items from a device
+ * work queue -- the row compaction of Algorithm 2 ("put completed lines at
+ * the end of the batch") done by letting finished warps take new work.
+ *   indexes[w], d_q[w] (NULL = self-query), m[w], params[w], d_idx[w],
+ *   d_d2[w]: as tnn_knn, per window.  The arrays are read at creation; the
+ *   device buffers must stay valid while the batch is run.
+ * The launch is captured once into a CUDA graph; tnn_batch_run replays it.
+ */
+tnn_status tnn_batch_create(const tnn_index *const *indexes,
+                            const float *const *d_q, const int64_t *m,
+                            const tnn_knn_params *params, int32_t n_windows,
+                            int32_t *const *d_idx, float *const *d_d2,
+                            tnn_batch **out);
+tnn_status tnn_batch_run(tnn_batch *batch, tnn_stream_t stream);
+/* Counters of the last completed run (synchronises `stream`). */
+tnn_status tnn_batch_stats(tnn_batch *batch, tnn_stats *h_stats,
+                           tnn_stream_t stream);
+void tnn_batch_destroy(tnn_batch *batch);
+
+/* -------------------------------------------------------------- autotune */
+
+/*
+ * Choose seed_segments, seed_window and extra for one index and k by timing
+ * the search on a sample of `m_sample` self-queries spread over the index
+ * (CUDA events).  Writes the best into *params (k, lag, flags untouched).
+ * Synchronises `stream`.
+ */
+tnn_status tnn_autotune(const tnn_index *index, tnn_knn_params *params,
+                        int64_t m_sample, tnn_stream_t stream);
+
+/* --------------------------------------------------------------- nowcast */
+
+#define TNN_N_FEAT 6
+
+/*
+ * Context features and inverse-distance-weighted wind (the context of
+ * Sec. 3.1-3.2: neighbours retrieved by TNN feed an aggregator; the paper's
+ * GKA weights by a kernel of the scaled distance, this library's fallback
+ * weights by 1 / (d2 + eps)).
+ *   d_wind [n_points][2] float (u, v) of the indexed points, device.
+ *   d_q    [m][4] queries or NULL (self-query), d_idx/d_d2 [m][k] from tnn_knn.
+ *   h_mean, h_std [6] host: per-channel standardisation of the features
+ *     (dx, dy, dz, dt scaled by sqrt(sigma), u, v); NULL = none.
+ *   d_feat [m][k*6] bf16 out (device) or NULL; missing neighbours give 0.
+ *   d_idw  [m][2] float out (device) or NULL; NaN when no neighbour exists.
+ */
+tnn_status tnn_context_features(const tnn_index *index, const float *d_wind,
+                                const float *d_q, int64_t m,
+                                const int32_t *d_idx, const float *d_d2,
+                                int32_t k, const float *h_mean,
+                                const float *h_std, float idw_eps,
+                                uint16_t *d_feat, float *d_idw,
+                                tnn_stream_t stream);
+
+typedef struct tnn_mlp tnn_mlp;
+
+typedef struct {
+    float lr, beta1, beta2, eps, weight_decay;
+} tnn_adamw_params;
+
+/*
+ * Two-layer GELU MLP aggregator, d_in -> d_hidden -> 2 (the MLP of Sec. 3.2
+ * used here to map a context to the wind at the query).  FP32 master
+ * weights and AdamW moments on the device; BF16 operands with FP32
+ * accumulation in the kernels.  Kaiming-uniform initialisation from `seed`.
+ * d_in a multiple of 16 (<= 1024), d_hidden a multiple of 64 (<= 512).
+ */
+tnn_status tnn_mlp_create(int32_t d_in, int32_t d_hidden, uint64_t seed,
+                          tnn_mlp **out);
+void tnn_mlp_destroy(tnn_mlp *mlp);
+/* Number of floats in the flat parameter layout [W1 (d_in x d_hidden,
+   row-major) | b1 | W2 (d_hidden x 2) | b2]. */
+int64_t tnn_mlp_num_params(const tnn_mlp *mlp);
+/* Host copies of the parameters, optionally the AdamW moments and step
+   (checkpoint / resume).  Synchronous. */
+tnn_status tnn_mlp_get_params(const tnn_mlp *mlp, float *h_params,
+                              float *h_m, float *h_v, int64_t *h_step);
+tnn_status tnn_mlp_set_params(tnn_mlp *mlp, const float *h_params,
+                              const float *h_m, const float *h_v,
+                              int64_t step);
+/* y [B][2] = MLP(x), x [B][d_in] bf16 (device). */
+tnn_status tnn_mlp_forward(const tnn_mlp *mlp, const uint16_t *d_x, int64_t B,
+                           float *d_y, tnn_stream_t stream);
+/* Loss mean((y - target)^2) over B x 2 and its gradient in the flat layout
+   (d_grad, device, tnn_mlp_num_params floats); no update. */
+tnn_status tnn_mlp_gradients(tnn_mlp *mlp, const uint16_t *d_x,
+                             const float *d_target, int64_t B, float *d_loss,
+                             float *d_grad, tnn_stream_t stream);
+/* One AdamW step (decoupled weight decay) on that loss; d_loss optional. */
+tnn_status tnn_mlp_train_step(tnn_mlp *mlp, const uint16_t *d_x,
+                              const float *d_target, int64_t B,
+                              const tnn_adamw_params *opt, float *d_loss,
+                              tnn_stream_t stream);
+
+/*
+ * Nowcast wind at the queries: TNN context (tnn_knn), features and IDW
+ * (tnn_context_features), then the MLP when `mlp` is non-NULL (its input
+ * width must be k * 6), else the IDW average.
+ *   d_uv [m][2] float out (device).  Temporaries come from the
+ *   stream-ordered allocator.
+ */
+tnn_status tnn_nowcast(const tnn_index *index, const float *d_wind,
+                       const float *d_q, int64_t m,
+                       const tnn_knn_params *params, const tnn_mlp *mlp,
+                       const float *h_mean, const float *h_std, float idw_eps,
+                       float *d_uv, tnn_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TNN_H */

@@ -1,0 +1,528 @@
+// Index construction: Sec. 3.4 (partitioning trajectories into sets of K
+// points approximated by segments, the approximation error) and the segment
+// matrices A, t_A, B, t_B, U, E of the Fig. 2 caption.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "tnn_internal.cuh"
+
+// ------------------------------------------------------------------ errors
+
+static thread_local char g_err[512];
+
+void tnn_set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void tnn_clear_error() { g_err[0] = 0; }
+
+extern "C" const char *tnn_last_error(void) { return g_err; }
+
+extern "C" const char *tnn_status_string(tnn_status s)
+{
+    switch (s) {
+    case TNN_OK: return "ok";
+    case TNN_ERR_INVALID_ARG: return "invalid argument";
+    case TNN_ERR_OOM: return "out of device memory";
+    case TNN_ERR_CUDA: return "CUDA error";
+    case TNN_ERR_TIMEOUT: return "device wait timed out";
+    case TNN_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+// ----------------------------------------------------------- device helpers
+
+// Order-preserving map of a float to uint32 (negative values included).
+__device__ __forceinline__ uint32_t f2ord(float f)
+{
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+enum { BAD_VALUE = 1, BAD_ORDER = 2 };
+
+// Every coordinate finite with |v| <= 1e15 (so every FP32 squared
+// difference stays finite); largest |sqrt(sigma) * x| over the spatial axes.
+__global__ void k_validate_points(const float4 *__restrict__ p, int n,
+                                  float s0, float s1, float s2,
+                                  unsigned int *flag, unsigned int *cmax_bits)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float m = 0.f;
+    if (i < n) {
+        float4 v = p[i];
+        bool ok = fabsf(v.x) <= 1e15f && fabsf(v.y) <= 1e15f &&
+                  fabsf(v.z) <= 1e15f && fabsf(v.w) <= 1e15f;
+        if (!ok)
+            atomicOr(flag, (unsigned)BAD_VALUE);
+        else
+            m = fmaxf(fmaxf(fabsf(s0 * v.x), fabsf(s1 * v.y)), fabsf(s2 * v.z));
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.f)
+        atomicMax(cmax_bits, __float_as_uint(m)); // m >= 0: bits are monotone
+}
+
+// Times non-decreasing inside each trajectory.
+__global__ void k_validate_order(const float4 *__restrict__ p,
+                                 const int32_t *__restrict__ traj_off,
+                                 int n_traj, unsigned int *flag)
+{
+    int tr = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tr >= n_traj)
+        return;
+    int b = traj_off[tr], e = traj_off[tr + 1];
+    for (int i = b + 1; i < e; ++i)
+        if (!(p[i].w >= p[i - 1].w)) {
+            atomicOr(flag, (unsigned)BAD_ORDER);
+            return;
+        }
+}
+
+// One thread per segment (build order).  FP64 throughout, rounded once to
+// the stored FP32 record:
+//   A' = fl(sqrt(s) A),  AB' = fl(sqrt(s) B - A'),  U' = fl(AB' / |AB'|^2)
+// The stored segment is [A', A' + AB'] (both exactly representable);
+// r bounds, with upward rounding, the distance of every member's scaled
+// position sqrt(s) p_j to it (Sec. 3.4 E_app, in the cylinder reading).
+__global__ void k_segment_fit(const float4 *__restrict__ p,
+                              const int32_t *__restrict__ traj_off,
+                              const int32_t *__restrict__ seg_off, int n_traj,
+                              int S, int K, double q0, double q1, double q2,
+                              float4 *__restrict__ rec,
+                              unsigned long long *__restrict__ keys,
+                              unsigned int *rmax_bits)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S)
+        return;
+    // trajectory of segment s: largest tr with seg_off[tr] <= s
+    int lo = 0, hi = n_traj; // seg_off[lo] <= s < seg_off[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (seg_off[mid] <= s)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    int tr = lo;
+    int first = traj_off[tr] + (s - seg_off[tr]) * K;
+    int count = min(K, traj_off[tr + 1] - first);
+    float4 pa = p[first], pb = p[first + count - 1];
+    double A[3], E[3], AB[3];
+    float Af[3], ABf[3], Uf[3];
+    const double qq[3] = {q0, q1, q2};
+    const float pav[3] = {pa.x, pa.y, pa.z}, pbv[3] = {pb.x, pb.y, pb.z};
+    for (int i = 0; i < 3; ++i) {
+        Af[i] = (float)(qq[i] * (double)pav[i]);
+        A[i] = (double)Af[i];
+        ABf[i] = (float)(qq[i] * (double)pbv[i] - A[i]);
+        AB[i] = (double)ABf[i];
+        E[i] = A[i] + AB[i];
+    }
+    double ab2 = AB[0] * AB[0] + AB[1] * AB[1] + AB[2] * AB[2];
+    for (int i = 0; i < 3; ++i)
+        Uf[i] = ab2 > 1e-30 ? (float)(AB[i] / ab2) : 0.f;
+    double r2 = 0.0, mag = fabs(A[0]) + fabs(A[1]) + fabs(A[2]) +
+                          fabs(E[0]) + fabs(E[1]) + fabs(E[2]);
+    for (int j = 0; j < count; ++j) {
+        float4 v = p[first + j];
+        double P[3] = {qq[0] * (double)v.x, qq[1] * (double)v.y, qq[2] * (double)v.z};
+        double lam = 0.0;
+        if (ab2 > 0.0) {
+            lam = ((P[0] - A[0]) * AB[0] + (P[1] - A[1]) * AB[1] +
+                   (P[2] - A[2]) * AB[2]) / ab2;
+            lam = fmin(fmax(lam, 0.0), 1.0);
+        }
+        double d2 = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            double e = P[i] - (A[i] + lam * AB[i]);
+            d2 += e * e;
+        }
+        r2 = fmax(r2, d2);
+        mag = fmax(mag, fabs(P[0]) + fabs(P[1]) + fabs(P[2]));
+    }
+    // FP64 rounding of the distances above is far below 1e-12 * mag.
+    double r = sqrt(r2) + 1e-12 * (1.0 + mag);
+    float rf = __double2float_ru(r);
+    rec[4 * s + 0] = make_float4(Af[0], Af[1], Af[2], pa.w);
+    rec[4 * s + 1] = make_float4(Uf[0], Uf[1], Uf[2], pb.w);
+    rec[4 * s + 2] = make_float4(ABf[0], ABf[1], ABf[2], rf);
+    rec[4 * s + 3] = make_float4(__int_as_float(first), __int_as_float(count),
+                                 __int_as_float(tr), __int_as_float(s));
+    keys[s] = ((unsigned long long)f2ord(pa.w) << 32) | (unsigned)s;
+    atomicMax(rmax_bits, __float_as_uint(rf));
+}
+
+__global__ void k_time_keys(const float4 *__restrict__ p, int n,
+                            unsigned long long *__restrict__ keys, int n2)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        keys[i] = ((unsigned long long)f2ord(p[i].w) << 32) | (unsigned)i;
+    else if (i < n2)
+        keys[i] = ~0ull;
+}
+
+__global__ void k_fill(unsigned long long *keys, int from, int n2)
+{
+    int i = from + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n2)
+        keys[i] = ~0ull;
+}
+
+// ------------------------------------------------------------ bitonic sort
+
+#define BS_BLOCK 2048
+
+__device__ __forceinline__ void cmpx(unsigned long long &a,
+                                     unsigned long long &b, bool asc)
+{
+    if ((a > b) == asc) {
+        unsigned long long t = a;
+        a = b;
+        b = t;
+    }
+}
+
+// Full bitonic sort of every 2048-element block (direction of each block
+// follows its global position, as the network requires).
+__global__ void k_bitonic_block(unsigned long long *keys)
+{
+    __shared__ unsigned long long s[BS_BLOCK];
+    const int base = blockIdx.x * BS_BLOCK;
+    s[threadIdx.x] = keys[base + threadIdx.x];
+    s[threadIdx.x + 1024] = keys[base + threadIdx.x + 1024];
+    __syncthreads();
+    for (int k = 2; k <= BS_BLOCK; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            int t = threadIdx.x;
+            int i = (t / j) * 2 * j + (t % j);
+            bool asc = ((base + i) & k) == 0;
+            cmpx(s[i], s[i + j], asc);
+            __syncthreads();
+        }
+    keys[base + threadIdx.x] = s[threadIdx.x];
+    keys[base + threadIdx.x + 1024] = s[threadIdx.x + 1024];
+}
+
+// Steps j < 2048 of merge stage k, inside each block.
+__global__ void k_bitonic_merge_local(unsigned long long *keys, int k)
+{
+    __shared__ unsigned long long s[BS_BLOCK];
+    const int base = blockIdx.x * BS_BLOCK;
+    s[threadIdx.x] = keys[base + threadIdx.x];
+    s[threadIdx.x + 1024] = keys[base + threadIdx.x + 1024];
+    __syncthreads();
+    for (int j = BS_BLOCK >> 1; j > 0; j >>= 1) {
+        int t = threadIdx.x;
+        int i = (t / j) * 2 * j + (t % j);
+        bool asc = ((base + i) & k) == 0;
+        cmpx(s[i], s[i + j], asc);
+        __syncthreads();
+    }
+    keys[base + threadIdx.x] = s[threadIdx.x];
+    keys[base + threadIdx.x + 1024] = s[threadIdx.x + 1024];
+}
+
+__global__ void k_bitonic_global(unsigned long long *keys, int j, int k)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x; // one per pair
+    int i = (t / j) * 2 * j + (t % j);
+    bool asc = (i & k) == 0;
+    unsigned long long a = keys[i], b = keys[i + j];
+    if ((a > b) == asc) {
+        keys[i] = b;
+        keys[i + j] = a;
+    }
+}
+
+static int next_pow2_sort(int64_t n)
+{
+    int64_t p = BS_BLOCK;
+    while (p < n)
+        p <<= 1;
+    return (int)p;
+}
+
+static void bitonic_sort(unsigned long long *keys, int n2, cudaStream_t st)
+{
+    k_bitonic_block<<<n2 / BS_BLOCK, 1024, 0, st>>>(keys);
+    for (int k = 2 * BS_BLOCK; k <= n2; k <<= 1) {
+        for (int j = k >> 1; j >= BS_BLOCK; j >>= 1)
+            k_bitonic_global<<<(n2 / 2 + 255) / 256, 256, 0, st>>>(keys, j, k);
+        k_bitonic_merge_local<<<n2 / BS_BLOCK, 1024, 0, st>>>(keys, k);
+    }
+}
+
+// --------------------------------------------------------- gather / scans
+
+__global__ void k_gather_segments(const unsigned long long *__restrict__ keys,
+                                  const float4 *__restrict__ rec, int S,
+                                  float4 *__restrict__ out,
+                                  float *__restrict__ tA)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S)
+        return;
+    int s = (int)(keys[i] & 0xffffffffu);
+    float4 a = rec[4 * s];
+    out[4 * i + 0] = a;
+    out[4 * i + 1] = rec[4 * s + 1];
+    out[4 * i + 2] = rec[4 * s + 2];
+    out[4 * i + 3] = rec[4 * s + 3];
+    tA[i] = a.w;
+}
+
+// Running maximum of t_B over the t_A order (one block).
+__global__ void k_prefix_max_tB(const float4 *__restrict__ seg, int S,
+                                float *__restrict__ pm)
+{
+    __shared__ float wmax[32];
+    __shared__ float carry;
+    if (threadIdx.x == 0)
+        carry = -INFINITY;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = 0; base < S; base += 1024) {
+        int i = base + threadIdx.x;
+        float v = i < S ? seg[4 * i + 1].w : -INFINITY;
+        for (int o = 1; o < 32; o <<= 1) {
+            float u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o)
+                v = fmaxf(v, u);
+        }
+        if (lane == 31)
+            wmax[w] = v;
+        __syncthreads();
+        if (w == 0) {
+            float x = wmax[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                float u = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o)
+                    x = fmaxf(x, u);
+            }
+            wmax[lane] = x;
+        }
+        __syncthreads();
+        float c = carry;
+        if (w > 0)
+            v = fmaxf(v, wmax[w - 1]);
+        v = fmaxf(v, c);
+        if (i < S)
+            pm[i] = v;
+        __syncthreads();
+        if (threadIdx.x == 1023)
+            carry = v;
+        __syncthreads();
+    }
+}
+
+__global__ void k_gather_points(const unsigned long long *__restrict__ keys,
+                                const float4 *__restrict__ p, int n,
+                                float4 *__restrict__ out,
+                                int32_t *__restrict__ idx)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    int j = (int)(keys[i] & 0xffffffffu);
+    out[i] = p[j];
+    idx[i] = j;
+}
+
+// ---------------------------------------------------------------- host API
+
+static void free_index(tnn_index *ix)
+{
+    if (!ix)
+        return;
+    cudaFree(ix->pts);
+    cudaFree(ix->seg);
+    cudaFree(ix->segTA);
+    cudaFree(ix->segPM);
+    cudaFree(ix->pts_t);
+    cudaFree(ix->idx_t);
+    delete ix;
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() { cudaFree(p); }
+};
+
+extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
+                                         const int64_t *h_traj_off,
+                                         int64_t n_traj,
+                                         const tnn_build_params *params,
+                                         tnn_stream_t stream, tnn_index **out)
+{
+    tnn_clear_error();
+    TNN_ARG_CHECK(out != nullptr, "out is NULL");
+    *out = nullptr;
+    TNN_ARG_CHECK(params != nullptr, "params is NULL");
+    TNN_ARG_CHECK(n >= 1 && n < (1ll << 31) - 64, "n must be in [1, 2^31-64), got %lld",
+                  (long long)n);
+    TNN_ARG_CHECK(d_xyzt != nullptr && h_traj_off != nullptr, "NULL input");
+    TNN_ARG_CHECK(((uintptr_t)d_xyzt & 15) == 0, "d_xyzt must be 16-byte aligned");
+    TNN_ARG_CHECK(n_traj >= 1 && n_traj <= n, "n_traj must be in [1, n]");
+    const int K = params->seg_len;
+    TNN_ARG_CHECK(K >= 2 && K <= 64, "seg_len must be in [2, 64], got %d", K);
+    for (int i = 0; i < 4; ++i) {
+        double s = params->sigma[i];
+        TNN_ARG_CHECK(isfinite(s) && s >= 0.0 && s <= 1e6,
+                      "sigma[%d] must be finite in [0, 1e6]", i);
+    }
+    TNN_ARG_CHECK(h_traj_off[0] == 0 && h_traj_off[n_traj] == n,
+                  "traj_off must start at 0 and end at n");
+    std::vector<int32_t> toff(n_traj + 1), soff(n_traj + 1);
+    int64_t S = 0;
+    for (int64_t t = 0; t < n_traj; ++t) {
+        int64_t len = h_traj_off[t + 1] - h_traj_off[t];
+        TNN_ARG_CHECK(len >= 0, "traj_off must be non-decreasing");
+        toff[t] = (int32_t)h_traj_off[t];
+        soff[t] = (int32_t)S;
+        S += (len + K - 1) / K;
+    }
+    toff[n_traj] = (int32_t)n;
+    soff[n_traj] = (int32_t)S;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    tnn_index *ix = new tnn_index();
+    memset(ix, 0, sizeof(*ix));
+    cudaGetDevice(&ix->device);
+    ix->n = n;
+    ix->n_traj = n_traj;
+    ix->S = S;
+    ix->K = K;
+    for (int i = 0; i < 4; ++i) {
+        ix->sigma[i] = params->sigma[i];
+        ix->sig_f[i] = (float)params->sigma[i];
+    }
+    for (int i = 0; i < 3; ++i)
+        ix->ssq_f[i] = (float)sqrt(params->sigma[i]);
+
+    const int n2 = next_pow2_sort(n);
+    const int s2 = next_pow2_sort(S);
+    DevBuf toff_d, soff_d, rec_d, keys_d, flags_d;
+    cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, bytes)                                                     \
+    if (e == cudaSuccess)                                                     \
+        e = cudaMalloc((void **)&(ptr), (bytes));
+    ALLOC(ix->pts, sizeof(float4) * n);
+    ALLOC(ix->seg, sizeof(float4) * 4 * S);
+    ALLOC(ix->segTA, sizeof(float) * S);
+    ALLOC(ix->segPM, sizeof(float) * S);
+    ALLOC(ix->pts_t, sizeof(float4) * n);
+    ALLOC(ix->idx_t, sizeof(int32_t) * n);
+    ALLOC(toff_d.p, sizeof(int32_t) * (n_traj + 1));
+    ALLOC(soff_d.p, sizeof(int32_t) * (n_traj + 1));
+    ALLOC(rec_d.p, sizeof(float4) * 4 * S);
+    ALLOC(keys_d.p, sizeof(unsigned long long) * (n2 > s2 ? n2 : s2));
+    ALLOC(flags_d.p, sizeof(unsigned int) * 4);
+#undef ALLOC
+    if (e != cudaSuccess) {
+        free_index(ix);
+        tnn_set_error("index allocation failed: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? TNN_ERR_OOM : TNN_ERR_CUDA;
+    }
+    unsigned int *flag = (unsigned int *)flags_d.p;
+    unsigned long long *keys = (unsigned long long *)keys_d.p;
+    const int tb = 256;
+    e = cudaMemcpyAsync(ix->pts, d_xyzt, sizeof(float4) * n, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(toff_d.p, toff.data(), sizeof(int32_t) * (n_traj + 1),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(soff_d.p, soff.data(), sizeof(int32_t) * (n_traj + 1),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(flag, 0, sizeof(unsigned int) * 4, st);
+    if (e != cudaSuccess) {
+        free_index(ix);
+        tnn_set_error("index upload failed: %s", cudaGetErrorString(e));
+        return TNN_ERR_CUDA;
+    }
+    const int ni = (int)n, Si = (int)S, Ti = (int)n_traj;
+    k_validate_points<<<(ni + tb - 1) / tb, tb, 0, st>>>(
+        ix->pts, ni, ix->ssq_f[0], ix->ssq_f[1], ix->ssq_f[2], flag, flag + 1);
+    k_validate_order<<<(Ti + tb - 1) / tb, tb, 0, st>>>(
+        ix->pts, (const int32_t *)toff_d.p, Ti, flag);
+    k_segment_fit<<<(Si + tb - 1) / tb, tb, 0, st>>>(
+        ix->pts, (const int32_t *)toff_d.p, (const int32_t *)soff_d.p, Ti, Si, K,
+        sqrt(params->sigma[0]), sqrt(params->sigma[1]), sqrt(params->sigma[2]),
+        (float4 *)rec_d.p, keys, flag + 2);
+    k_fill<<<(s2 - Si + tb - 1) / tb + 1, tb, 0, st>>>(keys, Si, s2);
+    bitonic_sort(keys, s2, st);
+    k_gather_segments<<<(Si + tb - 1) / tb, tb, 0, st>>>(keys, (const float4 *)rec_d.p,
+                                                         Si, ix->seg, ix->segTA);
+    k_prefix_max_tB<<<1, 1024, 0, st>>>(ix->seg, Si, ix->segPM);
+    k_time_keys<<<(n2 + tb - 1) / tb, tb, 0, st>>>(ix->pts, ni, keys, n2);
+    bitonic_sort(keys, n2, st);
+    k_gather_points<<<(ni + tb - 1) / tb, tb, 0, st>>>(keys, ix->pts, ni, ix->pts_t,
+                                                       ix->idx_t);
+    unsigned int hflag[4] = {0, 0, 0, 0};
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hflag, flag, sizeof(hflag), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        free_index(ix);
+        tnn_set_error("index build failed: %s", cudaGetErrorString(e));
+        return TNN_ERR_CUDA;
+    }
+    if (hflag[0] & BAD_VALUE) {
+        free_index(ix);
+        tnn_set_error("non-finite or too large (|v| > 1e15) coordinate in input");
+        return TNN_ERR_INVALID_ARG;
+    }
+    if (hflag[0] & BAD_ORDER) {
+        free_index(ix);
+        tnn_set_error("times are not sorted inside a trajectory");
+        return TNN_ERR_INVALID_ARG;
+    }
+    memcpy(&ix->coord_max, &hflag[1], sizeof(float));
+    memcpy(&ix->max_radius, &hflag[2], sizeof(float));
+    *out = ix;
+    return TNN_OK;
+}
+
+extern "C" void tnn_index_destroy(tnn_index *index) { free_index(index); }
+
+extern "C" tnn_status tnn_index_get_info(const tnn_index *ix, tnn_index_info *out)
+{
+    tnn_clear_error();
+    TNN_ARG_CHECK(ix && out, "NULL argument");
+    out->n_points = ix->n;
+    out->n_traj = ix->n_traj;
+    out->n_segments = ix->S;
+    out->seg_len = ix->K;
+    out->coord_max = ix->coord_max;
+    out->max_radius = ix->max_radius;
+    return TNN_OK;
+}
+
+extern "C" tnn_status tnn_index_export(const tnn_index *ix, float *d_seg,
+                                       float *d_pm, tnn_stream_t stream)
+{
+    tnn_clear_error();
+    TNN_ARG_CHECK(ix && d_seg, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    TNN_CUDA_TRY(cudaMemcpyAsync(d_seg, ix->seg, sizeof(float4) * 4 * ix->S,
+                                 cudaMemcpyDeviceToDevice, st));
+    if (d_pm)
+        TNN_CUDA_TRY(cudaMemcpyAsync(d_pm, ix->segPM, sizeof(float) * ix->S,
+                                     cudaMemcpyDeviceToDevice, st));
+    return TNN_OK;
+}

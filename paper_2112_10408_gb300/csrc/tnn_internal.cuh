@@ -1,0 +1,116 @@
+// Internal declarations shared by the translation units of libtnn.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tnn.h"
+
+// ------------------------------------------------------------------ errors
+
+void tnn_set_error(const char *fmt, ...);
+void tnn_clear_error();
+
+#define TNN_CUDA_TRY(call)                                                    \
+    do {                                                                      \
+        cudaError_t e__ = (call);                                             \
+        if (e__ != cudaSuccess) {                                             \
+            tnn_set_error("%s failed: %s (%s:%d)", #call,                     \
+                          cudaGetErrorString(e__), __FILE__, __LINE__);       \
+            return e__ == cudaErrorMemoryAllocation ? TNN_ERR_OOM             \
+                                                    : TNN_ERR_CUDA;           \
+        }                                                                     \
+    } while (0)
+
+#define TNN_ARG_CHECK(cond, ...)                                              \
+    do {                                                                      \
+        if (!(cond)) {                                                        \
+            tnn_set_error(__VA_ARGS__);                                       \
+            return TNN_ERR_INVALID_ARG;                                       \
+        }                                                                     \
+    } while (0)
+
+// ------------------------------------------------------------------- index
+
+// Floats per exported / stored segment record (4 x float4).
+#define TNN_SEG_FLOATS 16
+
+struct tnn_index {
+    int device;
+    int64_t n;      // points
+    int64_t n_traj; // trajectories
+    int64_t S;      // segments
+    int32_t K;      // points per segment
+    double sigma[4];
+    float sig_f[4];  // sigma rounded to float
+    float ssq_f[3];  // sqrt(sigma) rounded to float, spatial axes
+    float coord_max; // max |ssq * coordinate| over the points
+    float max_radius;
+    float4 *pts;     // [n] raw (x, y, z, t) in input order
+    float4 *seg;     // [S][4] records ordered by t_A (see tnn_index_export)
+    float *segTA;    // [S] t_A in that order
+    float *segPM;    // [S] running max of t_B in that order
+    float4 *pts_t;   // [n] points ordered by (t, index)  (linear search)
+    int32_t *idx_t;  // [n] their input index
+};
+
+// Parameters of one independent k-NN problem, read by the search kernels.
+struct KnnWin {
+    const float4 *pts;
+    const float4 *seg;
+    const float *segTA;
+    const float *segPM;
+    const float4 *pts_t;
+    const int32_t *idx_t;
+    const float4 *q; // queries (== pts for self-query)
+    int32_t *out_idx;
+    float *out_d2;
+    int64_t m;
+    int64_t tile_begin; // first global tile of this window
+    double sigd[4];
+    double lag;
+    float sig[4];
+    float ssq[3];
+    float coord_max;
+    int32_t n;
+    int32_t S;
+    int32_t k;
+    int32_t L; // candidate slots per query (k + extra)
+    int32_t F; // seed segments
+    int32_t W0; // seed window
+    int32_t flags;
+    int32_t pad_;
+};
+
+#define TNN_MAX_WINDOWS_PARAM 1
+
+struct KnnScratch {
+    unsigned long long tile_counter;
+    unsigned long long stats[8]; // queries, lb, pairs, segs, fp64, fallback
+    unsigned int n_fallback;
+    unsigned int status;
+};
+
+struct KnnLaunch {
+    KnnWin w0;            // used when nwin == 1
+    const KnnWin *wins;   // device array when nwin > 1
+    int32_t nwin;
+    int32_t L_max;
+    int32_t kseg_max;     // largest segment length over the windows
+    int32_t pad_;
+    int64_t total_tiles;
+    KnnScratch *scr;
+    int2 *fb_list;        // (window, query) needing the exact FP64 scan
+    int64_t fb_cap;
+};
+
+// Launch helpers (tnn_knn.cu).
+tnn_status tnn_fill_window(const tnn_index *ix, const float *d_q, int64_t m,
+                           const tnn_knn_params *p, int32_t *d_idx,
+                           float *d_d2, KnnWin *w);
+tnn_status tnn_launch_search(const KnnLaunch &L, bool brute,
+                             cudaStream_t stream);
+size_t tnn_search_smem_per_warp(int L_max, int kseg_max, bool brute);
+
+#define TNN_WARPS_PER_CTA 4
+#define TNN_TILE 32

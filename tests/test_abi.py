@@ -1,0 +1,60 @@
+"""The C-ABI library loads and exports every entry point include/tnn.h
+declares; argument checks answer before any device work (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2112_10408_gb300 import build as tnn_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tnn.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tnn_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = tnn_build.build()
+    return ctypes.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, f"missing exports: {missing}"
+
+
+def test_binding_covers_header():
+    from paper_2112_10408_gb300 import tnn
+    assert set(declared_functions()) == set(tnn.exported_symbols())
+
+
+def test_argument_errors_without_device(lib):
+    from paper_2112_10408_gb300 import tnn
+    L = tnn.load_library()
+    h = ctypes.c_void_p()
+    p = tnn.tnn_build_params()
+    p.seg_len = 1  # K < 2
+    off = (ctypes.c_int64 * 2)(0, 10)
+    st = L.tnn_build_segments(ctypes.c_void_p(16), 10, off, 1, ctypes.byref(p), None, ctypes.byref(h))
+    assert st == 1 and b"seg_len" in L.tnn_last_error()
+    p.seg_len = 10
+    p.sigma[3] = -1.0
+    st = L.tnn_build_segments(ctypes.c_void_p(16), 10, off, 1, ctypes.byref(p), None, ctypes.byref(h))
+    assert st == 1 and b"sigma" in L.tnn_last_error()
+    kp = tnn.make_knn_params(0)
+    st = L.tnn_knn(ctypes.c_void_p(8), None, 10, ctypes.byref(kp), None, None, None, None)
+    assert st == 1 and b"k must" in L.tnn_last_error()
+    kp = tnn.make_knn_params(8, lag=-1.0)
+    st = L.tnn_knn(ctypes.c_void_p(8), None, 10, ctypes.byref(kp), None, None, None, None)
+    assert st == 1 and b"lag" in L.tnn_last_error()
+    st = L.tnn_mlp_create(100, 256, 0, ctypes.byref(h))
+    assert st == 1 and b"d_in" in L.tnn_last_error()
+    assert L.tnn_status_string(0) == b"ok"

@@ -1,0 +1,293 @@
+"""Parity of the CUDA search (TNN and the linear-search comparator) with the
+FP64 oracle, through the C ABI: neighbour indices bit-exact (ties by index),
+distances within 1e-5 relative; plus the index and bound invariants."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2112_10408_gb300 import synth
+from paper_2112_10408_gb300 import tnn
+from tests._helpers import assert_knn_equal
+
+pytestmark = pytest.mark.gpu
+SIG = synth.SIGMA_DEFAULT
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2112_10408_gb300 import build
+    build.build()
+    tnn.load_library()
+    torch.cuda.init()
+
+
+def _index(wl, K, sigma=SIG):
+    return tnn.tnn_build_segments(torch.from_numpy(wl.xyzt).cuda(), wl.traj_off, sigma, K)
+
+
+def _both(ix, k, lag, q=None, **kw):
+    ti, td = tnn.tnn_knn(ix, k, lag, q=q, **kw)
+    bi, bd = tnn.tnn_knn_bruteforce(ix, k, lag, q=q, **kw)
+    torch.cuda.synchronize()
+    return ti.cpu().numpy(), td.cpu().numpy(), bi.cpu().numpy(), bd.cpu().numpy()
+
+
+def test_tiny_config_all_queries():
+    # 200 flights x 50 samples, k = 8, 10-point segments, mask t_j < t_i.
+    wl = synth.tiny()
+    ix = _index(wl, 10)
+    ti, td, bi, bd = _both(ix, 8, 0.0)
+    oi, od = oracle.knn(wl.xyzt, 8, SIG)
+    assert_knn_equal(ti, td, oi, od, what="tnn tiny")
+    assert_knn_equal(bi, bd, oi, od, what="linear tiny")
+
+
+@pytest.mark.parametrize("k,lag,K", [(1, 0.0, 10), (5, 37.0, 7), (32, 0.0, 20),
+                                     (64, 120.0, 13), (17, 0.0, 2), (40, 0.0, 64)])
+def test_small_configs(k, lag, K):
+    # several warps of queries and a ragged tail (2,173 rows)
+    wl = synth.flights(41, 53, seed=100 + k, n_routes=5)
+    ix = _index(wl, K)
+    ti, td, bi, bd = _both(ix, k, lag)
+    oi, od = oracle.knn(wl.xyzt, k, SIG, lag=lag)
+    assert_knn_equal(ti, td, oi, od, what=f"tnn k={k} lag={lag} K={K}")
+    assert_knn_equal(bi, bd, oi, od, what=f"linear k={k} lag={lag} K={K}")
+
+
+@pytest.mark.parametrize("tuning", [dict(seed_segments=1, seed_window=1, extra=2),
+                                    dict(seed_segments=8, seed_window=256, extra=32),
+                                    dict(seed_segments=3, seed_window=17, extra=5)])
+def test_tuning_knobs_do_not_change_results(tuning):
+    wl = synth.flights(60, 70, seed=7, n_routes=6)
+    ix = _index(wl, 12)
+    ti, td = tnn.tnn_knn(ix, 16, 30.0, **tuning)
+    oi, od = oracle.knn(wl.xyzt, 16, SIG, lag=30.0)
+    assert_knn_equal(ti.cpu().numpy(), td.cpu().numpy(), oi, od, what=str(tuning))
+
+
+def test_exact_d2_flag_gives_fp64_rounded_distances():
+    wl = synth.flights(30, 40, seed=3, n_routes=4)
+    ix = _index(wl, 10)
+    ti, td = tnn.tnn_knn(ix, 12, 0.0, exact_d2=True)
+    bi, bd = tnn.tnn_knn_bruteforce(ix, 12, 0.0, exact_d2=True)
+    oi, od = oracle.knn(wl.xyzt, 12, SIG)
+    for i, d in ((ti, td), (bi, bd)):
+        np.testing.assert_array_equal(i.cpu().numpy(), oi)
+        np.testing.assert_array_equal(d.cpu().numpy(), od)  # bit-identical
+
+
+def test_tie_heavy_lattice_uses_exact_settlement():
+    # integer lattice, integer times: many equal distances and duplicates
+    wl = synth.lattice(40, 30, seed=11, side=4)
+    sigma = (1.0, 1.0, 1.0, 1.0)
+    ix = _index(wl, 6, sigma)
+    for k in (3, 8, 20):
+        ti, td, st = tnn.tnn_knn(ix, k, 0.0, stats=True)
+        bi, bd = tnn.tnn_knn_bruteforce(ix, k, 0.0)
+        oi, od = oracle.knn(wl.xyzt, k, sigma)
+        assert_knn_equal(ti.cpu().numpy(), td.cpu().numpy(), oi, od, what=f"tnn lattice k={k}")
+        assert_knn_equal(bi.cpu().numpy(), bd.cpu().numpy(), oi, od, what=f"linear lattice k={k}")
+        assert st["fp64_rechecks"] > 0
+
+
+def test_external_queries_and_future_queries():
+    wl = synth.flights(50, 60, seed=21, n_routes=5)
+    ix = _index(wl, 15)
+    rng = np.random.default_rng(0)
+    q = wl.xyzt[rng.choice(wl.n, 333, replace=False)].copy()
+    q[:, :3] += rng.normal(0, 3.0, size=(333, 3)).astype(np.float32)
+    q[::3, 3] = 1e5  # after every point: the whole set is valid
+    q[1::7, 3] = -1.0  # before every point: nothing valid
+    qd = torch.from_numpy(q).cuda()
+    ti, td, bi, bd = _both(ix, 9, 15.0, q=qd)
+    oi, od = oracle.knn(wl.xyzt, 9, SIG, lag=15.0, queries=q)
+    assert_knn_equal(ti, td, oi, od, what="tnn external")
+    assert_knn_equal(bi, bd, oi, od, what="linear external")
+    assert (ti[1::7] == -1).all() and np.isinf(td[1::7]).all()
+
+
+@pytest.mark.parametrize("sigma", [(1.0, 1.0, 1.0, 0.0), (0.0, 0.0, 0.0, 1.0), (0.0, 0.0, 0.0, 0.0),
+                                   (3.0, 0.5, 40.0, 2.0)])
+def test_sigma_special_cases(sigma):
+    # st = 0: no temporal pruning; spatial weights 0: pure time; all 0: every
+    # valid point ties at 0 and the order is by index.
+    wl = synth.flights(25, 33, seed=5, n_routes=3)
+    ix = _index(wl, 8, sigma)
+    ti, td, bi, bd = _both(ix, 6, 0.0)
+    oi, od = oracle.knn(wl.xyzt, 6, sigma)
+    assert_knn_equal(ti, td, oi, od, what=f"tnn sigma={sigma}")
+    assert_knn_equal(bi, bd, oi, od, what=f"linear sigma={sigma}")
+
+
+def test_degenerate_inputs():
+    # one point; trajectories of length 1; a single trajectory; k > N
+    one = np.array([[1.0, 2.0, 3.0, 4.0]], np.float32)
+    ix = tnn.tnn_build_segments(torch.from_numpy(one).cuda(), [0, 1], SIG, 4)
+    i, d = tnn.tnn_knn(ix, 3, 0.0)
+    assert (i.cpu().numpy() == -1).all() and np.isinf(d.cpu().numpy()).all()
+    rng = np.random.default_rng(1)
+    pts = np.column_stack([rng.uniform(0, 10, 97), rng.uniform(0, 10, 97),
+                           rng.uniform(0, 1, 97), np.sort(rng.uniform(0, 100, 97))]).astype(np.float32)
+    for off in ([0, 97], list(range(98))):
+        ix = tnn.tnn_build_segments(torch.from_numpy(pts).cuda(), off, SIG, 5)
+        for k in (1, 64):
+            ti, td, bi, bd = _both(ix, k, 0.0)
+            oi, od = oracle.knn(pts, k, SIG)
+            assert_knn_equal(ti, td, oi, od, what=f"tnn degenerate off={len(off)} k={k}")
+            assert_knn_equal(bi, bd, oi, od, what=f"linear degenerate off={len(off)} k={k}")
+
+
+def test_invalid_inputs_are_rejected():
+    bad = np.array([[0, 0, 0, 0], [np.nan, 0, 0, 1]], np.float32)
+    with pytest.raises(tnn.TNNError, match="non-finite"):
+        tnn.tnn_build_segments(torch.from_numpy(bad).cuda(), [0, 2], SIG, 2)
+    unsorted = np.array([[0, 0, 0, 5], [0, 0, 0, 1]], np.float32)
+    with pytest.raises(tnn.TNNError, match="sorted"):
+        tnn.tnn_build_segments(torch.from_numpy(unsorted).cuda(), [0, 2], SIG, 2)
+    wl = synth.flights(3, 10, seed=1, n_routes=1)
+    ix = _index(wl, 5)
+    with pytest.raises(tnn.TNNError, match="k must"):
+        tnn.tnn_knn(ix, 65, 0.0)
+    with pytest.raises(tnn.TNNError, match="self-query"):
+        idx = torch.empty((5, 4), dtype=torch.int32, device="cuda")
+        d2 = torch.empty((5, 4), dtype=torch.float32, device="cuda")
+        ctypes_p = tnn.make_knn_params(4)
+        import ctypes
+        tnn._check(tnn._L().tnn_knn(ix.handle, None, 5, ctypes.byref(ctypes_p), tnn._ptr(idx),
+                                    tnn._ptr(d2), None, tnn._stream()))
+
+
+def test_stress_layouts_random_points_and_srw():
+    # Sec. 4.2: random points (pathological: the bound prunes almost nothing,
+    # comparisons approach the linear search) and smoothed random walks.
+    rnd = synth.random_points(6000, 20, seed=4)
+    srw = synth.smoothed_random_walks(40, 150, seed=4)
+    for wl, name in ((rnd, "rand"), (srw, "srw")):
+        ix = _index(wl, 20)
+        ti, td, st = tnn.tnn_knn(ix, 32, 0.0, stats=True)
+        bi, bd, sb = tnn.tnn_knn_bruteforce(ix, 32, 0.0, stats=True)
+        q = synth.query_sample(wl.n, 700, seed=9)
+        oi, od = oracle.knn(wl.xyzt, 32, SIG, qsel=q)
+        assert_knn_equal(ti.cpu().numpy()[q], td.cpu().numpy()[q], oi, od, what=f"tnn {name}")
+        assert_knn_equal(bi.cpu().numpy()[q], bd.cpu().numpy()[q], oi, od, what=f"linear {name}")
+        if name == "srw":
+            assert st["pairs"] < 0.5 * sb["pairs"]
+
+
+def test_index_segments_match_oracle():
+    wl = synth.flights(20, 47, seed=2, n_routes=3)
+    ix = _index(wl, 10)
+    seg, pm = tnn.tnn_index_export(ix)
+    seg = seg.cpu().numpy()
+    pm = pm.cpu().numpy()
+    ref = oracle.segments(wl.xyzt, wl.traj_off, SIG, 10)
+    S = ref["first"].shape[0]
+    assert ix.n_segments == S
+    bid = seg[:, 15].view(np.int32)
+    # ordered by t_A, stable by build order
+    order = np.lexsort((np.arange(S), ref["tA"]))
+    np.testing.assert_array_equal(bid, order)
+    np.testing.assert_array_equal(seg[:, 12].view(np.int32), ref["first"][bid])
+    np.testing.assert_array_equal(seg[:, 13].view(np.int32), ref["count"][bid])
+    np.testing.assert_allclose(seg[:, 0:3], ref["A"][bid], rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(seg[:, 0:3] + seg[:, 8:11], ref["B"][bid], rtol=1e-6, atol=1e-4)
+    assert (seg[:, 11] >= ref["radius"][bid] - 1e-4).all()
+    assert (seg[:, 11] <= ref["radius"][bid] + 1e-3).all()
+    np.testing.assert_array_equal(pm, np.maximum.accumulate(seg[:, 7]))
+    # every member within r of the stored segment [A', A' + AB'] (FP64 check)
+    sq = np.sqrt(np.asarray(SIG[:3]))
+    for s in range(S):
+        f, c = seg[s, 12:14].view(np.int32)
+        A = seg[s, 0:3].astype(np.float64)
+        B = A + seg[s, 8:11].astype(np.float64)
+        for p in wl.xyzt[f:f + c]:
+            d = math.sqrt(oracle.point_segment_sq(p[:3].astype(np.float64) * sq, A, B))
+            assert d <= seg[s, 11]
+
+
+def test_lower_bounds_never_exceed_point_distances():
+    wl = synth.flights(30, 50, seed=8, n_routes=4)
+    ix = _index(wl, 10)
+    seg, _ = tnn.tnn_index_export(ix)
+    seg = seg.cpu().numpy()
+    rng = np.random.default_rng(2)
+    rows = rng.choice(wl.n, 64, replace=False)
+    for lag in (0.0, 60.0):
+        q = torch.from_numpy(wl.xyzt[rows]).cuda()
+        lb = tnn.tnn_segment_lower_bounds(ix, q=q, lag=lag).cpu().numpy()
+        for a, r in enumerate(rows):
+            qp = wl.xyzt[r]
+            for s in range(seg.shape[0]):
+                f, c = seg[s, 12:14].view(np.int32)
+                mem = wl.xyzt[f:f + c]
+                valid = mem[:, 3].astype(np.float64) < float(qp[3]) - lag
+                if not valid.any():
+                    assert math.isinf(lb[a, s])
+                    continue
+                dmin = min(oracle.d2(qp, p, SIG) for p in mem[valid])
+                assert lb[a, s] <= dmin * (1 - 2.0 ** -21), (a, s, lb[a, s], dmin)
+
+
+def test_medium_config_sampled_queries():
+    # 2,000 flights x 200 samples = 400,000 points, k = 32, 20-point segments
+    wl = synth.medium()
+    ix = _index(wl, 20)
+    ti, td, st = tnn.tnn_knn(ix, 32, 0.0, stats=True)
+    q = synth.query_sample(wl.n, 4096)
+    oi, od = oracle.knn(wl.xyzt, 32, SIG, qsel=q)
+    assert_knn_equal(ti.cpu().numpy()[q], td.cpu().numpy()[q], oi, od, what="tnn medium")
+    assert st["queries"] == wl.n
+    qd = torch.from_numpy(wl.xyzt[q]).cuda()
+    bi, bd = tnn.tnn_knn_bruteforce(ix, 32, 0.0, q=qd)
+    assert_knn_equal(bi.cpu().numpy(), bd.cpu().numpy(), oi, od, what="linear medium")
+    # invariants on every query: sorted by (d2, idx), unique, mask respected
+    ti = ti.cpu().numpy()
+    td = td.cpu().numpy()
+    assert (np.diff(td, axis=1) >= 0).all()
+    t = wl.xyzt[:, 3]
+    valid = ti >= 0
+    assert (t[np.where(valid, ti, 0)][valid] < np.repeat(t[:, None], 32, axis=1)[valid]).all()
+    srt = np.sort(ti, axis=1)
+    assert ((np.diff(srt, axis=1) != 0) | (srt[:, 1:] < 0)).all()
+
+
+def test_precision_config_sampled_queries():
+    # 20,000 flights x 200 samples = 4,000,000 points, k = 32
+    wl = synth.precision()
+    ix = _index(wl, 20)
+    ti, td, st = tnn.tnn_knn(ix, 32, 0.0, stats=True)
+    q = synth.query_sample(wl.n, 1024)
+    oi, od = oracle.knn(wl.xyzt, 32, SIG, qsel=q)
+    assert_knn_equal(ti.cpu().numpy()[q], td.cpu().numpy()[q], oi, od, what="tnn precision")
+    assert st["fallback_queries"] <= wl.n * 1e-4
+
+
+def test_batched_windows_match_oracle():
+    wins = synth.batched_windows(n_windows=9, lo=2e3, hi=3e4, seed=77)
+    idxs = [_index(wl, 20) for wl, _ in wins]
+    ks = [k for _, k in wins]
+    b = tnn.Batch(idxs, ks)
+    for _ in range(2):  # replaying the graph gives the same answer
+        b.run()
+    torch.cuda.synchronize()
+    st = b.stats()
+    assert st["queries"] == sum(wl.n for wl, _ in wins)
+    for w, (wl, k) in enumerate(wins):
+        q = synth.query_sample(wl.n, 300, seed=w)
+        oi, od = oracle.knn(wl.xyzt, k, SIG, qsel=q)
+        assert_knn_equal(b.idx[w].cpu().numpy()[q], b.d2[w].cpu().numpy()[q], oi, od,
+                         what=f"window {w} k={k}")
+
+
+def test_autotune_returns_valid_knobs():
+    wl = synth.flights(200, 100, seed=12, n_routes=8)
+    ix = _index(wl, 20)
+    p = tnn.tnn_autotune(ix, 32, 0.0, m_sample=1024)
+    assert 1 <= p["seed_segments"] <= 8 and 1 <= p["seed_window"] <= 256 and 2 <= p["extra"] <= 32
+    ti, td = tnn.tnn_knn(ix, 32, 0.0, **p)
+    q = synth.query_sample(wl.n, 500)
+    oi, od = oracle.knn(wl.xyzt, 32, SIG, qsel=q)
+    assert_knn_equal(ti.cpu().numpy()[q], td.cpu().numpy()[q], oi, od, what="autotuned")

@@ -1,0 +1,172 @@
+"""Parity of the nowcast kernels with the float64 oracle (features, IDW, MLP
+forward, gradient, AdamW), the checkpoint round trip, and what the trained
+MLP gains over the IDW fallback on held-out flights."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import nowcast as nc
+from paper_2112_10408_gb300 import synth
+from paper_2112_10408_gb300 import tnn
+
+pytestmark = pytest.mark.gpu
+SIG = synth.SIGMA_DEFAULT
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2112_10408_gb300 import build
+    build.build()
+    tnn.load_library()
+
+
+def _bf16_round(a):
+    return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+def test_features_and_idw_match_oracle():
+    wl = synth.flights(40, 60, seed=31, n_routes=4)
+    ix = tnn.tnn_build_segments(torch.from_numpy(wl.xyzt).cuda(), wl.traj_off, SIG, 10)
+    idx, d2 = tnn.tnn_knn(ix, 32, 30.0)
+    wind = torch.from_numpy(wl.wind).cuda()
+    mean = np.array([0.5, -1.0, 0.2, -3.0, 20.0, 5.0], np.float32)
+    std = np.array([10.0, 12.0, 2.0, 4.0, 8.0, 8.0], np.float32)
+    feat, idw = tnn.tnn_context_features(ix, wind, idx, d2, mean=mean, std=std)
+    torch.cuda.synchronize()
+    i_np, d_np = idx.cpu().numpy(), d2.cpu().numpy()
+    ref = nc.features(wl.xyzt, wl.wind, wl.xyzt, i_np, SIG, mean, std).reshape(wl.n, -1)
+    np.testing.assert_allclose(feat.float().cpu().numpy(), ref, rtol=1e-2, atol=1e-2)
+    ref_idw = nc.idw(d_np, i_np, wl.wind)
+    got = idw.cpu().numpy()
+    nan = np.isnan(ref_idw)
+    assert np.array_equal(np.isnan(got), nan)
+    np.testing.assert_allclose(got[~nan], ref_idw[~nan], rtol=1e-5, atol=1e-5)
+
+
+def _mlp_with_params(d_in, dh, seed=0):
+    m = tnn.MLP(d_in, dh, seed=seed)
+    rng = np.random.default_rng(seed)
+    w = rng.normal(0, 0.1, size=m.n_params).astype(np.float32)
+    m.set_params(w)
+    return m, w
+
+
+def test_mlp_forward_matches_oracle():
+    m, w = _mlp_with_params(192, 256)
+    W1, b1, W2, b2 = m.unflatten(w.astype(np.float64))
+    rng = np.random.default_rng(1)
+    X = rng.normal(0, 1, size=(777, 192)).astype(np.float32)
+    xb = torch.from_numpy(X).to(torch.bfloat16).cuda()
+    y = m.forward(xb).cpu().numpy()
+    _, _, Yr = nc.mlp_forward(_bf16_round(X), _bf16_round(W1), b1, W2, b2)
+    np.testing.assert_allclose(y, Yr, rtol=2e-2, atol=2e-2 * np.abs(Yr).max())
+
+
+def test_mlp_gradients_match_oracle():
+    m, w = _mlp_with_params(192, 256, seed=2)
+    W1, b1, W2, b2 = m.unflatten(w.astype(np.float64))
+    rng = np.random.default_rng(3)
+    B = 1000
+    X = rng.normal(0, 1, size=(B, 192)).astype(np.float32)
+    T = rng.normal(0, 1, size=(B, 2)).astype(np.float32)
+    loss, g = m.gradients(torch.from_numpy(X).to(torch.bfloat16).cuda(), torch.from_numpy(T).cuda())
+    g = g.cpu().numpy().astype(np.float64)
+    lr, gr = nc.mlp_grads(_bf16_round(X), T, _bf16_round(W1), b1, W2, b2)
+    assert float(loss.item()) == pytest.approx(lr, rel=2e-2)
+    gW1, gb1, gW2, gb2 = m.unflatten(g)
+    for name, got in (("W1", gW1), ("b1", gb1), ("W2", gW2), ("b2", gb2)):
+        ref = gr[name]
+        rel = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-12)
+        assert rel < 2e-2, (name, rel)
+
+
+def test_adamw_step_matches_oracle_update():
+    m, w = _mlp_with_params(64, 64, seed=4)
+    rng = np.random.default_rng(5)
+    X = torch.from_numpy(rng.normal(0, 1, size=(300, 64)).astype(np.float32)).to(torch.bfloat16).cuda()
+    T = torch.from_numpy(rng.normal(0, 1, size=(300, 2)).astype(np.float32)).cuda()
+    opt = tnn.AdamW(lr=3e-3, weight_decay=0.05)
+    wk = w.astype(np.float64)
+    mm = np.zeros_like(wk)
+    vv = np.zeros_like(wk)
+    for t in range(1, 4):
+        _, g = m.gradients(X, T)
+        g = g.cpu().numpy().astype(np.float64)
+        m.train_step(X, T, opt)
+        wk, mm, vv = nc.adamw_step(wk, g, mm, vv, t, lr=opt.lr, beta1=opt.beta1, beta2=opt.beta2,
+                                   eps=opt.eps, wd=opt.weight_decay)
+        got = m.get_params().astype(np.float64)
+        np.testing.assert_allclose(got, wk, rtol=1e-5, atol=1e-7)
+
+
+def test_checkpoint_round_trip(tmp_path):
+    m, _ = _mlp_with_params(64, 64, seed=6)
+    rng = np.random.default_rng(7)
+    X = torch.from_numpy(rng.normal(0, 1, size=(128, 64)).astype(np.float32)).to(torch.bfloat16).cuda()
+    T = torch.from_numpy(rng.normal(0, 1, size=(128, 2)).astype(np.float32)).cuda()
+    m.train_step(X, T, tnn.AdamW())
+    p = tmp_path / "mlp.bin"
+    m.save(str(p))
+    m2 = tnn.MLP(64, 64, seed=99)
+    m2.load(str(p))
+    a = m.get_params(with_moments=True)
+    b = m2.get_params(with_moments=True)
+    for x, y in zip(a[:3], b[:3]):
+        np.testing.assert_array_equal(x, y)
+    assert a[3] == b[3] == 1
+    m.train_step(X, T, tnn.AdamW())
+    m2.train_step(X, T, tnn.AdamW())
+    np.testing.assert_array_equal(m.get_params(), m2.get_params())
+
+
+def test_nowcast_entry_point_composes_the_stages():
+    wl = synth.flights(30, 60, seed=41, n_routes=3)
+    ix = tnn.tnn_build_segments(torch.from_numpy(wl.xyzt).cuda(), wl.traj_off, SIG, 10)
+    wind = torch.from_numpy(wl.wind).cuda()
+    uv = tnn.tnn_nowcast(ix, wind, 8, 20.0)
+    idx, d2 = tnn.tnn_knn(ix, 8, 20.0)
+    _, idw = tnn.tnn_context_features(ix, wind, idx, d2, want_feat=False)
+    torch.testing.assert_close(uv, idw, equal_nan=True)
+    m = tnn.MLP(48, 64, seed=1)
+    uvm = tnn.tnn_nowcast(ix, wind, 8, 20.0, mlp=m)
+    feat, _ = tnn.tnn_context_features(ix, wind, idx, d2, want_idw=False)
+    torch.testing.assert_close(uvm, m.forward(feat))
+
+
+def test_trained_mlp_beats_idw_on_held_out_flights():
+    # Learned form at reduced size: TNN contexts (k = 32, lag 1800 s) of
+    # 120,000 points, 80/20 split by flight, features standardised on the
+    # training split, AdamW, batch 4096.
+    wl = synth.flights(600, 200, seed=synth.SEED_LEARNED)
+    k, lag = 32, 1800.0
+    ix = tnn.tnn_build_segments(torch.from_numpy(wl.xyzt).cuda(), wl.traj_off, SIG, 20)
+    idx, d2 = tnn.tnn_knn(ix, k, lag)
+    wind = torch.from_numpy(wl.wind).cuda()
+    full = (idx >= 0).all(dim=1).cpu().numpy()
+    train, test = synth.flight_split(wl)
+    tr = np.nonzero(train & full)[0]
+    te = np.nonzero(test & full)[0]
+    assert tr.size > 20000 and te.size > 5000
+    raw, idw = tnn.tnn_context_features(ix, wind, idx, d2)
+    f = raw.float()[torch.from_numpy(tr).cuda()].view(-1, k, 6)
+    mean = f.mean(dim=(0, 1)).cpu().numpy()
+    std = f.std(dim=(0, 1)).cpu().numpy() + 1e-6
+    feat, _ = tnn.tnn_context_features(ix, wind, idx, d2, mean=mean, std=std, want_idw=False)
+    y = wind
+    mlp = tnn.MLP(k * 6, 256, seed=0)
+    opt = tnn.AdamW(lr=1e-3, weight_decay=1e-2)
+    rng = np.random.default_rng(0)
+    trd = torch.from_numpy(tr).cuda()
+    for epoch in range(12):
+        perm = trd[torch.from_numpy(rng.permutation(tr.size)).cuda()]
+        for b in range(0, perm.numel() - 4095, 4096):
+            sel = perm[b:b + 4096]
+            mlp.train_step(feat[sel].contiguous(), y[sel].contiguous(), opt)
+    ted = torch.from_numpy(te).cuda()
+    pred = mlp.forward(feat[ted].contiguous())
+    rmse_mlp = float(torch.sqrt(((pred - y[ted]) ** 2).mean()))
+    rmse_idw = float(torch.sqrt(((idw[ted] - y[ted]) ** 2).mean()))
+    print(f"held-out RMSE (m/s): MLP {rmse_mlp:.3f}  IDW {rmse_idw:.3f}")
+    assert rmse_mlp < rmse_idw
+    assert rmse_mlp > 0.9  # the noise floor is 1 m/s per component
