@@ -43,6 +43,8 @@ def _args():
     ap.add_argument("--comparator-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tuning", choices=["auto", "default"], default="auto",
+                    help="autotune the seed/extra knobs (auto) or use the library defaults")
     return ap.parse_args()
 
 
@@ -195,7 +197,7 @@ def run_ours(a):
     sigma = (1.0, 1.0, 10.0, 0.01)
     xyzt_d = torch.from_numpy(wl.xyzt).cuda()
     ix = tnn.tnn_build_segments(xyzt_d, wl.traj_off, sigma, K)
-    tune = tnn.tnn_autotune(ix, k, 0.0, m_sample=8192)
+    tune = tnn.tnn_autotune(ix, k, 0.0, m_sample=8192) if a.tuning == "auto" else {}
     m = wl.n
     idx = torch.empty((m, k), dtype=torch.int32, device="cuda")
     d2 = torch.empty((m, k), dtype=torch.float32, device="cuda")
@@ -291,7 +293,7 @@ def run_ours(a):
     h_d = torch.empty((m, k), dtype=torch.float32).pin_memory()
     d_x = torch.empty_like(xyzt_d)
     e2e_ms = []
-    for s in range(max(a.e2e_steps, 1) + 1):
+    for s in range(a.e2e_steps + 1 if a.e2e_steps > 0 else 0):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         d_x.copy_(h_x, non_blocking=True)
@@ -304,7 +306,7 @@ def run_ours(a):
         ix2.destroy()
         if s > 0:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e_avg = sum(e2e_ms) / len(e2e_ms)
+    e2e_avg = sum(e2e_ms) / len(e2e_ms) if e2e_ms else float("nan")
     e2e = {"value": world * m / (e2e_avg / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": int(h_x.numel() * 4), "d2h_bytes_per_step": int(m * k * 8),
            "ms_per_step": e2e_avg, "includes": "H2D points, tnn_build_segments, tnn_knn, D2H results"}

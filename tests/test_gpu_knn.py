@@ -246,7 +246,7 @@ def test_medium_config_sampled_queries():
     # invariants on every query: sorted by (d2, idx), unique, mask respected
     ti = ti.cpu().numpy()
     td = td.cpu().numpy()
-    assert (np.diff(td, axis=1) >= 0).all()
+    assert (td[:, 1:] >= td[:, :-1]).all()  # +inf padding compares equal
     t = wl.xyzt[:, 3]
     valid = ti >= 0
     assert (t[np.where(valid, ti, 0)][valid] < np.repeat(t[:, None], 32, axis=1)[valid]).all()
