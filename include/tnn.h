@@ -121,11 +121,13 @@ enum {
 typedef struct {
     int32_t k;             /* neighbours per query, 1..64                    */
     double lag;            /* t_w >= 0 (s): valid iff t_j < t_q - lag        */
-    int32_t seed_segments; /* F: segments scanned first, by lower bound,
-                              1..8 (0 = default 4)  (Algorithm 2, F)          */
-    int32_t seed_window;   /* most recent causal segments searched for those
-                              F (0 = default 64, max 256)                     */
-    int32_t extra;         /* candidate slots kept beyond k, 2..32 (0 = 8)   */
+    int32_t seed_segments; /* F: the F segments of smallest bound are scanned
+                              first (Algorithm 2 fetches F segments, nearest
+                              first), 1..6 (0 = default 4)                    */
+    int32_t seed_window;   /* at most this many of the most recent causal
+                              segments are searched for those F
+                              (0 = no limit, the default)                     */
+    int32_t extra;         /* candidate slots kept beyond k, 2..32 (0 = 4)   */
     int32_t flags;         /* TNN_FLAG_*                                      */
 } tnn_knn_params;
 

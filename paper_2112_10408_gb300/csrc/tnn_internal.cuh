@@ -87,8 +87,10 @@ struct KnnWin {
 struct KnnScratch {
     unsigned long long tile_counter;
     unsigned long long stats[8]; // queries, lb, pairs, segs, fp64, fallback
-    unsigned int n_fallback;
+    unsigned int n_fallback;  // queries handed to the FP32 warp scan
     unsigned int status;
+    unsigned int n_fallback3; // queries handed to the exact FP64 warp scan
+    unsigned int pad_;
 };
 
 struct KnnLaunch {
@@ -100,8 +102,9 @@ struct KnnLaunch {
     int32_t pad_;
     int64_t total_tiles;
     KnnScratch *scr;
-    int2 *fb_list;        // (window, query) needing the exact FP64 scan
-    int64_t fb_cap;
+    int2 *fb_list;        // (window, query) for the FP32 warp scan
+    int2 *fb_list3;       // (window, query) for the exact FP64 warp scan
+    int64_t fb_cap;       // capacity of each list
 };
 
 // Launch helpers (tnn_knn.cu).

@@ -57,8 +57,8 @@ def test_small_configs(k, lag, K):
     assert_knn_equal(bi, bd, oi, od, what=f"linear k={k} lag={lag} K={K}")
 
 
-@pytest.mark.parametrize("tuning", [dict(seed_segments=1, seed_window=1, extra=2),
-                                    dict(seed_segments=8, seed_window=256, extra=32),
+@pytest.mark.parametrize("tuning", [dict(seed_segments=1, seed_window=32, extra=2),
+                                    dict(seed_segments=6, seed_window=0, extra=32),
                                     dict(seed_segments=3, seed_window=17, extra=5)])
 def test_tuning_knobs_do_not_change_results(tuning):
     wl = synth.flights(60, 70, seed=7, n_routes=6)
@@ -286,7 +286,7 @@ def test_autotune_returns_valid_knobs():
     wl = synth.flights(200, 100, seed=12, n_routes=8)
     ix = _index(wl, 20)
     p = tnn.tnn_autotune(ix, 32, 0.0, m_sample=1024)
-    assert 1 <= p["seed_segments"] <= 8 and 1 <= p["seed_window"] <= 256 and 2 <= p["extra"] <= 32
+    assert 1 <= p["seed_segments"] <= 6 and p["seed_window"] >= 0 and 2 <= p["extra"] <= 32
     ti, td = tnn.tnn_knn(ix, 32, 0.0, **p)
     q = synth.query_sample(wl.n, 500)
     oi, od = oracle.knn(wl.xyzt, 32, SIG, qsel=q)
