@@ -174,6 +174,28 @@ tnn_status tnn_knn_bruteforce(const tnn_index *index, const float *d_q,
                               tnn_stream_t stream);
 
 /*
+ * tnn_knn for callers that cannot allocate device memory: a plugin whose
+ * host framework owns every device allocation, or a real-time loop that must
+ * not call an allocator that may block or fail under memory pressure.  (The
+ * paper has no counterpart: this is a deployment variant of tnn_knn.)
+ * Arguments and results as tnn_knn, without statistics.  It allocates
+ * nothing: its scratch -- work-queue counter, counters and the lists of
+ * queries handed to the fallback scans, 1 MiB + 256 B -- is a static array
+ * of this library in device memory, held by every GPU that loads the
+ * library until the process exits.
+ *  - At most 65,536 queries per call (TNN_ERR_INVALID_ARG beyond, before any
+ *    device work); answer more by calling it on slices of the queries.
+ *  - The first call on a device looks up the array's device address, with
+ *    that device current; make that first call before any stream capture.
+ *  - Every call uses the same array and clears its counters first: calls
+ *    whose work overlaps on the GPU (other streams, other threads) race and
+ *    corrupt each other's results.  Order them, e.g. on one stream.
+ */
+tnn_status tnn_knn_noalloc(const tnn_index *index, const float *d_q, int64_t m,
+                           const tnn_knn_params *params, int32_t *d_idx,
+                           float *d_d2, tnn_stream_t stream);
+
+/*
  * Lower bounds used by the search (Algorithm 1 with the cylinder reading of
  * the exclusion criterion of Sec. 3.4): d_lb [m][n_segments] float (device),
  * column j for the j-th segment of the t_A order; +inf where the segment

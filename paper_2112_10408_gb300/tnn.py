@@ -72,6 +72,7 @@ _SIGNATURES = [
                         ctypes.POINTER(tnn_stats), c_p]),
     ("tnn_knn_bruteforce", c_i32, [c_p, c_p, c_i64, ctypes.POINTER(tnn_knn_params), c_p, c_p,
                                    ctypes.POINTER(tnn_stats), c_p]),
+    ("tnn_knn_noalloc", c_i32, [c_p, c_p, c_i64, ctypes.POINTER(tnn_knn_params), c_p, c_p, c_p]),
     ("tnn_segment_lower_bounds", c_i32, [c_p, c_p, c_i64, c_f64, c_p, c_p]),
     ("tnn_knn_work", c_i32, [c_p, c_p, c_i64, c_i32, c_f64, c_p, c_p, c_p]),
     ("tnn_profile_enable", c_i32, [c_i32]),
