@@ -115,7 +115,12 @@ enum {
        separated from their rank neighbours report the FP32 distance, which is
        within 2^-20 relative of the FP64 value; the neighbour set and order
        are exact either way. */
-    TNN_FLAG_EXACT_D2 = 1
+    TNN_FLAG_EXACT_D2 = 1,
+    /* Visit the segments by walking the t_A order backwards (the sweep)
+       instead of through the time-bucketed spatial grid of the index.  Both
+       give the same exact result; the grid skips whole groups of segments
+       and is the default. */
+    TNN_FLAG_SWEEP = 2
 };
 
 typedef struct {
@@ -129,6 +134,12 @@ typedef struct {
                               (0 = no limit, the default)                     */
     int32_t extra;         /* candidate slots kept beyond k, 2..32 (0 = 4)   */
     int32_t flags;         /* TNN_FLAG_*                                      */
+    float defer_cells;     /* grid order: a query whose k-th candidate after
+                              seeding is farther than defer_cells grid cells
+                              leaves its shared 32-query tile and is finished
+                              by a warp of its own (Algorithm 2 puts finished
+                              lines aside; here the slow ones are) -- 0 =
+                              default 1.5, < 0 = never                       */
 } tnn_knn_params;
 
 typedef struct {
@@ -138,7 +149,8 @@ typedef struct {
                                   Table 3)                                   */
     uint64_t segs_scanned;     /* (query, segment) scans                     */
     uint64_t fp64_rechecks;    /* distances recomputed in FP64               */
-    uint64_t fallback_queries; /* queries finished by the exact FP64 scan    */
+    uint64_t warp_queries;     /* queries finished by a warp of their own    */
+    uint64_t exact_queries;    /* queries ranked by the FP64 definition      */
 } tnn_stats;
 
 /*

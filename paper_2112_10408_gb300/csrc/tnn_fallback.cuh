@@ -1,25 +1,32 @@
-// Queries whose ranking the search could not settle (the chain of FP32 keys
-// that FP32 cannot order reaches the last candidate slot kept) are answered
-// again here, one warp per query:
+// Queries answered one warp per query.  Two kinds arrive here:
+//   - deferred: in the lane-per-query kernel their pruning key after seeding
+//     was too large for a shared tile (e.g. a flight's first samples, whose
+//     neighbours are far away); Algorithm 2 puts such unfinished lines
+//     aside and carries on with the others -- they are finished here, where
+//     the whole warp works on one query;
+//   - unsettled: the chain of FP32 keys that FP32 cannot order reached the
+//     last candidate slot.  Here the list keeps k + 32 candidates.
 //
-//   k_fallback_scan   every causally valid point (time-ordered copy, newest
-//                     first, lanes interleaved) in FP32 with a candidate list
-//                     of k + 32 per lane; a lane stops once the temporal part
-//                     alone exceeds its list's largest key; the 32 lists are
-//                     merged and settled exactly like the search.  A query
-//                     whose near-tie chain still reaches the end of the
-//                     merged list moves on to
-//   k_fallback_exact  the definition itself: the FP64 distance of every
-//                     valid point, ranked by (d2, index).
+// k_tnn_warp: the 32 lanes split the grid keys, the member segments and the
+// member points of one query.  Candidates below the pruning key are sorted
+// across the warp (bitonic) and merged into a sorted list in shared memory
+// (merge path).  Seeding visits cubes of keys of growing radius around the
+// query's own key (cells in the plane, buckets backwards in time) and scans
+// every point in them until the list is full; the main phase is the
+// exclusion criterion and stop rule of Algorithm 2 over the remaining keys.
+// A query still unsettled goes to k_fallback_exact: the FP64 definition.
 #pragma once
 #include "tnn_device.cuh"
+#include "tnn_grid.cuh"
 
 #define FB_EXTRA 32
+#define WQ_CMAX (64 + FB_EXTRA)
 
-__host__ __device__ inline size_t fb_scan_smem_per_warp(int k_max)
+__host__ __device__ inline size_t wq_smem_per_warp()
 {
-    const size_t C = (size_t)k_max + FB_EXTRA;
-    return C * 32 * 8 + C * 8 + (size_t)CMAX * 32 * 12;
+    // list [WQ_CMAX] + merge output [WQ_CMAX] + batch [32] (u64), and the
+    // settlement scratch ([CMAX][32] u64 + [CMAX][32] int) after them
+    return (size_t)(2 * WQ_CMAX + 32) * 8 + (size_t)CMAX * 32 * 12;
 }
 
 __host__ __device__ inline size_t fb_exact_smem_per_warp(int k_max)
@@ -27,29 +34,85 @@ __host__ __device__ inline size_t fb_exact_smem_per_warp(int k_max)
     return (size_t)k_max * 32 * 12;
 }
 
-// Warp minimum of 64-bit keys.
-__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
+__device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int m)
 {
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long w = __shfl_xor_sync(FULLMASK, v, o);
-        v = w < v ? w : v;
+    return __shfl_xor_sync(FULLMASK, v, m);
+}
+
+// Ascending bitonic sort of one key per lane across the warp.
+__device__ __forceinline__ unsigned long long warp_sort_u64(unsigned long long v, int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const unsigned long long o = shfl_xor_u64(v, j);
+            const bool up = (lane & k) == 0;
+            const bool lower = (lane & j) == 0;
+            const unsigned long long mn = o < v ? o : v, mx = o < v ? v : o;
+            v = (lower == up) ? mn : mx;
+        }
     }
     return v;
 }
 
+struct WarpList {
+    unsigned long long *L;   // [C] sorted keys, SENT beyond nv
+    unsigned long long *tmp; // [C]
+    unsigned long long *B;   // [32]
+    int C, nv;
+    unsigned long long tauk; // largest key kept once full, else SENT
+};
+
+// Merge the keys below the pruning key (at most one per lane) into the list.
+__device__ __forceinline__ void wl_merge(WarpList &w, unsigned long long ck, int lane)
+{
+    const bool take = ck < w.tauk;
+    const unsigned m = __ballot_sync(FULLMASK, take);
+    if (!m)
+        return;
+    const int nb = __popc(m);
+    const unsigned long long v = warp_sort_u64(take ? ck : SENT, lane);
+    w.B[lane] = v;
+    __syncwarp();
+    const int na = w.nv;
+    for (int p = lane; p < w.C; p += 32) {
+        int lo = max(0, p - nb), hi = min(p, na);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (w.L[mid] < w.B[p - mid - 1])
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        const int i = lo, j = p - lo;
+        unsigned long long out = SENT;
+        if (i < na && (j >= nb || w.L[i] < w.B[j]))
+            out = w.L[i];
+        else if (j < nb)
+            out = w.B[j];
+        w.tmp[p] = out;
+    }
+    __syncwarp();
+    for (int p = lane; p < w.C; p += 32)
+        w.L[p] = w.tmp[p];
+    __syncwarp();
+    w.nv = min(na + nb, w.C);
+    w.tauk = w.nv == w.C ? w.L[w.C - 1] : SENT;
+}
+
 __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
-    k_fallback_scan(const __grid_constant__ KnnLaunch L)
+    k_tnn_warp(const __grid_constant__ KnnLaunch L)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
-    const int kmax = L.L_max;
-    const int Cmax = kmax + FB_EXTRA;
-    unsigned char *ws = smem + (threadIdx.x >> 5) * fb_scan_smem_per_warp(kmax);
-    unsigned long long *K = (unsigned long long *)ws + lane;          // [Cmax][32]
-    unsigned long long *merged = (unsigned long long *)ws + (size_t)Cmax * 32; // [Cmax]
-    unsigned char *cl = ws + (size_t)Cmax * 32 * 8 + (size_t)Cmax * 8;
-    unsigned long long *cl_d = (unsigned long long *)cl; // lane 0's columns
-    int *cl_i = (int *)(cl + CMAX * 32 * 8);
+    unsigned char *ws = smem + (threadIdx.x >> 5) * wq_smem_per_warp();
+    WarpList wl;
+    wl.L = (unsigned long long *)ws;
+    wl.tmp = wl.L + WQ_CMAX;
+    wl.B = wl.tmp + WQ_CMAX;
+    unsigned long long *cl_d = (unsigned long long *)(ws + (size_t)(2 * WQ_CMAX + 32) * 8);
+    int *cl_i = (int *)((unsigned char *)cl_d + CMAX * 32 * 8);
 
     unsigned nfb = *(volatile unsigned *)&L.scr->n_fallback;
     if ((long long)nfb > L.fb_cap)
@@ -63,47 +126,141 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
         const float4 q = W->q[ent.y];
         const QCtx c = make_qctx(W, q, true);
         const float s0 = W->sig[0], s1 = W->sig[1], s2 = W->sig[2], s3 = W->sig[3];
-        const float4 *__restrict__ pts_t = W->pts_t;
-        const int32_t *__restrict__ idx_t = W->idx_t;
-        const int C = W->k + FB_EXTRA;
-        for (int i = 0; i < C; ++i)
-            K[i * 32] = SENT;
-        int nv = 0;
-        unsigned long long tauk = SENT;
-        float tau = INFINITY;
-        const int hi = warp_count_less([&](int p) { return __ldg(&pts_t[p].w); }, W->n, c.T32, lane);
-        for (int base = hi - 1; base >= 0; base -= 32) {
-            const float tb = __ldg(&pts_t[base].w); // newest remaining time
-            if (__all_sync(FULLMASK, !(time_lb(c, s3, tb) <= tau)))
-                break;
-            const int j = base - lane;
-            if (j >= 0) {
-                const float4 p = __ldg(pts_t + j);
-                const float d = dist32(c, s0, s1, s2, s3, p);
-                st.pairs++;
-                if (p.w < c.T32 && d <= tau) {
-                    const unsigned long long key = pack_key(d, __ldg(idx_t + j));
-                    if (key < tauk) {
-                        tauk = lane_push(K, C, nv, key);
-                        tau = key_d(tauk);
+        const float4 *__restrict__ seg = W->seg;
+        const float4 *__restrict__ pts = W->pts;
+        const GridDesc &G = W->grid;
+        wl.C = W->k + FB_EXTRA;
+        wl.nv = 0;
+        wl.tauk = SENT;
+        for (int p = lane; p < wl.C; p += 32)
+            wl.L[p] = SENT;
+        __syncwarp();
+
+        // all points of one segment, 32 at a time
+        auto scan_seg = [&](int first, int cnt) {
+            st.segs++;
+            for (int o = 0; o < cnt; o += 32) {
+                const int j = o + lane;
+                unsigned long long ck = SENT;
+                if (j < cnt) {
+                    const float4 p = __ldg(pts + first + j);
+                    const float d = dist32(c, s0, s1, s2, s3, p);
+                    if (p.w < c.T32)
+                        ck = pack_key(d, first + j);
+                    st.pairs++;
+                }
+                wl_merge(wl, ck, lane);
+            }
+        };
+        // the member segments of one key: all of them (seeding) or those whose
+        // cylinder bound does not exceed the pruning key
+        auto visit_key = [&](int key, bool all) {
+            const int lo = __ldg(G.off + key), hi = __ldg(G.off + key + 1);
+            for (int base = lo; base < hi; base += 32) {
+                const int i = base + lane;
+                bool need = false;
+                float4 meta = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (i < hi) {
+                    const float4 *src = seg + 4 * (size_t)__ldg(G.ids + i);
+                    meta = __ldg(src + 3);
+                    if (all) {
+                        need = true;
+                    } else {
+                        const float lb = seg_lb(c, s3, __ldg(src), __ldg(src + 1), __ldg(src + 2));
+                        st.lb++;
+                        need = lb <= key_d(wl.tauk);
+                    }
+                }
+                unsigned m = __ballot_sync(FULLMASK, need);
+                while (m) {
+                    const int j = __ffs(m) - 1;
+                    m &= m - 1;
+                    scan_seg(__float_as_int(__shfl_sync(FULLMASK, meta.x, j)),
+                             __float_as_int(__shfl_sync(FULLMASK, meta.y, j)));
+                }
+            }
+        };
+
+        int bhi = -1;
+        {
+            const float fb = (c.T32 - G.t0) * G.inv_dt;
+            if (fb >= 0.0f)
+                bhi = (int)fminf(floorf(fb), (float)(G.nb - 1));
+        }
+        if (bhi >= 0) {
+            const int hx = min(max((int)floorf((c.sx - G.x0) * G.inv_cell), 0), G.nx - 1);
+            const int hy = min(max((int)floorf((c.sy - G.y0) * G.inv_cell), 0), G.ny - 1);
+            const int rcover = max(max(max(hx, G.nx - 1 - hx), max(hy, G.ny - 1 - hy)), bhi);
+            // ---- seeding: cubes of keys of growing radius, every point
+            int rs = -1;
+            while (wl.nv < wl.C && rs < rcover) {
+                const int r = ++rs;
+                const int side = 2 * r + 1, nk = side * side * (r + 1);
+                for (int t0 = 0; t0 < nk; t0 += 32) {
+                    const int t = t0 + lane;
+                    int key = -1;
+                    if (t < nk) {
+                        const int db = t / (side * side), rem = t % (side * side);
+                        const int dy = rem / side - r, dx = rem % side - r;
+                        const int b = bhi - db, cx = hx + dx, cy = hy + dy;
+                        const bool shell = max(max(abs(dx), abs(dy)), db) == r;
+                        if (shell && b >= 0 && cx >= 0 && cx < G.nx && cy >= 0 && cy < G.ny) {
+                            const int k2 = b * G.ncell + cy * G.nx + cx;
+                            if (__ldg(G.off + k2 + 1) > __ldg(G.off + k2))
+                                key = k2;
+                        }
+                    }
+                    unsigned m = __ballot_sync(FULLMASK, key >= 0);
+                    while (m) {
+                        const int j = __ffs(m) - 1;
+                        m &= m - 1;
+                        visit_key(__shfl_sync(FULLMASK, key, j), true);
+                    }
+                }
+            }
+            // ---- main: buckets backwards, keys within reach, by bound
+            if (rs < rcover) {
+                for (int b = bhi; b >= 0; --b) {
+                    const float tau = key_d(wl.tauk);
+                    if (!(time_lb(c, s3, __ldg(G.bpm + b)) <= tau))
+                        break;
+                    const float R = sqrtf(tau) * (1.0f + 0x1p-18f) + G.ext_max + c.delta;
+                    const int cx0 = max((int)floorf(fmaxf((c.sx - R - G.x0) * G.inv_cell, -1.0f)) - 1, 0);
+                    const int cx1 = min((int)floorf(fminf((c.sx + R - G.x0) * G.inv_cell, (float)G.nx)) + 1, G.nx - 1);
+                    const int cy0 = max((int)floorf(fmaxf((c.sy - R - G.y0) * G.inv_cell, -1.0f)) - 1, 0);
+                    const int cy1 = min((int)floorf(fminf((c.sy + R - G.y0) * G.inv_cell, (float)G.ny)) + 1, G.ny - 1);
+                    const int wx = cx1 - cx0 + 1, nk = wx * (cy1 - cy0 + 1);
+                    const bool bseed = bhi - b <= rs;
+                    for (int t0 = 0; t0 < nk; t0 += 32) {
+                        const int t = t0 + lane;
+                        int key = -1;
+                        if (t < nk) {
+                            const int cx = cx0 + t % wx, cy = cy0 + t / wx;
+                            const bool seeded = bseed && abs(cx - hx) <= rs && abs(cy - hy) <= rs;
+                            if (!seeded) {
+                                const int k2 = b * G.ncell + cy * G.nx + cx;
+                                if (__ldg(G.off + k2 + 1) > __ldg(G.off + k2)) {
+                                    const float rx0 = G.x0 + (float)cx * G.cell;
+                                    const float ry0 = G.y0 + (float)cy * G.cell;
+                                    if (cell_lb(c, s3, rx0, rx0 + G.cell, ry0, ry0 + G.cell,
+                                                __ldg(G.ext + k2), __ldg(G.tB + k2)) <= key_d(wl.tauk))
+                                        key = k2;
+                                }
+                            }
+                        }
+                        unsigned m = __ballot_sync(FULLMASK, key >= 0);
+                        while (m) {
+                            const int j = __ffs(m) - 1;
+                            m &= m - 1;
+                            visit_key(__shfl_sync(FULLMASK, key, j), false);
+                        }
                     }
                 }
             }
         }
-        // merge the 32 sorted lists into the C smallest keys
-        int h = 0;
-        for (int r = 0; r < C; ++r) {
-            const unsigned long long v = h < nv ? K[h * 32] : SENT;
-            const unsigned long long mn = warp_min_u64(v);
-            if (lane == 0)
-                merged[r] = mn;
-            if (v == mn && mn != SENT)
-                ++h;
-        }
         __syncwarp();
         if (lane == 0) {
-            st.q++;
-            if (!finalize_query(W, q, merged, C, cl_d, cl_i, ent.y, st, 1)) {
+            if (!finalize_query(W, q, wl.L, wl.C, cl_d, cl_i, ent.y, st, 1)) {
                 const unsigned slot = atomicAdd(&L.scr->n_fallback3, 1u);
                 if (slot < (unsigned long long)L.fb_cap)
                     L.fb_list3[slot] = ent;
@@ -113,15 +270,15 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
         }
         __syncwarp();
     }
-    unsigned long long x = st.pairs, f = st.fp64;
-    for (int o = 16; o > 0; o >>= 1) {
-        x += __shfl_xor_sync(FULLMASK, x, o);
-        f += __shfl_xor_sync(FULLMASK, f, o);
+    unsigned long long v[4] = {st.lb, st.pairs, st.segs, st.fp64};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        unsigned long long x = v[i];
+        for (int o = 16; o > 0; o >>= 1)
+            x += __shfl_xor_sync(FULLMASK, x, o);
+        if (lane == 0 && x)
+            atomicAdd(&L.scr->stats[1 + i], x);
     }
-    if (lane == 0 && x)
-        atomicAdd(&L.scr->stats[2], x);
-    if (lane == 0 && f)
-        atomicAdd(&L.scr->stats[4], f);
     if (blockIdx.x == 0 && threadIdx.x == 0)
         L.scr->stats[5] = nfb;
 }
@@ -178,13 +335,13 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
             if (cnt < k)
                 ++cnt;
         }
-        // merge by (d2, index)
+        // merge the 32 lists by (d2, index)
         int h = 0;
         int32_t *oi = W->out_idx + (int64_t)ent.y * k;
         float *od = W->out_d2 + (int64_t)ent.y * k;
         for (int r = 0; r < k; ++r) {
-            unsigned long long vd = h < cnt ? kd[h * 32] : INF64;
-            int vi = h < cnt ? ki[h * 32] : 0x7fffffff;
+            const unsigned long long vd = h < cnt ? kd[h * 32] : INF64;
+            const int vi = h < cnt ? ki[h * 32] : 0x7fffffff;
             unsigned long long md = vd;
             int mi = vi;
             for (int o = 16; o > 0; o >>= 1) {
@@ -210,4 +367,6 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
         x += __shfl_xor_sync(FULLMASK, x, o);
     if (lane == 0 && x)
         atomicAdd(&L.scr->stats[4], x);
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        L.scr->stats[6] = nfb;
 }

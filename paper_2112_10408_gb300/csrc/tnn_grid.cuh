@@ -1,0 +1,360 @@
+// TNN search over the time-bucketed spatial grid of the index.
+//
+// Same tiles, candidate lists, seeds and settlement as the sweep kernel
+// (tnn_search.cuh); only the order in which segments are considered
+// changes.  A key of the grid (bucket of t_A, cell of the midpoint) has its
+// own lower bound -- distance from the query to the cell rectangle minus the
+// key's extent, plus the temporal part from the key's largest t_B -- which
+// never exceeds the cylinder bound of any member segment, so whole keys are
+// excluded at once by the exclusion criterion of Sec. 3.4.
+//
+//   seeds   the 3 x 3 cells around the warp in the two most recent buckets:
+//           every lane keeps its F smallest cylinder bounds there; the union
+//           of those segments is scanned first (Algorithm 2's first fetch).
+//   main    buckets from the causal end backwards; a bucket is visited while
+//           the temporal bound of its running maximum of t_B does not exceed
+//           some lane's pruning key (Algorithm 2's stop rule); inside it, the
+//           cells within reach of the warp's queries, and inside a cell whose
+//           bound does not exceed a lane's key, the member segments whose
+//           cylinder bound does not exceed it are scanned for that lane.
+#pragma once
+#include "tnn_device.cuh"
+
+#define TNN_GMAX_F 6
+
+// Lower bound on the cylinder bound (and so on the FP32 distance of any
+// valid member) of every segment of one key.
+__device__ __forceinline__ float cell_lb(const QCtx &c, float st, float rx0, float rx1,
+                                         float ry0, float ry1, float ext, float tBk)
+{
+    const float dx = fmaxf(fmaxf(rx0 - c.sx, c.sx - rx1), 0.0f);
+    const float dy = fmaxf(fmaxf(ry0 - c.sy, c.sy - ry1), 0.0f);
+    const float a2 = fmaf(dy, dy, dx * dx);
+    const float dist = a2 * rsqrtf(fmaxf(a2, 1e-37f));
+    const float sp = fmaxf(fmaf(dist, 1.0f - 0x1p-20f, -(ext + c.delta)), 0.0f);
+    const float et = fmaxf(__fsub_rd(c.qt, fminf(tBk, c.T32)), 0.0f);
+    return fmaf(sp, sp, (st * et) * et) * (1.0f - 0x1p-19f);
+}
+
+__device__ __forceinline__ float warp_minf(float v)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        v = fminf(v, __shfl_xor_sync(FULLMASK, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_maxf(float v)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        v = fmaxf(v, __shfl_xor_sync(FULLMASK, v, o));
+    return v;
+}
+
+#ifndef TNN_GRID_MINB
+#define TNN_GRID_MINB 3
+#endif
+
+__global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_GRID_MINB)
+    k_tnn_grid_search(const __grid_constant__ KnnLaunch L)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const size_t pw = smem_per_warp(L.L_max, L.kseg_max, false);
+    unsigned char *ws = smem + (threadIdx.x >> 5) * pw;
+    unsigned long long *K = (unsigned long long *)ws + lane;
+    unsigned char *rest = ws + (size_t)L.L_max * 256;
+    float4 *segbuf = (float4 *)rest;                     // [32][4]
+    float4 *pbuf = (float4 *)(rest + 2048);              // [kseg_max]
+    int *ulist = (int *)(rest + 2048 + 16 * L.kseg_max); // [TNN_UCAP] seeds
+    unsigned long long *cl_d = (unsigned long long *)rest + lane;
+    int *cl_i = (int *)(rest + CMAX * 32 * 8) + lane;
+
+    LaneStats st = {0, 0, 0, 0, 0};
+    for (;;) {
+        long long tile = 0;
+        if (lane == 0)
+            tile = (long long)atomicAdd(&L.scr->tile_counter, 1ull);
+        tile = __shfl_sync(FULLMASK, tile, 0);
+        if (tile >= L.total_tiles)
+            break;
+        const KnnWin *W = find_window(L, tile);
+        const int64_t qrow = (tile - W->tile_begin) * 32 + lane;
+        const bool active = qrow < W->m;
+        const float4 q = active ? W->q[qrow] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const QCtx c = make_qctx(W, q, active);
+        const float s0 = W->sig[0], s1 = W->sig[1], s2 = W->sig[2], s3 = W->sig[3];
+        const float4 *__restrict__ seg = W->seg;
+        const float4 *__restrict__ pts = W->pts;
+        const GridDesc &G = W->grid;
+        const int32_t *__restrict__ goff = G.off;
+        const int32_t *__restrict__ gids = G.ids;
+        const int Lw = W->L, F = W->F;
+
+        const float tmax = warp_maxf(c.T32);
+        const float bx0 = warp_minf(active ? c.sx : INFINITY);
+        const float bx1 = warp_maxf(active ? c.sx : -INFINITY);
+        const float by0 = warp_minf(active ? c.sy : INFINITY);
+        const float by1 = warp_maxf(active ? c.sy : -INFINITY);
+        const float dmax = warp_maxf(active ? c.delta : 0.0f);
+        int bhi = -1;
+        {
+            const float fb = (tmax - G.t0) * G.inv_dt;
+            if (fb >= 0.0f)
+                bhi = (int)fminf(floorf(fb), (float)(G.nb - 1));
+        }
+
+        for (int i = 0; i < Lw; ++i)
+            K[i * 32] = SENT;
+        int nv = 0;
+        unsigned long long tauk = SENT;
+        float tau = INFINITY;
+        bool done = !active;
+
+        auto scan_pbuf = [&](int first, int cnt, bool need) {
+            if (!need)
+                return;
+            st.segs++;
+            st.pairs += cnt;
+            for (int j = 0; j < cnt; ++j) {
+                const float4 p = pbuf[j];
+                const float d = dist32(c, s0, s1, s2, s3, p);
+                if (p.w < c.T32 && d <= tau) {
+                    const unsigned long long key = pack_key(d, first + j);
+                    if (key < tauk) {
+                        tauk = lane_push(K, Lw, nv, key);
+                        tau = key_d(tauk);
+                    }
+                }
+            }
+        };
+        auto scan_chunk = [&](unsigned any, unsigned need) {
+            if (!any)
+                return;
+            SegPoints cur, nxt;
+            int i = 31 - __clz(any);
+            any &= ~(1u << i);
+            seg_points_load(cur, pts, segbuf[4 * i + 3], lane);
+            for (;;) {
+                int inx = -1;
+                if (any) {
+                    inx = 31 - __clz(any);
+                    any &= ~(1u << inx);
+                    seg_points_load(nxt, pts, segbuf[4 * inx + 3], lane);
+                }
+                __syncwarp();
+                seg_points_store(cur, pbuf, lane);
+                __syncwarp();
+                scan_pbuf(cur.first, cur.cnt, (need >> i) & 1u);
+                if (inx < 0)
+                    break;
+                cur = nxt;
+                i = inx;
+            }
+        };
+
+        float bl[TNN_GMAX_F];
+        int bp[TNN_GMAX_F];
+#pragma unroll
+        for (int f = 0; f < TNN_GMAX_F; ++f) {
+            bl[f] = INFINITY;
+            bp[f] = -1;
+        }
+        float wF = INFINITY;
+        int nu = 0;
+
+        // Consider the member segments ids[lo, hi) of one key: seed mode keeps
+        // the F smallest bounds, main mode scans where the bound allows.
+        auto visit = [&](int lo, int hi, bool seed_mode) {
+            for (int base = lo; base < hi; base += 32) {
+                const int cnt = min(32, hi - base);
+                __syncwarp();
+                int mypos = -1;
+                if (lane < cnt) {
+                    mypos = __ldg(gids + base + lane);
+                    const float4 *src = seg + 4 * (size_t)mypos;
+                    segbuf[4 * lane] = __ldg(src);
+                    segbuf[4 * lane + 1] = __ldg(src + 1);
+                    segbuf[4 * lane + 2] = __ldg(src + 2);
+                    segbuf[4 * lane + 3] = __ldg(src + 3);
+                }
+                __syncwarp();
+                if (seed_mode) {
+                    for (int i = 0; i < cnt; ++i) {
+                        const int pos = __shfl_sync(FULLMASK, mypos, i);
+                        const float lb = seg_lb(c, s3, segbuf[4 * i], segbuf[4 * i + 1],
+                                                segbuf[4 * i + 2]);
+                        if (active && lb < wF) {
+                            float cur = lb;
+                            int cp = pos;
+#pragma unroll
+                            for (int f = 0; f < TNN_GMAX_F; ++f) {
+                                if (f < F && cur < bl[f]) {
+                                    const float tf = bl[f];
+                                    bl[f] = cur;
+                                    cur = tf;
+                                    const int tp = bp[f];
+                                    bp[f] = cp;
+                                    cp = tp;
+                                }
+                            }
+#pragma unroll
+                            for (int f = 0; f < TNN_GMAX_F; ++f)
+                                if (f == F - 1)
+                                    wF = bl[f];
+                        }
+                    }
+                    if (active)
+                        st.lb += cnt;
+                } else {
+                    bool sd = false;
+                    if (lane < cnt)
+                        for (int u = 0; u < nu; ++u)
+                            sd |= ulist[u] == mypos;
+                    const unsigned smask = __ballot_sync(FULLMASK, sd);
+                    unsigned need = 0;
+                    if (!done) {
+#pragma unroll 4
+                        for (int i = 0; i < cnt; ++i) {
+                            const float lb = seg_lb(c, s3, segbuf[4 * i], segbuf[4 * i + 1],
+                                                    segbuf[4 * i + 2]);
+                            if (lb <= tau)
+                                need |= 1u << i;
+                        }
+                        need &= ~smask;
+                        st.lb += cnt;
+                    }
+                    scan_chunk(__reduce_or_sync(FULLMASK, need), need);
+                }
+            }
+        };
+
+        // ---- seeds: 3 x 3 cells around the warp, two most recent buckets
+        if (bhi >= 0) {
+            const int hx = min(max((int)floorf((0.5f * (bx0 + bx1) - G.x0) * G.inv_cell), 0), G.nx - 1);
+            const int hy = min(max((int)floorf((0.5f * (by0 + by1) - G.y0) * G.inv_cell), 0), G.ny - 1);
+            for (int b = bhi; b >= 0 && b >= bhi - 1; --b) {
+                const int cx = hx + lane % 3 - 1, cy = hy + lane / 3 - 1;
+                const bool ok = lane < 9 && cx >= 0 && cx < G.nx && cy >= 0 && cy < G.ny;
+                int lo = 0, hi = 0;
+                if (ok) {
+                    const int key = b * G.ncell + cy * G.nx + cx;
+                    lo = __ldg(goff + key);
+                    hi = __ldg(goff + key + 1);
+                }
+                unsigned m = __ballot_sync(FULLMASK, hi > lo);
+                while (m) {
+                    const int j = __ffs(m) - 1;
+                    m &= m - 1;
+                    visit(__shfl_sync(FULLMASK, lo, j), __shfl_sync(FULLMASK, hi, j), true);
+                }
+            }
+        }
+
+        // ---- scan the union of the seeds (highest position first)
+        {
+            auto next_seed = [&]() {
+                int mm = -1;
+#pragma unroll
+                for (int f = 0; f < TNN_GMAX_F; ++f)
+                    mm = max(mm, bp[f]);
+                return __reduce_max_sync(FULLMASK, mm);
+            };
+            int pos = next_seed();
+            SegPoints cur, nxt;
+            if (pos >= 0)
+                seg_points_load(cur, pts, __ldg(seg + 4 * (size_t)pos + 3), lane);
+            while (pos >= 0 && nu < TNN_UCAP) {
+#pragma unroll
+                for (int f = 0; f < TNN_GMAX_F; ++f)
+                    if (bp[f] == pos)
+                        bp[f] = -1;
+                if (lane == 0)
+                    ulist[nu] = pos;
+                ++nu;
+                const int npos = nu < TNN_UCAP ? next_seed() : -1;
+                if (npos >= 0)
+                    seg_points_load(nxt, pts, __ldg(seg + 4 * (size_t)npos + 3), lane);
+                __syncwarp();
+                seg_points_store(cur, pbuf, lane);
+                __syncwarp();
+                scan_pbuf(cur.first, cur.cnt, active);
+                cur = nxt;
+                pos = npos;
+            }
+        }
+        __syncwarp();
+
+        // ---- a lane whose key is still above the deferral threshold (far
+        // neighbours, or a list not yet full) would make the whole tile visit
+        // a wide region: it is handed to the warp-per-query kernel instead
+        const bool deferred = active && !(tau <= W->tau_defer);
+        if (deferred) {
+            const unsigned slot = atomicAdd(&L.scr->n_fallback, 1u);
+            if (slot < (unsigned long long)L.fb_cap)
+                L.fb_list[slot] = make_int2(window_id(L, W), (int)qrow);
+            else
+                atomicOr(&L.scr->status, 1u);
+        }
+
+        // ---- main: buckets backwards, cells within reach, keys by bound
+        for (int b = bhi; b >= 0; --b) {
+            done = !active || deferred || !(time_lb(c, s3, __ldg(G.bpm + b)) <= tau);
+            if (__all_sync(FULLMASK, done))
+                break;
+            const float tmx = warp_maxf(done ? 0.0f : tau);
+            int cx0 = 0, cx1 = G.nx - 1, cy0 = 0, cy1 = G.ny - 1;
+            if (tmx < INFINITY) {
+                // any key outside this reach has a bound above every key
+                const float R = sqrtf(tmx) * (1.0f + 0x1p-18f) + G.ext_max + dmax;
+                cx0 = max((int)floorf(fmaxf((bx0 - R - G.x0) * G.inv_cell, -1.0f)) - 1, 0);
+                cx1 = min((int)floorf(fminf((bx1 + R - G.x0) * G.inv_cell, (float)G.nx)) + 1, G.nx - 1);
+                cy0 = max((int)floorf(fmaxf((by0 - R - G.y0) * G.inv_cell, -1.0f)) - 1, 0);
+                cy1 = min((int)floorf(fminf((by1 + R - G.y0) * G.inv_cell, (float)G.ny)) + 1, G.ny - 1);
+            }
+            const int kb = b * G.ncell;
+            for (int cy = cy0; cy <= cy1; ++cy) {
+                const float ry0 = G.y0 + (float)cy * G.cell, ry1 = ry0 + G.cell;
+                for (int cxb = cx0; cxb <= cx1; cxb += 32) {
+                    const int cx = cxb + lane;
+                    int lo = 0, hi = 0;
+                    float ex = 0.f, tk = 0.f;
+                    if (cx <= cx1) {
+                        const int key = kb + cy * G.nx + cx;
+                        lo = __ldg(goff + key);
+                        hi = __ldg(goff + key + 1);
+                        ex = __ldg(G.ext + key);
+                        tk = __ldg(G.tB + key);
+                    }
+                    unsigned m = __ballot_sync(FULLMASK, hi > lo);
+                    while (m) {
+                        const int j = __ffs(m) - 1;
+                        m &= m - 1;
+                        const int jlo = __shfl_sync(FULLMASK, lo, j);
+                        const int jhi = __shfl_sync(FULLMASK, hi, j);
+                        const float jex = __shfl_sync(FULLMASK, ex, j);
+                        const float jtk = __shfl_sync(FULLMASK, tk, j);
+                        const float rx0 = G.x0 + (float)(cxb + j) * G.cell, rx1 = rx0 + G.cell;
+                        const bool want = !done && cell_lb(c, s3, rx0, rx1, ry0, ry1, jex, jtk) <= tau;
+                        if (__any_sync(FULLMASK, want))
+                            visit(jlo, jhi, false);
+                    }
+                }
+            }
+        }
+
+        // ---- settle and write
+        __syncwarp();
+        if (active)
+            st.q++;
+        if (active && !deferred) {
+            if (!finalize_query(W, q, K, Lw, cl_d, cl_i, qrow, st)) {
+                const unsigned slot = atomicAdd(&L.scr->n_fallback, 1u);
+                if (slot < (unsigned long long)L.fb_cap)
+                    L.fb_list[slot] = make_int2(window_id(L, W), (int)qrow);
+                else
+                    atomicOr(&L.scr->status, 1u);
+            }
+        }
+        __syncwarp();
+    }
+    flush_stats(L.scr, st);
+}

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "tnn_internal.cuh"
@@ -341,6 +342,121 @@ __global__ void k_gather_points(const unsigned long long *__restrict__ keys,
     idx[i] = j;
 }
 
+// ------------------------------------------------------------------- grid
+
+__device__ __forceinline__ float ord2f(uint32_t u)
+{
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// Extremes of the segment midpoints (scaled x, y) and of t_A, and the sum of
+// the segment durations, for choosing the grid.
+__global__ void k_seg_extremes(const float4 *__restrict__ seg, int S,
+                               unsigned int *ext_ord, double *dur_sum)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S)
+        return;
+    const float4 a = seg[4 * s], u = seg[4 * s + 1], b = seg[4 * s + 2];
+    const float mx = fmaf(0.5f, b.x, a.x), my = fmaf(0.5f, b.y, a.y);
+    atomicMin(ext_ord + 0, f2ord(mx));
+    atomicMax(ext_ord + 1, f2ord(mx));
+    atomicMin(ext_ord + 2, f2ord(my));
+    atomicMax(ext_ord + 3, f2ord(my));
+    atomicMin(ext_ord + 4, f2ord(a.w));
+    atomicMax(ext_ord + 5, f2ord(a.w));
+    atomicAdd(dur_sum, (double)u.w - (double)a.w);
+}
+
+struct GridBuild {
+    float x0, y0, cell, inv_cell, t0, dt, inv_dt;
+    int nx, ny, ncell, nb;
+};
+
+// Key of every segment (t_A order position p) and the per-key aggregates:
+// the extent (FP64, rounded up) of the member cylinders around the key's cell
+// rectangle and the largest t_B; the per-bucket largest t_B.
+__global__ void k_grid_keys(const float4 *__restrict__ seg, int S, GridBuild g,
+                            unsigned long long *__restrict__ keys,
+                            unsigned int *__restrict__ ext_bits,
+                            unsigned int *__restrict__ tB_ord,
+                            unsigned int *__restrict__ bmax_ord)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= S)
+        return;
+    const float4 a = seg[4 * p], u = seg[4 * p + 1], b = seg[4 * p + 2];
+    const float mx = fmaf(0.5f, b.x, a.x), my = fmaf(0.5f, b.y, a.y);
+    const int bk = min(max((int)floorf((a.w - g.t0) * g.inv_dt), 0), g.nb - 1);
+    const int cx = min(max((int)floorf((mx - g.x0) * g.inv_cell), 0), g.nx - 1);
+    const int cy = min(max((int)floorf((my - g.y0) * g.inv_cell), 0), g.ny - 1);
+    const int key = bk * g.ncell + cy * g.nx + cx;
+    keys[p] = ((unsigned long long)(unsigned)key << 32) | (unsigned)p;
+    // every cylinder point is within |AB|/2 + r of the midpoint
+    const double ax = a.x, ay = a.y, az = a.z, bx = b.x, by = b.y, bz = b.z;
+    const double half = 0.5 * sqrt(bx * bx + by * by + bz * bz) + (double)b.w;
+    const double Mx = ax + 0.5 * bx, My = ay + 0.5 * by;
+    const double rx0 = (double)g.x0 + cx * (double)g.cell, rx1 = rx0 + g.cell;
+    const double ry0 = (double)g.y0 + cy * (double)g.cell, ry1 = ry0 + g.cell;
+    const double dx = fmax(fmax(rx0 - Mx, Mx - rx1), 0.0);
+    const double dy = fmax(fmax(ry0 - My, My - ry1), 0.0);
+    // margin for the FP32 evaluation of the rectangle corners at query time
+    const double margin = 1e-6 * (fabs((double)g.x0) + fabs((double)g.y0) +
+                                  (double)g.cell * (g.nx + g.ny + 2)) + 1e-9;
+    const float e = __double2float_ru(sqrt(dx * dx + dy * dy) + half + margin);
+    atomicMax(ext_bits + key, __float_as_uint(e));
+    atomicMax(tB_ord + key, f2ord(u.w));
+    atomicMax(bmax_ord + bk, f2ord(u.w));
+}
+
+// off[k] = number of sorted keys below k.
+__global__ void k_grid_offsets(const unsigned long long *__restrict__ keys, int S,
+                               int nkeys, int32_t *__restrict__ off)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > nkeys)
+        return;
+    const unsigned long long t = (unsigned long long)(unsigned)k << 32;
+    int lo = 0, hi = S;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (keys[mid] < t)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    off[k] = lo;
+}
+
+__global__ void k_grid_ids(const unsigned long long *__restrict__ keys, int S,
+                           int32_t *__restrict__ ids)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < S)
+        ids[i] = (int32_t)(keys[i] & 0xffffffffu);
+}
+
+__global__ void k_decode_ord(unsigned int *__restrict__ v, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const unsigned int u = v[i];
+        v[i] = u ? __float_as_uint(ord2f(u)) : __float_as_uint(-INFINITY);
+    }
+}
+
+// Running maximum over buckets (one block).
+__global__ void k_prefix_max(float *__restrict__ v, int n)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        float m = -INFINITY;
+        for (int i = 0; i < n; ++i) {
+            m = fmaxf(m, v[i]);
+            v[i] = m;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- host API
 
 static void free_index(tnn_index *ix)
@@ -353,6 +469,11 @@ static void free_index(tnn_index *ix)
     cudaFree(ix->segPM);
     cudaFree(ix->pts_t);
     cudaFree(ix->idx_t);
+    cudaFree(ix->g_off);
+    cudaFree(ix->g_ids);
+    cudaFree(ix->g_ext);
+    cudaFree(ix->g_tB);
+    cudaFree(ix->g_bpm);
     delete ix;
 }
 
@@ -360,6 +481,118 @@ struct DevBuf {
     void *p = nullptr;
     ~DevBuf() { cudaFree(p); }
 };
+
+static float host_ord2f(uint32_t u)
+{
+    uint32_t v = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+    float f;
+    memcpy(&f, &v, sizeof(f));
+    return f;
+}
+
+// Choose the grid from the segment extremes and build it (synchronises).
+// Buckets span about four mean segment durations (at most 4096 of them);
+// cells are square, about two segments per (bucket, cell) on average, at most
+// 65,536 cells and 2^22 keys.
+static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
+                             cudaStream_t st)
+{
+    const int S = (int)ix->S, tb = 256;
+    DevBuf sb;
+    TNN_CUDA_TRY(cudaMalloc(&sb.p, 64));
+    unsigned int init[8] = {0xffffffffu, 0u, 0xffffffffu, 0u, 0xffffffffu, 0u, 0u, 0u};
+    TNN_CUDA_TRY(cudaMemcpyAsync(sb.p, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    TNN_CUDA_TRY(cudaMemsetAsync((char *)sb.p + 32, 0, 8, st));
+    k_seg_extremes<<<(S + tb - 1) / tb, tb, 0, st>>>(ix->seg, S, (unsigned int *)sb.p,
+                                                    (double *)((char *)sb.p + 32));
+    unsigned int h[8];
+    double dur = 0.0;
+    TNN_CUDA_TRY(cudaMemcpyAsync(h, sb.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    TNN_CUDA_TRY(cudaMemcpyAsync(&dur, (char *)sb.p + 32, 8, cudaMemcpyDeviceToHost, st));
+    TNN_CUDA_TRY(cudaStreamSynchronize(st));
+    const double xmn = host_ord2f(h[0]), xmx = host_ord2f(h[1]);
+    const double ymn = host_ord2f(h[2]), ymx = host_ord2f(h[3]);
+    const double tmn = host_ord2f(h[4]), tmx = host_ord2f(h[5]);
+    const double T = tmx - tmn;
+    double dt = 4.0 * dur / S;
+    if (!(dt > 0.0))
+        dt = T > 0.0 ? T / 64.0 : 1.0;
+    if (T / dt > 4095.0)
+        dt = T / 4095.0;
+    int nb = (int)std::min(4096.0, floor(T / dt) + 1.0);
+    const double Wd = xmx - xmn, Hd = ymx - ymn;
+    const double target = std::min(65536.0, std::max(1.0, 2.0 * S / nb));
+    double cell = sqrt(std::max(Wd * Hd, 1e-12) / target);
+    cell = std::max(cell, std::max(std::max(Wd, Hd) / 1024.0, 1e-6));
+    int nx = 1, ny = 1;
+    for (;;) {
+        nx = (int)floor(Wd / cell) + 1;
+        ny = (int)floor(Hd / cell) + 1;
+        if ((double)nx * ny <= 65536.0 && (double)nb * nx * ny <= (double)(1 << 22))
+            break;
+        cell *= 1.25;
+    }
+    GridBuild g;
+    g.x0 = (float)xmn;
+    g.y0 = (float)ymn;
+    g.cell = (float)cell;
+    g.inv_cell = (float)(1.0 / cell);
+    g.t0 = (float)tmn;
+    g.dt = (float)dt;
+    g.inv_dt = (float)(1.0 / dt);
+    g.nx = nx;
+    g.ny = ny;
+    g.ncell = nx * ny;
+    g.nb = nb;
+    const int nkeys = nb * g.ncell;
+    TNN_CUDA_TRY(cudaMalloc(&ix->g_off, sizeof(int32_t) * (nkeys + 1)));
+    TNN_CUDA_TRY(cudaMalloc(&ix->g_ids, sizeof(int32_t) * S));
+    TNN_CUDA_TRY(cudaMalloc(&ix->g_ext, sizeof(float) * nkeys));
+    TNN_CUDA_TRY(cudaMalloc(&ix->g_tB, sizeof(float) * nkeys));
+    TNN_CUDA_TRY(cudaMalloc(&ix->g_bpm, sizeof(float) * nb));
+    TNN_CUDA_TRY(cudaMemsetAsync(ix->g_ext, 0, sizeof(float) * nkeys, st));
+    TNN_CUDA_TRY(cudaMemsetAsync(ix->g_tB, 0, sizeof(float) * nkeys, st));
+    TNN_CUDA_TRY(cudaMemsetAsync(ix->g_bpm, 0, sizeof(float) * nb, st));
+    TNN_CUDA_TRY(cudaMemsetAsync((char *)sb.p + 48, 0, 4, st));
+    k_fill<<<(s2 - S + tb - 1) / tb + 1, tb, 0, st>>>(keys, S, s2);
+    k_grid_keys<<<(S + tb - 1) / tb, tb, 0, st>>>(ix->seg, S, g, keys, (unsigned int *)ix->g_ext,
+                                                 (unsigned int *)ix->g_tB,
+                                                 (unsigned int *)ix->g_bpm);
+    bitonic_sort(keys, s2, st);
+    k_grid_offsets<<<(nkeys + 1 + tb - 1) / tb, tb, 0, st>>>(keys, S, nkeys, ix->g_off);
+    k_grid_ids<<<(S + tb - 1) / tb, tb, 0, st>>>(keys, S, ix->g_ids);
+    k_decode_ord<<<(nkeys + tb - 1) / tb, tb, 0, st>>>((unsigned int *)ix->g_tB, nkeys);
+    k_decode_ord<<<(nb + tb - 1) / tb, tb, 0, st>>>((unsigned int *)ix->g_bpm, nb);
+    k_prefix_max<<<1, 32, 0, st>>>(ix->g_bpm, nb);
+    TNN_CUDA_TRY(cudaGetLastError());
+    // largest extent (for the search region)
+    std::vector<float> hext(nkeys);
+    TNN_CUDA_TRY(cudaMemcpyAsync(hext.data(), ix->g_ext, sizeof(float) * nkeys,
+                                 cudaMemcpyDeviceToHost, st));
+    TNN_CUDA_TRY(cudaStreamSynchronize(st));
+    float emax = 0.f;
+    for (float v : hext)
+        emax = std::max(emax, v);
+    GridDesc &G = ix->grid;
+    G.x0 = g.x0;
+    G.y0 = g.y0;
+    G.cell = g.cell;
+    G.inv_cell = g.inv_cell;
+    G.t0 = g.t0;
+    G.dt = g.dt;
+    G.inv_dt = g.inv_dt;
+    G.ext_max = emax;
+    G.nx = nx;
+    G.ny = ny;
+    G.ncell = g.ncell;
+    G.nb = nb;
+    G.off = ix->g_off;
+    G.ids = ix->g_ids;
+    G.ext = ix->g_ext;
+    G.tB = ix->g_tB;
+    G.bpm = ix->g_bpm;
+    return TNN_OK;
+}
 
 extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
                                          const int64_t *h_traj_off,
@@ -467,6 +700,13 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
     k_gather_segments<<<(Si + tb - 1) / tb, tb, 0, st>>>(keys, (const float4 *)rec_d.p,
                                                          Si, ix->seg, ix->segTA);
     k_prefix_max_tB<<<1, 1024, 0, st>>>(ix->seg, Si, ix->segPM);
+    {
+        tnn_status gs = build_grid(ix, keys, s2, st);
+        if (gs != TNN_OK) {
+            free_index(ix);
+            return gs;
+        }
+    }
     k_time_keys<<<(n2 + tb - 1) / tb, tb, 0, st>>>(ix->pts, ni, keys, n2);
     bitonic_sort(keys, n2, st);
     k_gather_points<<<(ni + tb - 1) / tb, tb, 0, st>>>(keys, ix->pts, ni, ix->pts_t,

@@ -35,6 +35,24 @@ void tnn_clear_error();
 // Floats per exported / stored segment record (4 x float4).
 #define TNN_SEG_FLOATS 16
 
+// Time-bucketed spatial grid over the segments.  Every segment belongs to
+// exactly one key = (bucket of t_A, cell of its midpoint in the scaled x-y
+// plane); per key the search reads the CSR range of its segments, an extent
+// e such that every point of every member cylinder lies within e of the
+// key's cell rectangle, and the largest t_B of the members.
+struct GridDesc {
+    float x0, y0;       // scaled-space corner of cell (0, 0)
+    float cell, inv_cell;
+    float t0, dt, inv_dt; // bucket b covers t_A in [t0 + b dt, t0 + (b+1) dt)
+    float ext_max;      // largest extent over the keys
+    int32_t nx, ny, ncell, nb;
+    const int32_t *off; // [nb * ncell + 1]
+    const int32_t *ids; // [S] segment positions (t_A order) grouped by key
+    const float *ext;   // [nb * ncell]
+    const float *tB;    // [nb * ncell]
+    const float *bpm;   // [nb] running max over buckets <= b of the max t_B
+};
+
 struct tnn_index {
     int device;
     int64_t n;      // points
@@ -52,6 +70,9 @@ struct tnn_index {
     float *segPM;    // [S] running max of t_B in that order
     float4 *pts_t;   // [n] points ordered by (t, index)  (linear search)
     int32_t *idx_t;  // [n] their input index
+    GridDesc grid;   // views of the arrays below
+    int32_t *g_off, *g_ids;
+    float *g_ext, *g_tB, *g_bpm;
 };
 
 // Parameters of one independent k-NN problem, read by the search kernels.
@@ -67,6 +88,7 @@ struct KnnWin {
     float *out_d2;
     int64_t m;
     int64_t tile_begin; // first global tile of this window
+    GridDesc grid;
     double sigd[4];
     double lag;
     float sig[4];
@@ -78,6 +100,7 @@ struct KnnWin {
     int32_t L; // candidate slots per query (k + extra)
     int32_t F; // seed segments
     int32_t W0; // seed window
+    float tau_defer; // lanes whose key exceeds this after seeding are deferred
     int32_t flags;
     int32_t pad_;
 };

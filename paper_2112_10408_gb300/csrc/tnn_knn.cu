@@ -57,6 +57,7 @@
 
 #include "tnn_device.cuh"
 #include "tnn_search.cuh"
+#include "tnn_grid.cuh"
 #include "tnn_linear.cuh"
 #include "tnn_fallback.cuh"
 
@@ -116,8 +117,9 @@ static tnn_status device_setup()
     if (!attrs) {
         const int maxs = 227 * 1024;
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_tnn_search, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
+        TNN_CUDA_TRY(cudaFuncSetAttribute(k_tnn_grid_search, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_linear_search, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
-        TNN_CUDA_TRY(cudaFuncSetAttribute(k_fallback_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
+        TNN_CUDA_TRY(cudaFuncSetAttribute(k_tnn_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_fallback_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
         attrs = true;
     }
@@ -154,6 +156,7 @@ tnn_status tnn_fill_window(const tnn_index *ix, const float *d_q, int64_t m,
     w->segPM = ix->segPM;
     w->pts_t = ix->pts_t;
     w->idx_t = ix->idx_t;
+    w->grid = ix->grid;
     w->q = d_q ? (const float4 *)d_q : ix->pts;
     w->out_idx = d_idx;
     w->out_d2 = d_d2;
@@ -172,6 +175,11 @@ tnn_status tnn_fill_window(const tnn_index *ix, const float *d_q, int64_t m,
     w->L = p->k + E;
     w->F = F;
     w->W0 = W0;
+    {
+        const double dc = p->defer_cells == 0.0f ? 1.5 : (double)p->defer_cells;
+        const double side = dc * (double)ix->grid.cell;
+        w->tau_defer = dc > 0.0 ? (float)(side * side) : INFINITY;
+    }
     w->flags = p->flags;
     return TNN_OK;
 }
@@ -183,10 +191,10 @@ tnn_status tnn_launch_search(const KnnLaunch &L, bool brute, cudaStream_t st)
         return s;
     const size_t smem = smem_per_warp(L.L_max, L.kseg_max, brute) * TNN_WARPS_PER_CTA;
     int nb = 0;
-    if (brute)
-        TNN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_linear_search, TNN_WARPS_PER_CTA * 32, smem));
-    else
-        TNN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tnn_search, TNN_WARPS_PER_CTA * 32, smem));
+    const bool sweep = (L.w0.flags & TNN_FLAG_SWEEP) != 0;
+    const void *kern = brute ? (const void *)k_linear_search
+                             : sweep ? (const void *)k_tnn_search : (const void *)k_tnn_grid_search;
+    TNN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, TNN_WARPS_PER_CTA * 32, smem));
     if (nb < 1) {
         tnn_set_error("search kernel does not fit on an SM (%zu B shared memory)", smem);
         return TNN_ERR_UNSUPPORTED;
@@ -203,15 +211,21 @@ tnn_status tnn_launch_search(const KnnLaunch &L, bool brute, cudaStream_t st)
         TNN_CUDA_TRY(prof_begin(st, &pr));
     if (brute)
         k_linear_search<<<(unsigned)grid, TNN_WARPS_PER_CTA * 32, smem, st>>>(L);
-    else
+    else if (sweep)
         k_tnn_search<<<(unsigned)grid, TNN_WARPS_PER_CTA * 32, smem, st>>>(L);
+    else
+        k_tnn_grid_search<<<(unsigned)grid, TNN_WARPS_PER_CTA * 32, smem, st>>>(L);
     TNN_CUDA_TRY(cudaGetLastError());
     if (prof) {
         TNN_CUDA_TRY(cudaEventRecord(pr.second, st));
         g_prof_ev.push_back(pr);
     }
-    k_fallback_scan<<<(unsigned)g_num_sms, TNN_WARPS_PER_CTA * 32,
-                      fb_scan_smem_per_warp(L.L_max) * TNN_WARPS_PER_CTA, st>>>(L);
+    {
+        const size_t wsm = wq_smem_per_warp() * TNN_WARPS_PER_CTA;
+        int nbw = 0;
+        TNN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbw, k_tnn_warp, TNN_WARPS_PER_CTA * 32, wsm));
+        k_tnn_warp<<<(unsigned)(std::max(nbw, 1) * g_num_sms), TNN_WARPS_PER_CTA * 32, wsm, st>>>(L);
+    }
     TNN_CUDA_TRY(cudaGetLastError());
     k_fallback_exact<<<(unsigned)g_num_sms, TNN_WARPS_PER_CTA * 32,
                        fb_exact_smem_per_warp(L.L_max) * TNN_WARPS_PER_CTA, st>>>(L);
@@ -266,7 +280,8 @@ static tnn_status run_single(const tnn_index *ix, const float *d_q, int64_t m,
             h_stats->pairs = hs.stats[2];
             h_stats->segs_scanned = hs.stats[3];
             h_stats->fp64_rechecks = hs.stats[4];
-            h_stats->fallback_queries = hs.stats[5];
+            h_stats->warp_queries = hs.stats[5];
+            h_stats->exact_queries = hs.stats[6];
         }
     }
     cudaFreeAsync(buf, st);
@@ -441,7 +456,8 @@ extern "C" tnn_status tnn_batch_stats(tnn_batch *b, tnn_stats *h, tnn_stream_t s
     h->pairs = hs.stats[2];
     h->segs_scanned = hs.stats[3];
     h->fp64_rechecks = hs.stats[4];
-    h->fallback_queries = hs.stats[5];
+    h->warp_queries = hs.stats[5];
+    h->exact_queries = hs.stats[6];
     return TNN_OK;
 }
 

@@ -39,13 +39,15 @@ class tnn_index_info(ctypes.Structure):
 
 class tnn_knn_params(ctypes.Structure):
     _fields_ = [("k", c_i32), ("lag", c_f64), ("seed_segments", c_i32),
-                ("seed_window", c_i32), ("extra", c_i32), ("flags", c_i32)]
+                ("seed_window", c_i32), ("extra", c_i32), ("flags", c_i32),
+                ("defer_cells", c_f32)]
 
 
 class tnn_stats(ctypes.Structure):
     _fields_ = [("queries", ctypes.c_uint64), ("lb_evals", ctypes.c_uint64),
                 ("pairs", ctypes.c_uint64), ("segs_scanned", ctypes.c_uint64),
-                ("fp64_rechecks", ctypes.c_uint64), ("fallback_queries", ctypes.c_uint64)]
+                ("fp64_rechecks", ctypes.c_uint64), ("warp_queries", ctypes.c_uint64),
+                ("exact_queries", ctypes.c_uint64)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -57,6 +59,7 @@ class tnn_adamw_params(ctypes.Structure):
 
 
 TNN_FLAG_EXACT_D2 = 1
+TNN_FLAG_SWEEP = 2
 N_FEAT = 6
 
 # (name, restype, argtypes)
@@ -210,14 +213,16 @@ def tnn_index_export(index: Index):
 
 
 def make_knn_params(k: int, lag: float = 0.0, seed_segments: int = 0, seed_window: int = 0,
-                    extra: int = 0, exact_d2: bool = False) -> tnn_knn_params:
+                    extra: int = 0, exact_d2: bool = False, sweep: bool = False,
+                    defer_cells: float = 0.0) -> tnn_knn_params:
     p = tnn_knn_params()
     p.k = int(k)
     p.lag = float(lag)
     p.seed_segments = int(seed_segments)
     p.seed_window = int(seed_window)
     p.extra = int(extra)
-    p.flags = TNN_FLAG_EXACT_D2 if exact_d2 else 0
+    p.flags = (TNN_FLAG_EXACT_D2 if exact_d2 else 0) | (TNN_FLAG_SWEEP if sweep else 0)
+    p.defer_cells = float(defer_cells)
     return p
 
 
