@@ -270,7 +270,8 @@ void tnn_batch_destroy(tnn_batch *batch);
 /* -------------------------------------------------------------- autotune */
 
 /*
- * Choose seed_segments, seed_window and extra for one index and k by timing
+ * Choose the segment order (TNN_FLAG_SWEEP), seed_segments, extra and
+ * defer_cells for one index and k by timing
  * the search on a sample of `m_sample` self-queries spread over the index
  * (CUDA events).  Writes the best into *params (k, lag, flags untouched).
  * Synchronises `stream`.

@@ -3,17 +3,21 @@
 //     was too large for a shared tile (e.g. a flight's first samples, whose
 //     neighbours are far away); Algorithm 2 puts such unfinished lines
 //     aside and carries on with the others -- they are finished here, where
-//     the whole warp works on one query;
-//   - unsettled: the chain of FP32 keys that FP32 cannot order reached the
-//     last candidate slot.  Here the list keeps k + 32 candidates.
+//     the whole warp works on one query (list of k + extra candidates);
+//   - unsettled (window id stored as -1 - w): the chain of FP32 keys that FP32
+//     cannot order reached the last candidate slot; here the list keeps
+//     k + 32 candidates.
 //
 // k_tnn_warp: the 32 lanes split the grid keys, the member segments and the
 // member points of one query.  Candidates below the pruning key are sorted
 // across the warp (bitonic) and merged into a sorted list in shared memory
 // (merge path).  Seeding visits cubes of keys of growing radius around the
-// query's own key (cells in the plane, buckets backwards in time) and scans
-// every point in them until the list is full; the main phase is the
-// exclusion criterion and stop rule of Algorithm 2 over the remaining keys.
+// query's own key (cells in the plane, buckets backwards in time) until the
+// list is full; inside a chunk of segments, while the list is not full, the
+// segment of smallest bound is scanned first (Algorithm 2's nearest-first
+// fetch), so the pruning key is tight as soon as it exists.  The main phase
+// is the exclusion criterion and stop rule of Algorithm 2 over the other
+// keys, scanning the needed segments of a chunk 32 points at a time.
 // A query still unsettled goes to k_fallback_exact: the FP64 definition.
 #pragma once
 #include "tnn_device.cuh"
@@ -21,12 +25,15 @@
 
 #define FB_EXTRA 32
 #define WQ_CMAX (64 + FB_EXTRA)
+#define WQ_RSEED 3
 
 __host__ __device__ inline size_t wq_smem_per_warp()
 {
-    // list [WQ_CMAX] + merge output [WQ_CMAX] + batch [32] (u64), and the
-    // settlement scratch ([CMAX][32] u64 + [CMAX][32] int) after them
-    return (size_t)(2 * WQ_CMAX + 32) * 8 + (size_t)CMAX * 32 * 12;
+    // list [WQ_CMAX] + merge output [WQ_CMAX] + batch [32] (u64), packed
+    // segment starts and firsts, packed key starts and ranges [4][32] (int),
+    // and the settlement scratch
+    // ([CMAX][32] u64 + [CMAX][32] int) after them
+    return (size_t)(2 * WQ_CMAX + 32) * 8 + 128 * 4 + (size_t)CMAX * 32 * 12;
 }
 
 __host__ __device__ inline size_t fb_exact_smem_per_warp(int k_max)
@@ -52,6 +59,15 @@ __device__ __forceinline__ unsigned long long warp_sort_u64(unsigned long long v
             const unsigned long long mn = o < v ? o : v, mx = o < v ? v : o;
             v = (lower == up) ? mn : mx;
         }
+    }
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = shfl_xor_u64(v, o);
+        v = w < v ? w : v;
     }
     return v;
 }
@@ -111,7 +127,11 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
     wl.L = (unsigned long long *)ws;
     wl.tmp = wl.L + WQ_CMAX;
     wl.B = wl.tmp + WQ_CMAX;
-    unsigned long long *cl_d = (unsigned long long *)(ws + (size_t)(2 * WQ_CMAX + 32) * 8);
+    int *Sstart = (int *)(wl.B + 32);
+    int *Sfirst = Sstart + 32;
+    int *Kstart = Sfirst + 32;
+    int *Klo = Kstart + 32;
+    unsigned long long *cl_d = (unsigned long long *)(Klo + 32);
     int *cl_i = (int *)((unsigned char *)cl_d + CMAX * 32 * 8);
 
     unsigned nfb = *(volatile unsigned *)&L.scr->n_fallback;
@@ -119,17 +139,28 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
         nfb = (unsigned)L.fb_cap;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
+    (void)gw;
+    (void)nw;
     LaneStats st = {0, 0, 0, 0, 0};
-    for (unsigned e = gw; e < nfb; e += nw) {
+    for (;;) {
+        // dynamic queue: query costs differ by orders of magnitude
+        unsigned e = 0;
+        if (lane == 0)
+            e = atomicAdd(&L.scr->fb_next, 1u);
+        e = __shfl_sync(FULLMASK, e, 0);
+        if (e >= nfb)
+            break;
         const int2 ent = L.fb_list[e];
-        const KnnWin *W = L.nwin <= 1 ? &L.w0 : L.wins + ent.x;
+        const bool unsettled = ent.x < 0;
+        const int wid = unsettled ? -1 - ent.x : ent.x;
+        const KnnWin *W = L.nwin <= 1 ? &L.w0 : L.wins + wid;
         const float4 q = W->q[ent.y];
         const QCtx c = make_qctx(W, q, true);
         const float s0 = W->sig[0], s1 = W->sig[1], s2 = W->sig[2], s3 = W->sig[3];
         const float4 *__restrict__ seg = W->seg;
         const float4 *__restrict__ pts = W->pts;
         const GridDesc &G = W->grid;
-        wl.C = W->k + FB_EXTRA;
+        wl.C = unsettled ? W->k + FB_EXTRA : W->L;
         wl.nv = 0;
         wl.tauk = SENT;
         for (int p = lane; p < wl.C; p += 32)
@@ -138,7 +169,8 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
 
         // all points of one segment, 32 at a time
         auto scan_seg = [&](int first, int cnt) {
-            st.segs++;
+            if (lane == 0)
+                st.segs++;
             for (int o = 0; o < cnt; o += 32) {
                 const int j = o + lane;
                 unsigned long long ck = SENT;
@@ -152,32 +184,107 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
                 wl_merge(wl, ck, lane);
             }
         };
-        // the member segments of one key: all of them (seeding) or those whose
-        // cylinder bound does not exceed the pruning key
-        auto visit_key = [&](int key, bool all) {
-            const int lo = __ldg(G.off + key), hi = __ldg(G.off + key + 1);
-            for (int base = lo; base < hi; base += 32) {
-                const int i = base + lane;
-                bool need = false;
-                float4 meta = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (i < hi) {
-                    const float4 *src = seg + 4 * (size_t)__ldg(G.ids + i);
-                    meta = __ldg(src + 3);
-                    if (all) {
-                        need = true;
-                    } else {
-                        const float lb = seg_lb(c, s3, __ldg(src), __ldg(src + 1), __ldg(src + 2));
-                        st.lb++;
-                        need = lb <= key_d(wl.tauk);
+        // the points of every lane's segment with `need`, packed 32 per step
+        auto scan_packed = [&](bool need, float4 meta) {
+            const unsigned m = __ballot_sync(FULLMASK, need);
+            const int cnt = need ? __float_as_int(meta.y) : 0;
+            int incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(FULLMASK, incl, o);
+                if (lane >= o)
+                    incl += t;
+            }
+            const int total = __shfl_sync(FULLMASK, incl, 31);
+            const int nseg = __popc(m);
+            if (need) {
+                const int rank = __popc(m & ((1u << lane) - 1u));
+                Sstart[rank] = incl - cnt;
+                Sfirst[rank] = __float_as_int(meta.x);
+            }
+            if (lane == 0)
+                st.segs += nseg;
+            __syncwarp();
+            for (int s = 0; s < total; s += 32) {
+                const int g = s + lane;
+                unsigned long long ck = SENT;
+                if (g < total) {
+                    int lo = 0, hi = nseg - 1; // largest r with Sstart[r] <= g
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (Sstart[mid] <= g)
+                            lo = mid;
+                        else
+                            hi = mid - 1;
                     }
+                    const int j = Sfirst[lo] + (g - Sstart[lo]);
+                    const float4 p = __ldg(pts + j);
+                    const float d = dist32(c, s0, s1, s2, s3, p);
+                    if (p.w < c.T32)
+                        ck = pack_key(d, j);
+                    st.pairs++;
                 }
-                unsigned m = __ballot_sync(FULLMASK, need);
-                while (m) {
-                    const int j = __ffs(m) - 1;
-                    m &= m - 1;
-                    scan_seg(__float_as_int(__shfl_sync(FULLMASK, meta.x, j)),
-                             __float_as_int(__shfl_sync(FULLMASK, meta.y, j)));
+                wl_merge(wl, ck, lane);
+            }
+            __syncwarp();
+        };
+        // the member segments of one key whose cylinder bound does not exceed
+        // the pruning key; nearest first while the list is not full
+        // The member segments of every lane's key (key < 0: none; [klo, khi)
+        // its range of G.ids) are handled together, 32 segments per step
+        // whatever key they belong to.
+        auto visit_keys = [&](bool has, int klo, int khi) {
+            const unsigned km = __ballot_sync(FULLMASK, has);
+            if (!km)
+                return;
+            const int kc = has ? khi - klo : 0;
+            int incl = kc;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(FULLMASK, incl, o);
+                if (lane >= o)
+                    incl += t;
+            }
+            const int total = __shfl_sync(FULLMASK, incl, 31);
+            const int nk = __popc(km);
+            __syncwarp();
+            if (has) {
+                const int rank = __popc(km & ((1u << lane) - 1u));
+                Kstart[rank] = incl - kc;
+                Klo[rank] = klo;
+            }
+            __syncwarp();
+            for (int base = 0; base < total; base += 32) {
+                const int g = base + lane;
+                float lb = __int_as_float(0x7fffffff);
+                float4 meta = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (g < total) {
+                    int a = 0, z = nk - 1; // largest r with Kstart[r] <= g
+                    while (a < z) {
+                        const int mid = (a + z + 1) >> 1;
+                        if (Kstart[mid] <= g)
+                            a = mid;
+                        else
+                            z = mid - 1;
+                    }
+                    const float4 *src = seg + 4 * (size_t)__ldg(G.ids + Klo[a] + (g - Kstart[a]));
+                    meta = __ldg(src + 3);
+                    lb = seg_lb(c, s3, __ldg(src), __ldg(src + 1), __ldg(src + 2));
+                    st.lb++;
                 }
+                while (wl.nv < wl.C) {
+                    const bool need = lb <= key_d(wl.tauk);
+                    const unsigned long long arg = warp_min_u64(
+                        need ? (((unsigned long long)__float_as_uint(lb) << 32) | (unsigned)lane) : ~0ull);
+                    if (arg == ~0ull)
+                        break;
+                    const int who = (int)(arg & 31u);
+                    scan_seg(__float_as_int(__shfl_sync(FULLMASK, meta.x, who)),
+                             __float_as_int(__shfl_sync(FULLMASK, meta.y, who)));
+                    if (lane == who)
+                        lb = __int_as_float(0x7fffffff);
+                }
+                const bool need = lb <= key_d(wl.tauk);
+                if (__any_sync(FULLMASK, need))
+                    scan_packed(need, meta);
             }
         };
 
@@ -191,14 +298,17 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
             const int hx = min(max((int)floorf((c.sx - G.x0) * G.inv_cell), 0), G.nx - 1);
             const int hy = min(max((int)floorf((c.sy - G.y0) * G.inv_cell), 0), G.ny - 1);
             const int rcover = max(max(max(hx, G.nx - 1 - hx), max(hy, G.ny - 1 - hy)), bhi);
-            // ---- seeding: cubes of keys of growing radius, every point
+            // ---- seeding: shells of growing radius around the query's key, at
+            // most WQ_RSEED of them (a query with fewer than C valid points
+            // would otherwise grow the cube over the whole grid; the main
+            // phase visits each causal bucket once instead)
             int rs = -1;
-            while (wl.nv < wl.C && rs < rcover) {
+            while (wl.nv < wl.C && rs < rcover && rs < WQ_RSEED) {
                 const int r = ++rs;
                 const int side = 2 * r + 1, nk = side * side * (r + 1);
                 for (int t0 = 0; t0 < nk; t0 += 32) {
                     const int t = t0 + lane;
-                    int key = -1;
+                    int klo = 0, khi = 0;
                     if (t < nk) {
                         const int db = t / (side * side), rem = t % (side * side);
                         const int dy = rem / side - r, dx = rem % side - r;
@@ -206,16 +316,11 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
                         const bool shell = max(max(abs(dx), abs(dy)), db) == r;
                         if (shell && b >= 0 && cx >= 0 && cx < G.nx && cy >= 0 && cy < G.ny) {
                             const int k2 = b * G.ncell + cy * G.nx + cx;
-                            if (__ldg(G.off + k2 + 1) > __ldg(G.off + k2))
-                                key = k2;
+                            klo = __ldg(G.off + k2);
+                            khi = __ldg(G.off + k2 + 1);
                         }
                     }
-                    unsigned m = __ballot_sync(FULLMASK, key >= 0);
-                    while (m) {
-                        const int j = __ffs(m) - 1;
-                        m &= m - 1;
-                        visit_key(__shfl_sync(FULLMASK, key, j), true);
-                    }
+                    visit_keys(khi > klo, klo, khi);
                 }
             }
             // ---- main: buckets backwards, keys within reach, by bound
@@ -233,27 +338,25 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
                     const bool bseed = bhi - b <= rs;
                     for (int t0 = 0; t0 < nk; t0 += 32) {
                         const int t = t0 + lane;
-                        int key = -1;
+                        int klo = 0, khi = 0;
                         if (t < nk) {
                             const int cx = cx0 + t % wx, cy = cy0 + t / wx;
                             const bool seeded = bseed && abs(cx - hx) <= rs && abs(cy - hy) <= rs;
                             if (!seeded) {
                                 const int k2 = b * G.ncell + cy * G.nx + cx;
-                                if (__ldg(G.off + k2 + 1) > __ldg(G.off + k2)) {
+                                const int a0 = __ldg(G.off + k2), a1 = __ldg(G.off + k2 + 1);
+                                if (a1 > a0) {
                                     const float rx0 = G.x0 + (float)cx * G.cell;
                                     const float ry0 = G.y0 + (float)cy * G.cell;
                                     if (cell_lb(c, s3, rx0, rx0 + G.cell, ry0, ry0 + G.cell,
-                                                __ldg(G.ext + k2), __ldg(G.tB + k2)) <= key_d(wl.tauk))
-                                        key = k2;
+                                                __ldg(G.ext + k2), __ldg(G.tB + k2)) <= key_d(wl.tauk)) {
+                                        klo = a0;
+                                        khi = a1;
+                                    }
                                 }
                             }
                         }
-                        unsigned m = __ballot_sync(FULLMASK, key >= 0);
-                        while (m) {
-                            const int j = __ffs(m) - 1;
-                            m &= m - 1;
-                            visit_key(__shfl_sync(FULLMASK, key, j), false);
-                        }
+                        visit_keys(khi > klo, klo, khi);
                     }
                 }
             }
@@ -263,7 +366,7 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
             if (!finalize_query(W, q, wl.L, wl.C, cl_d, cl_i, ent.y, st, 1)) {
                 const unsigned slot = atomicAdd(&L.scr->n_fallback3, 1u);
                 if (slot < (unsigned long long)L.fb_cap)
-                    L.fb_list3[slot] = ent;
+                    L.fb_list3[slot] = make_int2(wid, ent.y);
                 else
                     atomicOr(&L.scr->status, 2u);
             }
@@ -299,7 +402,15 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const unsigned long long INF64 = 0x7ff0000000000000ull;
     unsigned long long nfp = 0;
-    for (unsigned e = gw; e < nfb; e += nw) {
+    (void)gw;
+    (void)nw;
+    for (;;) {
+        unsigned e = 0;
+        if (lane == 0)
+            e = atomicAdd(&L.scr->fb_next3, 1u);
+        e = __shfl_sync(FULLMASK, e, 0);
+        if (e >= nfb)
+            break;
         const int2 ent = L.fb_list3[e];
         const KnnWin *W = L.nwin <= 1 ? &L.w0 : L.wins + ent.x;
         const float4 q = W->q[ent.y];

@@ -113,6 +113,8 @@ struct KnnScratch {
     unsigned int n_fallback;  // queries handed to the FP32 warp scan
     unsigned int status;
     unsigned int n_fallback3; // queries handed to the exact FP64 warp scan
+    unsigned int fb_next;     // work queue over fb_list
+    unsigned int fb_next3;    // work queue over fb_list3
     unsigned int pad_;
 };
 

@@ -499,37 +499,47 @@ extern "C" tnn_status tnn_autotune(const tnn_index *ix, tnn_knn_params *params,
         tnn_set_error("autotune setup failed: %s", cudaGetErrorString(e));
         s = TNN_ERR_CUDA;
     }
-    const int Fs[] = {2, 3, 4, 6};
-    const int Ws[] = {0, 512};
-    const int Es[] = {4, 8, 16};
+    // Candidates: the grid order over seed count F, spare slots and the
+    // deferral threshold, plus the sweep order with two seed counts.
+    struct Cand {
+        int F, E, flags;
+        float defer;
+    };
+    std::vector<Cand> cands;
+    for (int F : {2, 3, 4})
+        for (int E : {4, 8})
+            for (float dfr : {0.75f, 1.5f, 3.0f})
+                cands.push_back({F, E, 0, dfr});
+    for (int F : {3, 4})
+        cands.push_back({F, 4, TNN_FLAG_SWEEP, 0.0f});
     float best = 1e30f;
     tnn_knn_params bestp = *params;
-    for (int a = 0; a < 4 && s == TNN_OK; ++a)
-        for (int b = 0; b < 2 && s == TNN_OK; ++b)
-            for (int c = 0; c < 3 && s == TNN_OK; ++c) {
-                tnn_knn_params p = *params;
-                p.seed_segments = Fs[a];
-                p.seed_window = Ws[b];
-                p.extra = Es[c];
-                s = tnn_knn(ix, (const float *)dq, m, &p, di, dd, nullptr, stream);
-                if (s != TNN_OK)
-                    break;
-                cudaEventRecord(e0, st);
-                for (int r = 0; r < 3 && s == TNN_OK; ++r)
-                    s = tnn_knn(ix, (const float *)dq, m, &p, di, dd, nullptr, stream);
-                cudaEventRecord(e1, st);
-                if (cudaEventSynchronize(e1) != cudaSuccess) {
-                    tnn_set_error("autotune timing failed");
-                    s = TNN_ERR_CUDA;
-                    break;
-                }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) {
-                    best = ms;
-                    bestp = p;
-                }
-            }
+    for (size_t ci = 0; ci < cands.size() && s == TNN_OK; ++ci) {
+        tnn_knn_params p = *params;
+        p.seed_segments = cands[ci].F;
+        p.seed_window = 0;
+        p.extra = cands[ci].E;
+        p.flags = (params->flags & ~TNN_FLAG_SWEEP) | cands[ci].flags;
+        p.defer_cells = cands[ci].defer;
+        s = tnn_knn(ix, (const float *)dq, m, &p, di, dd, nullptr, stream);
+        if (s != TNN_OK)
+            break;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && s == TNN_OK; ++r)
+            s = tnn_knn(ix, (const float *)dq, m, &p, di, dd, nullptr, stream);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            tnn_set_error("autotune timing failed");
+            s = TNN_ERR_CUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            bestp = p;
+        }
+    }
     if (e0)
         cudaEventDestroy(e0);
     if (e1)
@@ -540,6 +550,8 @@ extern "C" tnn_status tnn_autotune(const tnn_index *ix, tnn_knn_params *params,
     if (s == TNN_OK) {
         params->seed_segments = bestp.seed_segments;
         params->seed_window = bestp.seed_window;
+        params->flags = bestp.flags;
+        params->defer_cells = bestp.defer_cells;
         params->extra = bestp.extra;
     }
     return s;

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
             if (!finalize_query(W, q, K, Lw, cl_d, cl_i, qrow, st)) {
                 const unsigned slot = atomicAdd(&L.scr->n_fallback, 1u);
                 if (slot < (unsigned long long)L.fb_cap)
-                    L.fb_list[slot] = make_int2(window_id(L, W), (int)qrow);
+                    L.fb_list[slot] = make_int2(-1 - window_id(L, W), (int)qrow); // unsettled
                 else
                     atomicOr(&L.scr->status, 1u);
             }

@@ -301,7 +301,8 @@ def tnn_profile_read(reset: bool = True):
 def tnn_autotune(index: Index, k: int, lag: float = 0.0, m_sample: int = 4096, exact_d2=False):
     p = make_knn_params(k, lag, exact_d2=exact_d2)
     _check(_L().tnn_autotune(index.handle, ctypes.byref(p), int(m_sample), _stream()))
-    return dict(seed_segments=p.seed_segments, seed_window=p.seed_window, extra=p.extra)
+    return dict(seed_segments=p.seed_segments, seed_window=p.seed_window, extra=p.extra,
+                sweep=bool(p.flags & TNN_FLAG_SWEEP), defer_cells=float(p.defer_cells))
 
 
 # --------------------------------------------------------------------- batch
