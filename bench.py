@@ -27,10 +27,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "causal k-NN contexts/sec (exact, k=32) TNN vs GPU brute force on 1 GB300"
 UNIT = "contexts/s"
-# FP32 lane-operations per query-to-cylinder bound and per point distance
-# (instruction counts of seg_lb and of dist32 + mask + compare).
+# FP32 lane-operations per query-to-cylinder bound, per point distance and
+# per grid-key bound (instruction counts of seg_lb, of dist32 + mask +
+# compare, and of cell_lb).
 OPS_PER_LB = 26
 OPS_PER_PAIR = 14
+OPS_PER_KEY = 20
 
 
 def _args():
@@ -248,21 +250,23 @@ def run_ours(a):
 
     # executed and necessary work of one pass (outside the timed region)
     _, _, st = tnn.tnn_knn(ix, k, 0.0, stats=True, out=(idx, d2), **tune)
-    nlb, npairs = tnn.tnn_knn_work(ix, k, d2, 0.0)
+    nlb, npairs, nkeys = tnn.tnn_knn_work(ix, k, d2, 0.0)
     kern_avg_ms = kern_ms / max(launches, 1)
-    alg_ops = OPS_PER_LB * nlb + OPS_PER_PAIR * npairs
+    alg_ops = OPS_PER_LB * nlb + OPS_PER_PAIR * npairs + OPS_PER_KEY * nkeys
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = nsm * 128 * sm_max * 1e6 / 1e12  # T FP32 lane-ops/s
     achieved = alg_ops / (kern_avg_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "T FP32 lane-ops/s",
-                "frac": achieved / alu_peak, "traffic": None, "kernel": "k_tnn_search",
+                "frac": achieved / alu_peak, "traffic": None,
+                "kernel": "search = k_tnn_grid_search + k_tnn_warp + k_fallback_exact",
                 "kernel_ms": kern_avg_ms,
                 "peak_note": f"{nsm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived, not measured)",
-                "work_per_launch": {"lb_needed": nlb, "pairs_needed": npairs,
+                "work_per_launch": {"lb_needed": nlb, "pairs_needed": npairs, "keys_needed": nkeys,
                                     "lb_executed": st["lb_evals"], "pairs_executed": st["pairs"],
-                                    "ops_per_lb": OPS_PER_LB, "ops_per_pair": OPS_PER_PAIR}}
+                                    "ops_per_lb": OPS_PER_LB, "ops_per_pair": OPS_PER_PAIR,
+                                    "ops_per_key": OPS_PER_KEY}}
 
     # comparator: linear search on the same queries
     comparator = None
@@ -321,7 +325,7 @@ def run_ours(a):
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": dict(_config(wl, k, K, a.workload), tuning=tune,
                               parallelism=f"replicas x{world}: each rank its own window"),
-               "clocks": clocks, "e2e": e2e, "gpu_launches": 2 * a.steps,
+               "clocks": clocks, "e2e": e2e, "gpu_launches": 3 * a.steps,
                "roofline": roofline, "cpu_baseline": cpu, "comparator": comparator,
                "stats_per_step": st}
         print(json.dumps(out))

@@ -219,12 +219,15 @@ tnn_status tnn_segment_lower_bounds(const tnn_index *index, const float *d_q,
                                     tnn_stream_t stream);
 
 /*
- * The work the search must do for each query once its k-th distance d_k is
- * known (the "comparisons" of Table 3 reduced to the necessary ones):
- *   h_work[0] = sum over queries of the segments whose temporal bound does
- *               not exceed d_k (their cylinder bound has to be evaluated);
- *   h_work[1] = sum over queries of the member points of the segments whose
- *               cylinder bound does not exceed d_k (they have to be scanned).
+ * The work any exact search over this index must do for each query once its
+ * k-th distance d_k is known (the "comparisons" of Table 3 reduced to the
+ * necessary ones), summed over the queries:
+ *   h_work[0] = cylinder bounds: segments of the grid keys whose key bound
+ *               does not exceed d_k;
+ *   h_work[1] = point distances: members of the segments whose cylinder bound
+ *               does not exceed d_k;
+ *   h_work[2] = key bounds: non-empty keys of the causal buckets whose
+ *               temporal bound does not exceed d_k, within reach of d_k.
  * d_d2 [m][k] is the output of tnn_knn for the same queries (d_k = column
  * k-1, +inf when fewer than k points are valid).  Synchronises `stream`.
  */

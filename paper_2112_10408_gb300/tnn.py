@@ -273,17 +273,18 @@ def tnn_segment_lower_bounds(index: Index, q=None, lag: float = 0.0) -> torch.Te
 
 
 def tnn_knn_work(index: Index, k: int, d2: torch.Tensor, lag: float = 0.0, q=None):
-    """(segment bounds needed, member points needed) summed over the queries."""
+    """(segment bounds, member points, key bounds) any exact search over the
+    index must evaluate, summed over the queries."""
     if q is not None:
         q = _dev(q, torch.float32, (4,), "q")
         m = q.shape[0]
     else:
         m = index.n_points
     _dev(d2, torch.float32, (k,), "d2")
-    out = (ctypes.c_uint64 * 2)()
+    out = (ctypes.c_uint64 * 3)()
     _check(_L().tnn_knn_work(index.handle, _ptr(q), m, int(k), float(lag), _ptr(d2), out,
                              _stream()))
-    return int(out[0]), int(out[1])
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def tnn_profile_enable(on: bool = True):
