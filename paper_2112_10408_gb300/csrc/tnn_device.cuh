@@ -13,25 +13,30 @@
 
 static const unsigned long long SENT = (0x7f800000ull << 32) | 0xffffffffull;
 
-__host__ __device__ inline size_t smem_per_warp(int L_max, int kseg_max, bool brute)
+// Shared-memory layout per warp of the tile kernels.
+enum { SMEM_SWEEP = 0, SMEM_LINEAR = 1, SMEM_GRID = 2 };
+
+__host__ __device__ inline size_t smem_per_warp(int L_max, int kseg_max, int mode)
 {
-    // candidate lists [L_max][32] keys, then: TNN: segment chunk [32][4]
-    // float4 | points [kseg_max] float4 | seed union [TNN_UCAP] int |
-    // pass-1 list [TNN_WCAP] int; linear search: points [32] float4 |
-    // indices [32] int.  The FP64 settlement scratch ([CMAX][32] u64 +
-    // [CMAX][32] int) reuses that area.
+    // candidate lists [L_max][32] keys, then: sweep and grid: segment chunk
+    // [32][4] float4 | points [kseg_max] float4 | seed union [TNN_UCAP] int
+    // (| pass-1 list [TNN_WCAP] int for the sweep); linear search: points
+    // [32] float4 | indices [32] int.  The FP64 settlement scratch
+    // ([CMAX][32] u64 + [CMAX][32] int) reuses that area.
     size_t base = (size_t)L_max * 32 * 8;
-    size_t rest = brute ? (32 * 16 + 32 * 4)
-                        : (2048 + (size_t)kseg_max * 16 + 4 * (TNN_UCAP + TNN_WCAP));
+    size_t rest = mode == SMEM_LINEAR
+                      ? (32 * 16 + 32 * 4)
+                      : (2048 + (size_t)kseg_max * 16 +
+                         4 * (TNN_UCAP + (mode == SMEM_SWEEP ? TNN_WCAP : 0)));
     size_t cl = (size_t)CMAX * 32 * 12;
     if (rest < cl)
         rest = cl;
     return (base + rest + 15) & ~(size_t)15;
 }
 
-size_t tnn_search_smem_per_warp(int L_max, int kseg_max, bool brute)
+size_t tnn_search_smem_per_warp(int L_max, int kseg_max, int mode)
 {
-    return smem_per_warp(L_max, kseg_max, brute);
+    return smem_per_warp(L_max, kseg_max, mode);
 }
 
 // ----------------------------------------------------------------- helpers

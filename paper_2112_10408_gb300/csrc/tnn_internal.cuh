@@ -138,7 +138,7 @@ tnn_status tnn_fill_window(const tnn_index *ix, const float *d_q, int64_t m,
                            float *d_d2, KnnWin *w);
 tnn_status tnn_launch_search(const KnnLaunch &L, bool brute,
                              cudaStream_t stream);
-size_t tnn_search_smem_per_warp(int L_max, int kseg_max, bool brute);
+size_t tnn_search_smem_per_warp(int L_max, int kseg_max, int mode);
 
 #define TNN_WARPS_PER_CTA 4
 #define TNN_TILE 32

@@ -189,9 +189,11 @@ tnn_status tnn_launch_search(const KnnLaunch &L, bool brute, cudaStream_t st)
     tnn_status s = device_setup();
     if (s != TNN_OK)
         return s;
-    const size_t smem = smem_per_warp(L.L_max, L.kseg_max, brute) * TNN_WARPS_PER_CTA;
     int nb = 0;
     const bool sweep = (L.w0.flags & TNN_FLAG_SWEEP) != 0;
+    const size_t smem = smem_per_warp(L.L_max, L.kseg_max,
+                                      brute ? SMEM_LINEAR : sweep ? SMEM_SWEEP : SMEM_GRID) *
+                        TNN_WARPS_PER_CTA;
     const void *kern = brute ? (const void *)k_linear_search
                              : sweep ? (const void *)k_tnn_search : (const void *)k_tnn_grid_search;
     TNN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, TNN_WARPS_PER_CTA * 32, smem));

@@ -12,7 +12,7 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
-    const size_t pw = smem_per_warp(L.L_max, L.kseg_max, true);
+    const size_t pw = smem_per_warp(L.L_max, L.kseg_max, SMEM_LINEAR);
     unsigned char *ws = smem + (threadIdx.x >> 5) * pw;
     unsigned long long *K = (unsigned long long *)ws + lane;
     unsigned char *rest = ws + (size_t)L.L_max * 256;
