@@ -268,27 +268,39 @@ def run_ours(a):
                                     "ops_per_lb": OPS_PER_LB, "ops_per_pair": OPS_PER_PAIR,
                                     "ops_per_key": OPS_PER_KEY}}
 
-    # comparator: linear search on the same queries
+    # comparator: linear search on the same queries, distance tiles on the
+    # tensor cores (default) and on the CUDA cores (ffma)
     comparator = None
     if a.comparator_steps > 0:
         bi = torch.empty_like(idx)
         bd = torch.empty_like(d2)
-        tnn.tnn_knn_bruteforce(ix, k, 0.0, out=(bi, bd))
-        torch.cuda.synchronize()
-        cms = []
-        for _ in range(a.comparator_steps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            tnn.tnn_knn_bruteforce(ix, k, 0.0, out=(bi, bd))
-            e1.record()
+        comparator = {}
+        for name, ffma in (("tensor_core", False), ("cuda_core", True)):
+            tnn.tnn_knn_bruteforce(ix, k, 0.0, out=(bi, bd), ffma=ffma)
             torch.cuda.synchronize()
-            cms.append(e0.elapsed_time(e1))
-        same = bool(torch.equal(bi, idx))
-        cmean = sum(cms) / len(cms)
-        comparator = {"impl": "linear search (k_linear_search, same FP32 ranking + FP64 settlement)",
-                      "value": m / (cmean / 1e3), "unit": UNIT, "ms_per_step": cmean,
-                      "tnn_speedup": cmean / ms_step, "identical_neighbours": same}
+            _, _, cst = tnn.tnn_knn_bruteforce(ix, k, 0.0, out=(bi, bd), ffma=ffma, stats=True)
+            cms = []
+            for _ in range(a.comparator_steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                tnn.tnn_knn_bruteforce(ix, k, 0.0, out=(bi, bd), ffma=ffma)
+                e1.record()
+                torch.cuda.synchronize()
+                cms.append(e0.elapsed_time(e1))
+            cmean = sum(cms) / len(cms)
+            ent = {"kernel": "k_linear_search" if ffma else "k_linear_tc",
+                   "value": m / (cmean / 1e3), "unit": UNIT, "ms_per_step": cmean,
+                   "tnn_speedup": cmean / ms_step, "identical_neighbours": bool(torch.equal(bi, idx)),
+                   "pairs": cst["pairs"], "rescored": cst["lb_evals"]}
+            if not ffma:
+                # 3 TF32 MMAs of K = 8 per 128 x 128 tile: 48 flops per pair
+                tf = 48.0 * cst["pairs"] / (cmean / 1e3) / 1e12
+                tf32_peak = peaks.get("bf16_tflops", 1900.0) * (1.1 / 2.25)
+                ent["tensor"] = {"achieved_tflops": tf, "tf32_peak_tflops": tf32_peak,
+                                 "frac": tf / tf32_peak,
+                                 "peak_note": "measured bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"}
+            comparator[name] = ent
 
     # end to end through the C ABI: pinned host points -> build -> search ->
     # pinned host neighbour lists

@@ -46,7 +46,7 @@ typedef enum {
     TNN_ERR_INVALID_ARG = 1, /* bad size, pointer, parameter or input value */
     TNN_ERR_OOM = 2,         /* device allocation failed                    */
     TNN_ERR_CUDA = 3,        /* a CUDA runtime call or kernel failed        */
-    TNN_ERR_TIMEOUT = 4,     /* reserved: a bounded device wait expired     */
+    TNN_ERR_TIMEOUT = 4,     /* a bounded device wait expired (1 s)         */
     TNN_ERR_UNSUPPORTED = 5  /* the device is not sm_103 or lacks a feature */
 } tnn_status;
 
@@ -120,7 +120,11 @@ enum {
        instead of through the time-bucketed spatial grid of the index.  Both
        give the same exact result; the grid skips whole groups of segments
        and is the default. */
-    TNN_FLAG_SWEEP = 2
+    TNN_FLAG_SWEEP = 2,
+    /* tnn_knn_bruteforce only: compute the pair distances on the CUDA cores
+       (direct differences) instead of screening them with the tensor-core
+       distance matrix.  Same exact result. */
+    TNN_FLAG_FFMA = 4
 };
 
 typedef struct {
@@ -165,8 +169,10 @@ typedef struct {
  *   d_q     [m][4] float queries (device), or NULL for self-query: every
  *           indexed point is a query (m must equal n_points).
  *   d_idx   [m][k] int32 out, d_d2 [m][k] float out (device).
- *   h_stats optional; when non-NULL the call SYNCHRONISES `stream` and
- *           fills the counters.
+ *   h_stats optional; when non-NULL the call SYNCHRONISES `stream`, fills
+ *           the counters and reports what the kernels flagged: a device
+ *           wait that timed out (TNN_ERR_TIMEOUT; the outputs are then
+ *           incomplete) or an internal list overflow (TNN_ERR_CUDA).
  * Device scratch (a few bytes per query) is taken from the stream-ordered
  * allocator and released on the stream.
  */
@@ -179,6 +185,13 @@ tnn_status tnn_knn(const tnn_index *index, const float *d_q, int64_t m,
  * Table 1 "Linear search"; Table 3 "Lin. Search") over the time-ordered
  * copy of the points kept in the index, with the same FP32 ranking and FP64
  * settlement.  Arguments as tnn_knn (seed_* fields are ignored).
+ * By default the distance matrix of 128 queries x 128 points is formed on
+ * the tensor cores (tcgen05, expansion |q|^2 + |p|^2 - 2 q.p, split TF32
+ * operands) and used only to screen out points: every point within the
+ * current k-th candidate plus a certified margin is scored again with the
+ * exact FP32 distance, so the result is the one tnn_knn returns.
+ * TNN_FLAG_FFMA computes every distance directly on the CUDA cores.
+ * counters: lb_evals = points scored again, pairs = point pairs screened.
  */
 tnn_status tnn_knn_bruteforce(const tnn_index *index, const float *d_q,
                               int64_t m, const tnn_knn_params *params,

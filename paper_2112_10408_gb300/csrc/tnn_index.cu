@@ -368,6 +368,21 @@ __global__ void k_seg_extremes(const float4 *__restrict__ seg, int S,
     atomicAdd(dur_sum, (double)u.w - (double)a.w);
 }
 
+// Bounding box of the raw points (x, y, z, t): ordered min/max per axis.
+__global__ void k_point_bbox(const float4 *__restrict__ p, int n, unsigned int *ord)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const float4 v = p[i];
+    const float c[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        atomicMin(ord + 2 * d, f2ord(c[d]));
+        atomicMax(ord + 2 * d + 1, f2ord(c[d]));
+    }
+}
+
 struct GridBuild {
     float x0, y0, cell, inv_cell, t0, dt, inv_dt;
     int nx, ny, ncell, nb;
@@ -393,7 +408,7 @@ __global__ void k_grid_keys(const float4 *__restrict__ seg, int S, GridBuild g,
     const int key = bk * g.ncell + cy * g.nx + cx;
     keys[p] = ((unsigned long long)(unsigned)key << 32) | (unsigned)p;
     // every cylinder point is within |AB|/2 + r of the midpoint
-    const double ax = a.x, ay = a.y, az = a.z, bx = b.x, by = b.y, bz = b.z;
+    const double ax = a.x, ay = a.y, bx = b.x, by = b.y, bz = b.z;
     const double half = 0.5 * sqrt(bx * bx + by * by + bz * bz) + (double)b.w;
     const double Mx = ax + 0.5 * bx, My = ay + 0.5 * by;
     const double rx0 = (double)g.x0 + cx * (double)g.cell, rx1 = rx0 + g.cell;
@@ -505,11 +520,29 @@ static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
     TNN_CUDA_TRY(cudaMemsetAsync((char *)sb.p + 32, 0, 8, st));
     k_seg_extremes<<<(S + tb - 1) / tb, tb, 0, st>>>(ix->seg, S, (unsigned int *)sb.p,
                                                     (double *)((char *)sb.p + 32));
-    unsigned int h[8];
+    DevBuf bb;
+    TNN_CUDA_TRY(cudaMalloc(&bb.p, 32));
+    const unsigned int binit[8] = {0xffffffffu, 0u, 0xffffffffu, 0u, 0xffffffffu, 0u, 0xffffffffu, 0u};
+    TNN_CUDA_TRY(cudaMemcpyAsync(bb.p, binit, sizeof(binit), cudaMemcpyHostToDevice, st));
+    k_point_bbox<<<(int)((ix->n + tb - 1) / tb), tb, 0, st>>>(ix->pts, (int)ix->n, (unsigned int *)bb.p);
+    unsigned int h[8], hb[8];
     double dur = 0.0;
     TNN_CUDA_TRY(cudaMemcpyAsync(h, sb.p, sizeof(h), cudaMemcpyDeviceToHost, st));
     TNN_CUDA_TRY(cudaMemcpyAsync(&dur, (char *)sb.p + 32, 8, cudaMemcpyDeviceToHost, st));
+    TNN_CUDA_TRY(cudaMemcpyAsync(hb, bb.p, sizeof(hb), cudaMemcpyDeviceToHost, st));
     TNN_CUDA_TRY(cudaStreamSynchronize(st));
+    {
+        // centre of the point bounding box, and a bound on the scaled distance
+        // of any point from it (used by the tensor-core linear search)
+        double r2 = 0.0;
+        for (int d = 0; d < 4; ++d) {
+            const double lo = host_ord2f(hb[2 * d]), hi = host_ord2f(hb[2 * d + 1]);
+            ix->center[d] = (float)(0.5 * (lo + hi));
+            const double half = 0.5 * (hi - lo) + fabs((double)ix->center[d]) * 1e-6;
+            r2 += ix->sigma[d] * half * half;
+        }
+        ix->R4 = (float)(sqrt(r2) * (1.0 + 1e-6) + 1e-6);
+    }
     const double xmn = host_ord2f(h[0]), xmx = host_ord2f(h[1]);
     const double ymn = host_ord2f(h[2]), ymx = host_ord2f(h[3]);
     const double tmn = host_ord2f(h[4]), tmx = host_ord2f(h[5]);

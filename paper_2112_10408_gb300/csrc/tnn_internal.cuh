@@ -73,6 +73,8 @@ struct tnn_index {
     GridDesc grid;   // views of the arrays below
     int32_t *g_off, *g_ids;
     float *g_ext, *g_tB, *g_bpm;
+    float center[4]; // middle of the bounding box of the points (x, y, z, t)
+    float R4;        // bound on |sqrt(sigma) (p - center)| over the points
 };
 
 // Parameters of one independent k-NN problem, read by the search kernels.
@@ -89,6 +91,8 @@ struct KnnWin {
     int64_t m;
     int64_t tile_begin; // first global tile of this window
     GridDesc grid;
+    float center[4];
+    float R4;
     double sigd[4];
     double lag;
     float sig[4];

@@ -60,6 +60,7 @@
 #include "tnn_grid.cuh"
 #include "tnn_linear.cuh"
 #include "tnn_fallback.cuh"
+#include "tnn_linear_tc.cuh"
 
 // ------------------------------------------------------ lower-bound export
 
@@ -119,6 +120,7 @@ static tnn_status device_setup()
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_tnn_search, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_tnn_grid_search, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_linear_search, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
+        TNN_CUDA_TRY(cudaFuncSetAttribute(k_linear_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_tnn_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_fallback_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
         attrs = true;
@@ -157,6 +159,9 @@ tnn_status tnn_fill_window(const tnn_index *ix, const float *d_q, int64_t m,
     w->pts_t = ix->pts_t;
     w->idx_t = ix->idx_t;
     w->grid = ix->grid;
+    for (int i = 0; i < 4; ++i)
+        w->center[i] = ix->center[i];
+    w->R4 = ix->R4;
     w->q = d_q ? (const float4 *)d_q : ix->pts;
     w->out_idx = d_idx;
     w->out_d2 = d_d2;
@@ -184,6 +189,28 @@ tnn_status tnn_fill_window(const tnn_index *ix, const float *d_q, int64_t m,
     return TNN_OK;
 }
 
+// The per-query kernels that finish the tile kernel's deferred and
+// unsettled queries; the measured interval covers the whole search.
+static tnn_status finish_search(const KnnLaunch &L, cudaStream_t st, bool prof,
+                                std::pair<cudaEvent_t, cudaEvent_t> &pr)
+{
+    {
+        const size_t wsm = wq_smem_per_warp() * TNN_WARPS_PER_CTA;
+        int nbw = 0;
+        TNN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbw, k_tnn_warp, TNN_WARPS_PER_CTA * 32, wsm));
+        k_tnn_warp<<<(unsigned)(std::max(nbw, 1) * g_num_sms), TNN_WARPS_PER_CTA * 32, wsm, st>>>(L);
+    }
+    TNN_CUDA_TRY(cudaGetLastError());
+    k_fallback_exact<<<(unsigned)g_num_sms, TNN_WARPS_PER_CTA * 32,
+                       fb_exact_smem_per_warp(L.L_max) * TNN_WARPS_PER_CTA, st>>>(L);
+    TNN_CUDA_TRY(cudaGetLastError());
+    if (prof) {
+        TNN_CUDA_TRY(cudaEventRecord(pr.second, st));
+        g_prof_ev.push_back(pr);
+    }
+    return TNN_OK;
+}
+
 tnn_status tnn_launch_search(const KnnLaunch &L, bool brute, cudaStream_t st)
 {
     tnn_status s = device_setup();
@@ -191,6 +218,33 @@ tnn_status tnn_launch_search(const KnnLaunch &L, bool brute, cudaStream_t st)
         return s;
     int nb = 0;
     const bool sweep = (L.w0.flags & TNN_FLAG_SWEEP) != 0;
+    // Tensor-core linear search: one window, 128 queries per CTA; at least
+    // 48 KB of shared memory keeps at most 4 CTAs (4 x 128 TMEM columns) on
+    // an SM, so every TMEM allocation is granted at once.
+    const bool tc = brute && (L.w0.flags & TNN_FLAG_FFMA) == 0 && L.nwin <= 1 &&
+                    tc_smem_bytes(L.L_max) <= (size_t)227 * 1024;
+    if (tc) {
+        const size_t smem = std::max<size_t>(tc_smem_bytes(L.L_max), 48 * 1024);
+        TNN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_linear_tc, TC_Q, smem));
+        if (nb < 1) {
+            tnn_set_error("tensor-core search kernel does not fit on an SM (%zu B shared memory)", smem);
+            return TNN_ERR_UNSUPPORTED;
+        }
+        KnnLaunch Lt = L;
+        Lt.total_tiles = (L.w0.m + TC_Q - 1) / TC_Q;
+        long long grid = std::min<long long>(Lt.total_tiles, (long long)std::min(nb, 4) * g_num_sms);
+        if (grid < 1)
+            grid = 1;
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cap);
+        const bool prof = g_prof_on && cap == cudaStreamCaptureStatusNone;
+        std::pair<cudaEvent_t, cudaEvent_t> pr;
+        if (prof)
+            TNN_CUDA_TRY(prof_begin(st, &pr));
+        k_linear_tc<<<(unsigned)grid, TC_Q, smem, st>>>(Lt);
+        TNN_CUDA_TRY(cudaGetLastError());
+        return finish_search(L, st, prof, pr);
+    }
     const size_t smem = smem_per_warp(L.L_max, L.kseg_max,
                                       brute ? SMEM_LINEAR : sweep ? SMEM_SWEEP : SMEM_GRID) *
                         TNN_WARPS_PER_CTA;
@@ -218,23 +272,7 @@ tnn_status tnn_launch_search(const KnnLaunch &L, bool brute, cudaStream_t st)
     else
         k_tnn_grid_search<<<(unsigned)grid, TNN_WARPS_PER_CTA * 32, smem, st>>>(L);
     TNN_CUDA_TRY(cudaGetLastError());
-    {
-        const size_t wsm = wq_smem_per_warp() * TNN_WARPS_PER_CTA;
-        int nbw = 0;
-        TNN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbw, k_tnn_warp, TNN_WARPS_PER_CTA * 32, wsm));
-        k_tnn_warp<<<(unsigned)(std::max(nbw, 1) * g_num_sms), TNN_WARPS_PER_CTA * 32, wsm, st>>>(L);
-    }
-    TNN_CUDA_TRY(cudaGetLastError());
-    k_fallback_exact<<<(unsigned)g_num_sms, TNN_WARPS_PER_CTA * 32,
-                       fb_exact_smem_per_warp(L.L_max) * TNN_WARPS_PER_CTA, st>>>(L);
-    TNN_CUDA_TRY(cudaGetLastError());
-    // the measured interval covers the whole search: the tile kernel and the
-    // per-query kernels that finish its deferred and unsettled queries
-    if (prof) {
-        TNN_CUDA_TRY(cudaEventRecord(pr.second, st));
-        g_prof_ev.push_back(pr);
-    }
-    return TNN_OK;
+    return finish_search(L, st, prof, pr);
 }
 
 static tnn_status run_single(const tnn_index *ix, const float *d_q, int64_t m,
@@ -286,6 +324,13 @@ static tnn_status run_single(const tnn_index *ix, const float *d_q, int64_t m,
             h_stats->fp64_rechecks = hs.stats[4];
             h_stats->warp_queries = hs.stats[5];
             h_stats->exact_queries = hs.stats[6];
+            if (hs.status & 4u) {
+                tnn_set_error("a device wait of the tensor-core search timed out");
+                s = TNN_ERR_TIMEOUT;
+            } else if (hs.status) {
+                tnn_set_error("a device list overflowed (status %u)", hs.status);
+                s = TNN_ERR_CUDA;
+            }
         }
     }
     cudaFreeAsync(buf, st);

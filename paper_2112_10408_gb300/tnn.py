@@ -60,6 +60,7 @@ class tnn_adamw_params(ctypes.Structure):
 
 TNN_FLAG_EXACT_D2 = 1
 TNN_FLAG_SWEEP = 2
+TNN_FLAG_FFMA = 4
 N_FEAT = 6
 
 # (name, restype, argtypes)
@@ -214,14 +215,15 @@ def tnn_index_export(index: Index):
 
 def make_knn_params(k: int, lag: float = 0.0, seed_segments: int = 0, seed_window: int = 0,
                     extra: int = 0, exact_d2: bool = False, sweep: bool = False,
-                    defer_cells: float = 0.0) -> tnn_knn_params:
+                    defer_cells: float = 0.0, ffma: bool = False) -> tnn_knn_params:
     p = tnn_knn_params()
     p.k = int(k)
     p.lag = float(lag)
     p.seed_segments = int(seed_segments)
     p.seed_window = int(seed_window)
     p.extra = int(extra)
-    p.flags = (TNN_FLAG_EXACT_D2 if exact_d2 else 0) | (TNN_FLAG_SWEEP if sweep else 0)
+    p.flags = ((TNN_FLAG_EXACT_D2 if exact_d2 else 0) | (TNN_FLAG_SWEEP if sweep else 0)
+               | (TNN_FLAG_FFMA if ffma else 0))
     p.defer_cells = float(defer_cells)
     return p
 
@@ -256,7 +258,8 @@ def tnn_knn(index: Index, k: int, lag: float = 0.0, q=None, stats: bool = False,
 
 def tnn_knn_bruteforce(index: Index, k: int, lag: float = 0.0, q=None, stats: bool = False,
                        out=None, **kw):
-    """The same k-NN by linear search (the comparator)."""
+    """The same k-NN by linear search (the comparator): the distance matrix
+    on the tensor cores, or on the CUDA cores with ``ffma=True``."""
     return _knn_call(_L().tnn_knn_bruteforce, index, k, lag, q, stats, out, **kw)
 
 

@@ -278,6 +278,9 @@ def test_precision_config_sampled_queries():
     oi, od = oracle.knn(wl.xyzt, 32, SIG, qsel=q)
     assert_knn_equal(ti.cpu().numpy()[q], td.cpu().numpy()[q], oi, od, what="tnn precision")
     assert st["exact_queries"] <= wl.n * 1e-4
+    qd = torch.from_numpy(wl.xyzt[q]).cuda()
+    bi, bd = tnn.tnn_knn_bruteforce(ix, 32, 0.0, q=qd)
+    assert_knn_equal(bi.cpu().numpy(), bd.cpu().numpy(), oi, od, what="linear precision")
 
 
 def test_batched_windows_match_oracle():
@@ -306,3 +309,40 @@ def test_autotune_returns_valid_knobs():
     q = synth.query_sample(wl.n, 500)
     oi, od = oracle.knn(wl.xyzt, 32, SIG, qsel=q)
     assert_knn_equal(ti.cpu().numpy()[q], td.cpu().numpy()[q], oi, od, what="autotuned")
+
+
+@pytest.mark.parametrize("k,extra", [(1, 2), (32, 4), (64, 32)])
+def test_linear_search_tensor_core_and_cuda_core_paths(k, extra):
+    # The tensor-core screen (128 x 128 distance tiles) and the direct FP32
+    # distances must give the oracle's answer; 3,071 rows leave a ragged
+    # 128-query tile and a ragged 128-point chunk.
+    for wl in (synth.flights(37, 83, seed=500 + k, n_routes=4),
+               synth.random_points(3071, 20, seed=k),
+               synth.smoothed_random_walks(19, 97, seed=k)):
+        ix = _index(wl, 16)
+        oi, od = oracle.knn(wl.xyzt, k, SIG)
+        for ffma in (False, True):
+            bi, bd, st = tnn.tnn_knn_bruteforce(ix, k, 0.0, extra=extra, ffma=ffma, stats=True)
+            assert_knn_equal(bi.cpu().numpy(), bd.cpu().numpy(), oi, od,
+                             what=f"linear {wl.name} k={k} ffma={ffma}")
+            assert st["queries"] == wl.n
+
+
+def test_linear_tensor_core_far_and_large_coordinates():
+    # Queries far outside the data (a large |q - centre| widens the screening
+    # margin) and coordinates near 1e4 km, where FP32 spacing is coarse.
+    wl = synth.flights(40, 64, seed=9, n_routes=5)
+    xyzt = wl.xyzt.copy()
+    xyzt[:, 0] += 9000.0
+    xyzt[:, 1] -= 7000.0
+    ix = tnn.tnn_build_segments(torch.from_numpy(xyzt).cuda(), wl.traj_off, SIG, 10)
+    rng = np.random.default_rng(5)
+    q = xyzt[rng.choice(len(xyzt), 400, replace=False)].copy()
+    q[:100, :2] += rng.normal(0, 2000.0, size=(100, 2)).astype(np.float32)
+    q[100:150, 3] = -5.0  # nothing causal for a whole run of queries
+    q[150:200, 3] = 1e6
+    qd = torch.from_numpy(q).cuda()
+    oi, od = oracle.knn(xyzt, 10, SIG, lag=3.0, queries=q)
+    for ffma in (False, True):
+        bi, bd = tnn.tnn_knn_bruteforce(ix, 10, 3.0, q=qd, ffma=ffma)
+        assert_knn_equal(bi.cpu().numpy(), bd.cpu().numpy(), oi, od, what=f"far ffma={ffma}")
