@@ -187,26 +187,6 @@ __device__ __forceinline__ unsigned long long lane_push(unsigned long long *K, i
     return nv == L ? K[(L - 1) * 32] : SENT;
 }
 
-// lane_push for a list whose slots are `stride` keys apart (one column per
-// thread of a block of `stride` threads).
-__device__ __forceinline__ unsigned long long lane_push_s(unsigned long long *K, int L, int &nv,
-                                                          unsigned long long key, int stride)
-{
-    int i = nv < L ? nv : L - 1;
-#pragma unroll 1
-    while (i > 0) {
-        const unsigned long long pv = K[(i - 1) * stride];
-        if (pv < key)
-            break;
-        K[i * stride] = pv;
-        --i;
-    }
-    K[i * stride] = key;
-    if (nv < L)
-        ++nv;
-    return nv == L ? K[(L - 1) * stride] : SENT;
-}
-
 // Points of one segment held in registers (lane j keeps members j and
 // j + 32) so that the global load of the next segment overlaps the scan of
 // the current one.

@@ -248,7 +248,7 @@ __global__ void k_bitonic_global(unsigned long long *keys, int j, int k)
     }
 }
 
-static int next_pow2_sort(int64_t n)
+int tnn_next_pow2_sort(int64_t n)
 {
     int64_t p = BS_BLOCK;
     while (p < n)
@@ -256,7 +256,7 @@ static int next_pow2_sort(int64_t n)
     return (int)p;
 }
 
-static void bitonic_sort(unsigned long long *keys, int n2, cudaStream_t st)
+void tnn_bitonic_sort(unsigned long long *keys, int n2, cudaStream_t st)
 {
     k_bitonic_block<<<n2 / BS_BLOCK, 1024, 0, st>>>(keys);
     for (int k = 2 * BS_BLOCK; k <= n2; k <<= 1) {
@@ -531,17 +531,11 @@ static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
     TNN_CUDA_TRY(cudaMemcpyAsync(&dur, (char *)sb.p + 32, 8, cudaMemcpyDeviceToHost, st));
     TNN_CUDA_TRY(cudaMemcpyAsync(hb, bb.p, sizeof(hb), cudaMemcpyDeviceToHost, st));
     TNN_CUDA_TRY(cudaStreamSynchronize(st));
-    {
-        // centre of the point bounding box, and a bound on the scaled distance
-        // of any point from it (used by the tensor-core linear search)
-        double r2 = 0.0;
-        for (int d = 0; d < 4; ++d) {
-            const double lo = host_ord2f(hb[2 * d]), hi = host_ord2f(hb[2 * d + 1]);
-            ix->center[d] = (float)(0.5 * (lo + hi));
-            const double half = 0.5 * (hi - lo) + fabs((double)ix->center[d]) * 1e-6;
-            r2 += ix->sigma[d] * half * half;
-        }
-        ix->R4 = (float)(sqrt(r2) * (1.0 + 1e-6) + 1e-6);
+    // bounding box of the points (orders the queries of the tensor-core
+    // linear search)
+    for (int d = 0; d < 4; ++d) {
+        ix->bb_lo[d] = (float)host_ord2f(hb[2 * d]);
+        ix->bb_hi[d] = (float)host_ord2f(hb[2 * d + 1]);
     }
     const double xmn = host_ord2f(h[0]), xmx = host_ord2f(h[1]);
     const double ymn = host_ord2f(h[2]), ymx = host_ord2f(h[3]);
@@ -591,7 +585,7 @@ static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
     k_grid_keys<<<(S + tb - 1) / tb, tb, 0, st>>>(ix->seg, S, g, keys, (unsigned int *)ix->g_ext,
                                                  (unsigned int *)ix->g_tB,
                                                  (unsigned int *)ix->g_bpm);
-    bitonic_sort(keys, s2, st);
+    tnn_bitonic_sort(keys, s2, st);
     k_grid_offsets<<<(nkeys + 1 + tb - 1) / tb, tb, 0, st>>>(keys, S, nkeys, ix->g_off);
     k_grid_ids<<<(S + tb - 1) / tb, tb, 0, st>>>(keys, S, ix->g_ids);
     k_decode_ord<<<(nkeys + tb - 1) / tb, tb, 0, st>>>((unsigned int *)ix->g_tB, nkeys);
@@ -678,8 +672,8 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
     for (int i = 0; i < 3; ++i)
         ix->ssq_f[i] = (float)sqrt(params->sigma[i]);
 
-    const int n2 = next_pow2_sort(n);
-    const int s2 = next_pow2_sort(S);
+    const int n2 = tnn_next_pow2_sort(n);
+    const int s2 = tnn_next_pow2_sort(S);
     DevBuf toff_d, soff_d, rec_d, keys_d, flags_d;
     cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, bytes)                                                     \
@@ -690,7 +684,7 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
     ALLOC(ix->segTA, sizeof(float) * S);
     ALLOC(ix->segPM, sizeof(float) * S);
     ALLOC(ix->pts_t, sizeof(float4) * n);
-    ALLOC(ix->idx_t, sizeof(int32_t) * n);
+    ALLOC(ix->idx_t, sizeof(int32_t) * (n + 4)); // 4 entries of padding for 16-byte copies
     ALLOC(toff_d.p, sizeof(int32_t) * (n_traj + 1));
     ALLOC(soff_d.p, sizeof(int32_t) * (n_traj + 1));
     ALLOC(rec_d.p, sizeof(float4) * 4 * S);
@@ -729,7 +723,7 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
         sqrt(params->sigma[0]), sqrt(params->sigma[1]), sqrt(params->sigma[2]),
         (float4 *)rec_d.p, keys, flag + 2);
     k_fill<<<(s2 - Si + tb - 1) / tb + 1, tb, 0, st>>>(keys, Si, s2);
-    bitonic_sort(keys, s2, st);
+    tnn_bitonic_sort(keys, s2, st);
     k_gather_segments<<<(Si + tb - 1) / tb, tb, 0, st>>>(keys, (const float4 *)rec_d.p,
                                                          Si, ix->seg, ix->segTA);
     k_prefix_max_tB<<<1, 1024, 0, st>>>(ix->seg, Si, ix->segPM);
@@ -741,11 +735,13 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
         }
     }
     k_time_keys<<<(n2 + tb - 1) / tb, tb, 0, st>>>(ix->pts, ni, keys, n2);
-    bitonic_sort(keys, n2, st);
+    tnn_bitonic_sort(keys, n2, st);
     k_gather_points<<<(ni + tb - 1) / tb, tb, 0, st>>>(keys, ix->pts, ni, ix->pts_t,
                                                        ix->idx_t);
     unsigned int hflag[4] = {0, 0, 0, 0};
     e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(ix->idx_t + n, 0, 4 * sizeof(int32_t), st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(hflag, flag, sizeof(hflag), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)

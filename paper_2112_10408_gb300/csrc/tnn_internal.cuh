@@ -73,8 +73,7 @@ struct tnn_index {
     GridDesc grid;   // views of the arrays below
     int32_t *g_off, *g_ids;
     float *g_ext, *g_tB, *g_bpm;
-    float center[4]; // middle of the bounding box of the points (x, y, z, t)
-    float R4;        // bound on |sqrt(sigma) (p - center)| over the points
+    float bb_lo[4], bb_hi[4]; // bounding box of the points (x, y, z, t)
 };
 
 // Parameters of one independent k-NN problem, read by the search kernels.
@@ -91,8 +90,7 @@ struct KnnWin {
     int64_t m;
     int64_t tile_begin; // first global tile of this window
     GridDesc grid;
-    float center[4];
-    float R4;
+    float bb_lo[4], bb_hi[4]; // bounding box of the points
     double sigd[4];
     double lag;
     float sig[4];
@@ -134,7 +132,14 @@ struct KnnLaunch {
     int2 *fb_list;        // (window, query) for the FP32 warp scan
     int2 *fb_list3;       // (window, query) for the exact FP64 warp scan
     int64_t fb_cap;       // capacity of each list
+    const unsigned long long *qorder; // tensor-core linear search: sorted
+                                      // (space-time key << 32 | query row)
 };
+
+// Ascending sort of n2 (a power of two, >= 2048) 64-bit keys in place
+// (tnn_index.cu); tnn_next_pow2_sort gives the n2 for n keys.
+int tnn_next_pow2_sort(int64_t n);
+void tnn_bitonic_sort(unsigned long long *keys, int n2, cudaStream_t st);
 
 // Launch helpers (tnn_knn.cu).
 tnn_status tnn_fill_window(const tnn_index *ix, const float *d_q, int64_t m,

@@ -80,6 +80,7 @@ __global__ void k_segment_lb(const __grid_constant__ KnnWin W, float *out)
 // -------------------------------------------------------------- host side
 
 static int g_num_sms = 0;
+static int g_smem_per_sm = 0; // shared memory of one SM (bytes)
 
 // ---- kernel timing for measurement tools (tnn_profile_*)
 static bool g_prof_on = false;
@@ -114,6 +115,7 @@ static tnn_status device_setup()
         return TNN_ERR_UNSUPPORTED;
     }
     g_num_sms = prop.multiProcessorCount;
+    g_smem_per_sm = (int)prop.sharedMemPerMultiprocessor;
     static bool attrs = false;
     if (!attrs) {
         const int maxs = 227 * 1024;
@@ -159,9 +161,10 @@ tnn_status tnn_fill_window(const tnn_index *ix, const float *d_q, int64_t m,
     w->pts_t = ix->pts_t;
     w->idx_t = ix->idx_t;
     w->grid = ix->grid;
-    for (int i = 0; i < 4; ++i)
-        w->center[i] = ix->center[i];
-    w->R4 = ix->R4;
+    for (int i = 0; i < 4; ++i) {
+        w->bb_lo[i] = ix->bb_lo[i];
+        w->bb_hi[i] = ix->bb_hi[i];
+    }
     w->q = d_q ? (const float4 *)d_q : ix->pts;
     w->out_idx = d_idx;
     w->out_d2 = d_d2;
@@ -187,6 +190,37 @@ tnn_status tnn_fill_window(const tnn_index *ix, const float *d_q, int64_t m,
     }
     w->flags = p->flags;
     return TNN_OK;
+}
+
+// Space-time order of the queries for the tensor-core linear search: a
+// Morton key of (x, y, t), 10 bits each over the points' bounding box, above
+// the query row; rows [m, n2) are padding that sorts last.
+__device__ __forceinline__ uint32_t spread3(uint32_t v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__global__ void k_query_order_keys(const float4 *__restrict__ q, int64_t m, int64_t n2,
+                                   float4 lo, float4 sc, unsigned long long *__restrict__ keys)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n2)
+        return;
+    if (i >= m) {
+        keys[i] = ~0ull;
+        return;
+    }
+    const float4 v = q[i];
+    const uint32_t ix = (uint32_t)fminf(fmaxf((v.x - lo.x) * sc.x, 0.0f), 1023.0f);
+    const uint32_t iy = (uint32_t)fminf(fmaxf((v.y - lo.y) * sc.y, 0.0f), 1023.0f);
+    const uint32_t it = (uint32_t)fminf(fmaxf((v.w - lo.w) * sc.w, 0.0f), 1023.0f);
+    const uint32_t code = spread3(ix) | (spread3(iy) << 1) | (spread3(it) << 2);
+    keys[i] = ((unsigned long long)code << 32) | (unsigned long long)i;
 }
 
 // The per-query kernels that finish the tile kernel's deferred and
@@ -218,21 +252,23 @@ tnn_status tnn_launch_search(const KnnLaunch &L, bool brute, cudaStream_t st)
         return s;
     int nb = 0;
     const bool sweep = (L.w0.flags & TNN_FLAG_SWEEP) != 0;
-    // Tensor-core linear search: one window, 128 queries per CTA; at least
-    // 48 KB of shared memory keeps at most 4 CTAs (4 x 128 TMEM columns) on
-    // an SM, so every TMEM allocation is granted at once.
+    // Tensor-core linear search: one window, 128 queries per CTA, 256 TMEM
+    // columns per CTA.  At least 80 KB of shared memory keeps at most 2 CTAs
+    // (512 columns) on an SM, so every TMEM allocation is granted at once; the
+    // grid is sized from that bound (the occupancy query answers 1 block per
+    // SM for this kernel).
     const bool tc = brute && (L.w0.flags & TNN_FLAG_FFMA) == 0 && L.nwin <= 1 &&
                     tc_smem_bytes(L.L_max) <= (size_t)227 * 1024;
     if (tc) {
-        const size_t smem = std::max<size_t>(tc_smem_bytes(L.L_max), 48 * 1024);
-        TNN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_linear_tc, TC_Q, smem));
+        const size_t smem = std::max<size_t>(tc_smem_bytes(L.L_max), 80 * 1024);
+        nb = std::min<int>(2, (int)(g_smem_per_sm / (smem + 1024)));
         if (nb < 1) {
             tnn_set_error("tensor-core search kernel does not fit on an SM (%zu B shared memory)", smem);
             return TNN_ERR_UNSUPPORTED;
         }
         KnnLaunch Lt = L;
         Lt.total_tiles = (L.w0.m + TC_Q - 1) / TC_Q;
-        long long grid = std::min<long long>(Lt.total_tiles, (long long)std::min(nb, 4) * g_num_sms);
+        long long grid = std::min<long long>(Lt.total_tiles, (long long)nb * g_num_sms);
         if (grid < 1)
             grid = 1;
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -241,8 +277,27 @@ tnn_status tnn_launch_search(const KnnLaunch &L, bool brute, cudaStream_t st)
         std::pair<cudaEvent_t, cudaEvent_t> pr;
         if (prof)
             TNN_CUDA_TRY(prof_begin(st, &pr));
-        k_linear_tc<<<(unsigned)grid, TC_Q, smem, st>>>(Lt);
-        TNN_CUDA_TRY(cudaGetLastError());
+        // queries in space-time order (skipped beyond 2^29 queries)
+        unsigned long long *keys = nullptr;
+        if (L.w0.m <= (1ll << 29)) {
+            const int n2 = tnn_next_pow2_sort(L.w0.m);
+            TNN_CUDA_TRY(cudaMallocAsync((void **)&keys, (size_t)n2 * 8, st));
+            const float *lo = L.w0.bb_lo, *hi = L.w0.bb_hi;
+            float4 l4 = make_float4(lo[0], lo[1], lo[2], lo[3]), s4;
+            s4.x = hi[0] > lo[0] ? 1024.0f / (hi[0] - lo[0]) : 0.0f;
+            s4.y = hi[1] > lo[1] ? 1024.0f / (hi[1] - lo[1]) : 0.0f;
+            s4.z = 0.0f;
+            s4.w = hi[3] > lo[3] ? 1024.0f / (hi[3] - lo[3]) : 0.0f;
+            k_query_order_keys<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(L.w0.q, L.w0.m, n2, l4, s4,
+                                                                           keys);
+            tnn_bitonic_sort(keys, n2, st);
+            Lt.qorder = keys;
+        }
+        k_linear_tc<<<(unsigned)grid, TC_THREADS, smem, st>>>(Lt);
+        const cudaError_t le = cudaGetLastError();
+        if (keys)
+            cudaFreeAsync(keys, st);
+        TNN_CUDA_TRY(le);
         return finish_search(L, st, prof, pr);
     }
     const size_t smem = smem_per_warp(L.L_max, L.kseg_max,

@@ -2,45 +2,63 @@
 // the distance matrix with the classic expansion |q|^2 + |p|^2 - 2 q.p,
 // Table 1 "Distance Matrix").
 //
-// A CTA of 128 threads answers 128 queries (thread t = query t = TMEM lane t)
+// A CTA answers 128 queries (thread t of warps 0-3 = query t = TMEM lane t)
 // over the time-ordered copy of the points, most recent first, 128 points per
-// tile.  Each tile:
-//   1. its raw points arrive by TMA (cp.async.bulk, completion on an
-//      mbarrier), one tile ahead;
-//   2. every thread turns one point into a row of the B operand in shared
-//      memory (K-major, no swizzle): with e = sqrt(sigma) (p - c) for a
-//      fixed centre c, b = [-2 e, 1, |e|^2, 0, 0]; the query rows are
-//      a = [f, |f|^2, 1, 0, 0] with f = sqrt(sigma) (q - c), so a . b =
-//      |f - e|^2, the scaled squared distance;
-//   3. one thread issues tcgen05.mma kind::tf32 (M = 128, N = 128, K = 24):
-//      the 3-term TF32 split [a_hi | a_lo | a_hi] x [b_hi | b_hi | b_lo]
-//      keeps about 21 bits, the FP32 accumulator lives in TMEM;
-//   4. each thread reads its row of the accumulator (tcgen05.ld) and keeps
-//      only the points whose value is at most its pruning key plus a
-//      certified margin; those are scored again with the exact FP32
-//      distance of the other kernels, so candidate keys, lists and the FP64
-//      settlement are the same.
-// Margin: with R4 a bound on |e| over the points and |f| the query's, every
-// product a_k b_k is off by at most ~3 * 2^-22 |a_k||b_k| and the 18-term
-// FP32 accumulation by ~18 * 2^-24 of the sum of |a_k b_k| <= (|f| + R4)^2,
-// so 2^-16 (|f| + R4)^2 covers both with room; the FP32 centring of q and p
-// adds far less.  A point passing the FP32 test (d32 <= key) therefore
-// always passes the screen.
+// chunk.  The queries are taken in a space-time order (sorted key of x, y,
+// t), so the 128 of a CTA are close together and share a short causal prefix.
+// With c the centre of the CTA's queries, f = sqrt(sigma) (q - c) and
+// e = sqrt(sigma) (p - c), the TF32 operand rows are
+//     a = [f, (1 - eps) |f|^2, 1, eps |f|, -T]
+//     b = [-2 e, 1, (1 - eps) |e|^2, -2 |e|, 1]
+// so that a . b = |f - e|^2 - eps (|f| + |e|)^2 - T: the scaled squared
+// distance, minus an error allowance that scales with the magnitudes that
+// cancel, minus the query's current pruning threshold T.  A point can enter
+// the query's list only where that value is negative.
+//
+// Roles (warp specialisation, chained by mbarriers):
+//   warp 4, one thread: TMA (cp.async.bulk) of raw 128-point chunks and
+//     their input indices into a ring of TC_S slots, TC_S - 2 chunks ahead; one tcgen05.mma kind::tf32
+//     (M = N = 128, K = 8) per chunk into one of two TMEM accumulators,
+//     committed to an mbarrier;
+//   warps 0-3: write the A and B rows of chunk i + 1 (one row each), then
+//     read their accumulator rows of chunk i (tcgen05.ld), OR the bit
+//     patterns of 64 values at a time to find any negative one, and score
+//     only those points again with the exact FP32 distance of the other
+//     kernels -- so candidate keys, lists and the FP64 settlement are the
+//     same.  The MMA of chunk i + 1 runs while chunk i is screened.
+// Soundness of the screen (a point whose FP32 distance is at most the k-th
+// key must give a negative value): rounding every operand to TF32 changes
+// each product by at most 2^-10 |a_k b_k| and the FP32 sum of the 8 exact
+// products adds ~2^-20 of sum |a_k b_k| <= (|f| + |e|)^2 (1 + eps) + T;
+// centring and scaling in FP32 move |f - e|^2 by < 2^-21 (|f| + |e|)^2 and the
+// FP32 distance is within 2^-21 of the exact one.  eps = 2^-9 covers the
+// distance terms twice over, and T = RNA_tf32(thr (1 + 2^-8) + 2^-100)
+// exceeds the threshold by more than the error of its own term.
 #pragma once
 #include "tnn_device.cuh"
 
-#define TC_Q 128
-#define TC_P 128
-#define TC_KS 3
+#define TC_Q 128        // queries per CTA (TMEM lanes)
+#define TC_P 128        // points per chunk (accumulator columns)
+#define TC_S 16         // raw-point ring slots
+#define TC_THREADS 160  // 4 screening warps + 1 control warp
 #define TC_WAIT_NS 1000000000ull // 1 s: a copy or an MMA that takes longer is an error
+#define TC_EPS 0x1p-9f
 
-#define TC_OFF_A 0                       // [3 K-steps][128 rows x 8] TF32
-#define TC_OFF_B (TC_OFF_A + 12288)      // same for the points
-#define TC_OFF_RAW (TC_OFF_B + 12288)    // [2][128] float4 raw points
-#define TC_OFF_BAR (TC_OFF_RAW + 4096)   // mbarriers, TMEM slot, CTA scalars
-#define TC_OFF_LIST (TC_OFF_BAR + 128)   // [L][128] candidate keys
-// after the last tile the settlement scratch of the 4 warps (4 x 3 KB)
-// reuses the B operand and raw tiles (16 KB)
+#define TC_OFF_A 0                            // [2][128 rows x 8] TF32, K-major
+#define TC_OFF_B (TC_OFF_A + 8192)            // [2][128 rows x 8]
+#define TC_OFF_RAW (TC_OFF_B + 8192)          // [TC_S][128] float4
+#define TC_OFF_IDX (TC_OFF_RAW + TC_S * 2048) // [TC_S][128] int32 input index
+#define TC_OFF_BAR (TC_OFF_IDX + TC_S * 512)  // mbarriers and CTA scalars (512 B)
+#define TC_OFF_LIST (TC_OFF_BAR + 512)        // [L][128] candidate keys
+// the settlement scratch of the 4 warps (4 x 3 KB) reuses A and B once the
+// tile's last MMA has completed
+
+// mbarrier slots (8 B each) at TC_OFF_BAR
+#define TC_BAR_RAW 0    // [TC_S] raw chunk landed (TMA transaction count)
+#define TC_BAR_BFULL 16 // [2] A/B rows written (one arrival per warp)
+#define TC_BAR_ACC 18   // [2] accumulator ready (tcgen05.commit)
+#define TC_BAR_USED 20  // [TC_S] chunk screened (one arrival per warp)
+#define TC_BAR_END (TC_BAR_USED + TC_S)
 
 __host__ __device__ inline size_t tc_smem_bytes(int L_max)
 {
@@ -52,9 +70,9 @@ __device__ __forceinline__ uint32_t su32(const void *p)
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Byte offset of (row r, k) inside one K-step block (128 rows x 8 TF32):
-// core matrices of 8 rows x 16 B, K-adjacent ones 128 B apart, row-group
-// adjacent ones 256 B apart.
+// Byte offset of (row r, k) inside one 128-row x 8 TF32 operand: core
+// matrices of 8 rows x 16 B, K-adjacent ones 128 B apart, row-group adjacent
+// ones 256 B apart.
 __device__ __forceinline__ uint32_t kmaj_off(int r, int k)
 {
     return (uint32_t)((r >> 3) * 256 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
@@ -85,35 +103,78 @@ __device__ __forceinline__ uint64_t globaltimer_ns()
     return t;
 }
 
-// Wait for an mbarrier phase for at most TC_WAIT_NS; false if it timed out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t addr, uint32_t parity)
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity)
 {
-    uint64_t t0 = 0;
-    for (int it = 0;; ++it) {
-        uint32_t ok;
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                     "selp.u32 %0, 1, 0, p;\n}"
-                     : "=r"(ok)
-                     : "r"(addr), "r"(parity)
-                     : "memory");
-        if (ok)
+    uint32_t ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 "selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(addr), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Wait for an mbarrier phase.  Gives up (false) after TC_WAIT_NS, or as soon
+// as another thread of the CTA has flagged an error in *err (when err is
+// non-NULL); a thread that times out sets the flag.
+__device__ __noinline__ bool mbar_wait_slow(uint32_t addr, uint32_t parity, volatile int *err)
+{
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        if (mbar_try(addr, parity))
             return true;
-        if (it == 0)
-            t0 = globaltimer_ns();
-        else if (globaltimer_ns() - t0 > TC_WAIT_NS)
+        if (err && *err)
             return false;
+        if (globaltimer_ns() - t0 > TC_WAIT_NS) {
+            if (err)
+                *err = 1;
+            return false;
+        }
     }
 }
 
-__device__ __forceinline__ void tma_load_1d(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, volatile int *err)
 {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    return mbar_try(addr, parity) || mbar_wait_slow(addr, parity, err);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t addr)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+// Chunk i (0 = newest) of the causal prefix [0, hi): the 128-aligned block
+// [c_lo, c_lo + 128) clipped to hi, so every copy starts on a 16-byte boundary.
+__device__ __forceinline__ void tc_chunk(int hi, int i, int &c_lo, int &c_hi)
+{
+    c_lo = ((hi - 1) / TC_P - i) * TC_P;
+    c_hi = min(hi, c_lo + TC_P);
+}
+
+__device__ __forceinline__ void tma_copy_1d(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+// Chunk [c_lo, c_hi) of the time-ordered points and of their input indices
+// into ring slot s; both copies complete on the slot's barrier.  c_lo is a
+// multiple of 128 and sizes are multiples of 16 B: the index copy rounds up
+// to 4 entries (idx_t holds 4 entries of padding).
+__device__ __forceinline__ void tc_load_chunk(const float4 *pts_t, const int32_t *idx_t, int c_lo, int c_hi,
+                                              uint32_t raw_s, uint32_t idx_s, uint32_t bar)
+{
+    const uint32_t np = (uint32_t)(c_hi - c_lo);
+    const uint32_t ni = (np + 3u) & ~3u;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(np * 16u + ni * 4u)
+                 : "memory");
+    tma_copy_1d(raw_s, pts_t + c_lo, np * 16u, bar);
+    tma_copy_1d(idx_s, idx_t + c_lo, ni * 4u, bar);
+}
+
+// 32 consecutive accumulator columns of this warp's 32 lanes (no wait).
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t *r)
 {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                  "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -125,112 +186,195 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
                    "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
                    "=r"(r[30]), "=r"(r[31])
                  : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld()
+{
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Write the 3 K-step rows of one operand row: steps (s0, s1, s2) take the
-// high or low TF32 part of the 8 values v.
-__device__ __forceinline__ void write_split_row(unsigned char *base, int row, const float (&v)[8],
-                                                bool lo0, bool lo1, bool lo2)
+// One operand row (8 TF32 values, already rounded) as two 16-byte stores.
+__device__ __forceinline__ void store_row(unsigned char *base, int row, const float (&v)[8])
 {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const float hi = tf32_rna(v[k]);
-        const float lo = tf32_rna(v[k] - hi);
-        const uint32_t off = kmaj_off(row, k);
-        *(float *)(base + 0 * 4096 + off) = lo0 ? lo : hi;
-        *(float *)(base + 1 * 4096 + off) = lo1 ? lo : hi;
-        *(float *)(base + 2 * 4096 + off) = lo2 ? lo : hi;
+    *(float4 *)(base + kmaj_off(row, 0)) = make_float4(v[0], v[1], v[2], v[3]);
+    *(float4 *)(base + kmaj_off(row, 4)) = make_float4(v[4], v[5], v[6], v[7]);
+}
+
+// -T for a pruning threshold thr (see the soundness note above).
+__device__ __forceinline__ float tc_neg_T(float thr)
+{
+    return -tf32_rna(fmaf(thr, 0x1p-8f, thr) + 0x1p-100f);
+}
+
+// Candidate list of one query: at most Lw keys in a shared-memory column
+// (slots TC_Q keys apart).  Until it is full a key is appended; at Lw keys the
+// column becomes a binary max-heap, and from then on a smaller key replaces
+// the root and sinks (log2 Lw levels, two independent loads per level).
+// Returns the key a candidate must beat (SENT until the list is full).
+__device__ __forceinline__ void tc_heap_sink(unsigned long long *K, int Lw, int i, unsigned long long v)
+{
+    for (;;) {
+        const int l = 2 * i + 1;
+        if (l >= Lw)
+            break;
+        unsigned long long cv = K[l * TC_Q];
+        int c = l;
+        if (l + 1 < Lw) {
+            const unsigned long long rv = K[(l + 1) * TC_Q];
+            if (rv > cv) {
+                cv = rv;
+                c = l + 1;
+            }
+        }
+        if (cv <= v)
+            break;
+        K[i * TC_Q] = cv;
+        i = c;
+    }
+    K[i * TC_Q] = v;
+}
+
+__device__ __forceinline__ unsigned long long tc_list_put(unsigned long long *K, int Lw, int &nv,
+                                                          unsigned long long key)
+{
+    if (nv < Lw) {
+        K[nv * TC_Q] = key;
+        if (++nv < Lw)
+            return SENT;
+        for (int i = Lw / 2 - 1; i >= 0; --i)
+            tc_heap_sink(K, Lw, i, K[i * TC_Q]);
+    } else {
+        tc_heap_sink(K, Lw, 0, key);
+    }
+    return K[0];
+}
+
+// Ascending order of the nv keys of a column (insertion sort, once per tile).
+__device__ __forceinline__ void tc_list_sort(unsigned long long *K, int nv)
+{
+    for (int i = 1; i < nv; ++i) {
+        const unsigned long long v = K[i * TC_Q];
+        int j = i;
+        while (j > 0) {
+            const unsigned long long u = K[(j - 1) * TC_Q];
+            if (u <= v)
+                break;
+            K[j * TC_Q] = u;
+            --j;
+        }
+        K[j * TC_Q] = v;
     }
 }
 
-__global__ void __launch_bounds__(TC_Q, 1) k_linear_tc(const __grid_constant__ KnnLaunch L)
+__global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const __grid_constant__ KnnLaunch L)
 {
     extern __shared__ __align__(16) unsigned char smem[]; // no-swizzle operands need 16 B
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const bool ctrl = warp == 4;
+    const int tq = t & (TC_Q - 1);
     unsigned char *sA = smem + TC_OFF_A;
     unsigned char *sB = smem + TC_OFF_B;
     float4 *raw = (float4 *)(smem + TC_OFF_RAW);
-    unsigned long long *bar = (unsigned long long *)(smem + TC_OFF_BAR); // [3]
-    uint32_t *tmem_slot = (uint32_t *)(smem + TC_OFF_BAR + 24);
-    long long *s_tile = (long long *)(smem + TC_OFF_BAR + 32);
-    int *s_hi = (int *)(smem + TC_OFF_BAR + 40);
-    float *s_wmax = (float *)(smem + TC_OFF_BAR + 48); // [4]
-    unsigned long long *K = (unsigned long long *)(smem + TC_OFF_LIST) + t;
-    unsigned long long *cl_d = (unsigned long long *)(sB + warp * 3072) + lane;
-    int *cl_i = (int *)(sB + warp * 3072 + CMAX * 32 * 8) + lane;
+    const int32_t *sidx = (const int32_t *)(smem + TC_OFF_IDX);
+    const uint32_t bar0 = su32(smem + TC_OFF_BAR);
+    unsigned char *sc = smem + TC_OFF_BAR + 8 * TC_BAR_END;
+    uint32_t *tmem_slot = (uint32_t *)(sc + 0);
+    volatile int *s_err = (volatile int *)(sc + 4);
+    long long *s_tile = (long long *)(sc + 8);
+    int *s_hi = (int *)(sc + 16);
+    float *s_wmax = (float *)(sc + 32); // [4]
+    float *s_bb = (float *)(sc + 48);   // [4 warps][8]: min, max per axis
+    unsigned long long *K = (unsigned long long *)(smem + TC_OFF_LIST) + tq;
+    unsigned long long *cl_d = (unsigned long long *)(smem + TC_OFF_A + (warp & 3) * 3072) + lane;
+    int *cl_i = (int *)(smem + TC_OFF_A + (warp & 3) * 3072 + CMAX * 32 * 8) + lane;
+#define BAR(i) (bar0 + 8u * (uint32_t)(i))
 
     if (t == 0) {
-        for (int b = 0; b < 3; ++b)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar + b)));
+        for (int b = 0; b < TC_S; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(BAR(TC_BAR_RAW + b)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(BAR(TC_BAR_USED + b)));
+        }
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(BAR(TC_BAR_BFULL + b)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(BAR(TC_BAR_ACC + b)));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *s_err = 0;
     }
-    if (warp == 0) {
+    if (ctrl) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(su32(tmem_slot)), "r"(TC_P));
+                     ::"r"(su32(tmem_slot)), "r"(2 * TC_P));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    const uint32_t taddr_row = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t taddr_row = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     // F32 accumulate, A = B = TF32, both K-major, N = 128, M = 128
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_P >> 3) << 17) |
                            ((uint32_t)(TC_Q >> 4) << 24);
-    uint32_t ph[2] = {0u, 0u}, phm = 0u;
     LaneStats st = {0, 0, 0, 0, 0};
     const KnnWin *W = &L.w0;
     const float s0 = W->sig[0], s1 = W->sig[1], s2 = W->sig[2], s3 = W->sig[3];
     const float q0 = W->ssq[0], q1 = W->ssq[1], q2 = W->ssq[2], q3 = sqrtf(s3);
-    const float c0 = W->center[0], c1 = W->center[1], c2 = W->center[2], c3 = W->center[3];
     const float4 *__restrict__ pts_t = W->pts_t;
     const int32_t *__restrict__ idx_t = W->idx_t;
     const int Lw = W->L;
+    long long g = 0;        // chunks this CTA has processed (same in every thread)
+    long long issued = -1;  // control thread: last chunk copied
+    long long mma_last = -1; // control thread: last chunk multiplied
 
-    int err = 0; // the same in every thread: set only from __syncthreads_or results
     for (;;) {
         if (t == 0)
             *s_tile = (long long)atomicAdd(&L.scr->tile_counter, 1ull);
         __syncthreads();
         const long long tile = *s_tile;
-        if (tile >= L.total_tiles)
+        if (tile >= L.total_tiles || *s_err)
             break;
-        const int64_t qrow = tile * TC_Q + t;
-        const bool active = qrow < W->m;
+        const int64_t slot = tile * TC_Q + tq;
+        const bool active = !ctrl && slot < W->m;
+        const int64_t qrow = !active ? 0 : L.qorder ? (int64_t)(L.qorder[slot] & 0xffffffffull) : slot;
         const float4 q = active ? W->q[qrow] : make_float4(0.f, 0.f, 0.f, 0.f);
         const QCtx c = make_qctx(W, q, active);
 
-        // causal prefix of the CTA: points with t < max T32
-        float wm = c.T32;
-        for (int o = 16; o > 0; o >>= 1)
-            wm = fmaxf(wm, __shfl_xor_sync(FULLMASK, wm, o));
-        if (lane == 0)
-            s_wmax[warp] = wm;
-        // query rows of A and the candidate lists
-        float marg;
-        {
-            float f[4] = {q0 * (q.x - c0), q1 * (q.y - c1), q2 * (q.z - c2), q3 * (q.w - c3)};
-            float n2 = 0.f;
-#pragma unroll
-            for (int d = 0; d < 4; ++d)
-                n2 = fmaf(f[d], f[d], n2);
-            float a[8] = {f[0], f[1], f[2], f[3], n2, 1.0f, 0.0f, 0.0f};
+        // causal prefix of the CTA (points with t < max T32) and the bounding
+        // box of its queries
+        if (!ctrl) {
+            float wm = c.T32;
+            float bb[8] = {q.x, q.x, q.y, q.y, q.z, q.z, q.w, q.w};
             if (!active)
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    a[k] = 0.0f;
-            write_split_row(sA, t, a, false, true, false);
-            const float rr = sqrtf(n2) + W->R4;
-            marg = 0x1p-16f * rr * rr;
+                for (int d = 0; d < 4; ++d) {
+                    bb[2 * d] = INFINITY;
+                    bb[2 * d + 1] = -INFINITY;
+                }
+            for (int o = 16; o > 0; o >>= 1) {
+                wm = fmaxf(wm, __shfl_xor_sync(FULLMASK, wm, o));
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                    bb[2 * d] = fminf(bb[2 * d], __shfl_xor_sync(FULLMASK, bb[2 * d], o));
+                    bb[2 * d + 1] = fmaxf(bb[2 * d + 1], __shfl_xor_sync(FULLMASK, bb[2 * d + 1], o));
+                }
+            }
+            if (lane == 0) {
+                s_wmax[warp] = wm;
+#pragma unroll
+                for (int d = 0; d < 8; ++d)
+                    s_bb[warp * 8 + d] = bb[d];
+            }
         }
-        for (int i = 0; i < Lw; ++i)
-            K[i * TC_Q] = SENT;
-        int nv = 0;
-        unsigned long long tauk = SENT;
-        float tau = INFINITY, thr = INFINITY;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
+        float cc[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            float lo = s_bb[2 * d], hi = s_bb[2 * d + 1];
+            for (int w = 1; w < 4; ++w) {
+                lo = fminf(lo, s_bb[w * 8 + 2 * d]);
+                hi = fmaxf(hi, s_bb[w * 8 + 2 * d + 1]);
+            }
+            cc[d] = 0.5f * lo + 0.5f * hi; // a tile holds at least one query
+        }
         if (t == 0) {
             const float tm = fmaxf(fmaxf(s_wmax[0], s_wmax[1]), fmaxf(s_wmax[2], s_wmax[3]));
             int lo = 0, hi = W->n;
@@ -242,124 +386,231 @@ __global__ void __launch_bounds__(TC_Q, 1) k_linear_tc(const __grid_constant__ K
                     hi = mid;
             }
             *s_hi = lo;
-            if (lo > 0) {
-                const int cl = lo > TC_P ? lo - TC_P : 0;
-                tma_load_1d(su32(raw), pts_t + cl, (uint32_t)(lo - cl) * 16u, su32(bar + 0));
+        }
+        // causal end of this query: the time-ordered points [0, hq) are the
+        // ones with t < T32
+        int hq = 0;
+        if (active) {
+            int hi2 = W->n;
+            while (hq < hi2) {
+                const int mid = (hq + hi2) >> 1;
+                if (pts_t[mid].w < c.T32)
+                    hq = mid + 1;
+                else
+                    hi2 = mid;
             }
         }
+        // the fixed part of the query row
+        float arow[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (active) {
+            const float f[4] = {q0 * (q.x - cc[0]), q1 * (q.y - cc[1]), q2 * (q.z - cc[2]),
+                                q3 * (q.w - cc[3])};
+            float n2 = 0.f;
+#pragma unroll
+            for (int d = 0; d < 4; ++d)
+                n2 = fmaf(f[d], f[d], n2);
+            arow[0] = tf32_rna(f[0]);
+            arow[1] = tf32_rna(f[1]);
+            arow[2] = tf32_rna(f[2]);
+            arow[3] = tf32_rna(f[3]);
+            arow[4] = tf32_rna((1.0f - TC_EPS) * n2);
+            arow[5] = 1.0f;
+            arow[6] = tf32_rna(TC_EPS * sqrtf(n2));
+        }
+        if (!ctrl)
+            for (int i = 0; i < Lw; ++i)
+                K[i * TC_Q] = SENT;
         __syncthreads();
         const int hi = *s_hi;
         const int nch = (hi + TC_P - 1) / TC_P;
-        // Chunk i's copy is issued (one ahead) only once chunk i - 1's copy
-        // was waited for; a loop exit waits for the copy still in flight.
-        for (int i = 0; i < nch; ++i) {
-            const int b = i & 1;
-            const int c_hi = hi - TC_P * i, c_lo = c_hi > TC_P ? c_hi - TC_P : 0;
-            const int cnt = c_hi - c_lo;
-            const bool bad_copy = !mbar_wait_bounded(su32(bar + b), ph[b]);
-            ph[b] ^= 1u;
-            // point row t of B
-            {
+        int nv = 0;
+        unsigned long long tauk = SENT;
+        float tau = INFINITY;
+
+        if (ctrl) {
+            // ---- control thread: copies and MMAs
+            if (lane == 0 && nch > 0) {
+                const int pre = min(nch, TC_S - 2);
+                for (int j = 0; j < pre; ++j) {
+                    // the slot's previous chunk belongs to an earlier tile and
+                    // was screened before the tile barrier
+                    const long long gj = g + j;
+                    int c_lo, c_hi;
+                    tc_chunk(hi, j, c_lo, c_hi);
+                    tc_load_chunk(pts_t, idx_t, c_lo, c_hi, su32(raw + (gj % TC_S) * TC_P),
+                                  su32(sidx + (gj % TC_S) * TC_P), BAR(TC_BAR_RAW + gj % TC_S));
+                    issued = gj;
+                }
+                for (int i = 0; i < nch; ++i) {
+                    const long long gi = g + i;
+                    const int b = (int)(gi & 1);
+                    if (!mbar_wait(BAR(TC_BAR_BFULL + b), (uint32_t)((gi >> 1) & 1), s_err))
+                        break;
+                    // accumulator b and the raw slot of chunk gi - 2 are free
+                    // once that chunk is screened
+                    if (gi >= 2 && !mbar_wait(BAR(TC_BAR_USED + (gi - 2) % TC_S),
+                                              (uint32_t)(((gi - 2) / TC_S) & 1), s_err))
+                        break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint64_t da = umma_desc(su32(sA + b * 4096));
+                    const uint64_t db = umma_desc(su32(sB + b * 4096));
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                                 ::"r"(tmem + (uint32_t)(b * TC_P)), "l"(da), "l"(db), "r"(idesc), "r"(0));
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 ::"r"(BAR(TC_BAR_ACC + b))
+                                 : "memory");
+                    mma_last = gi;
+                    const int j = i + TC_S - 2;
+                    if (j < nch) {
+                        const long long gj = g + j; // slot of chunk gi - 2
+                        int c_lo, c_hi;
+                        tc_chunk(hi, j, c_lo, c_hi);
+                        tc_load_chunk(pts_t, idx_t, c_lo, c_hi, su32(raw + (gj % TC_S) * TC_P),
+                                      su32(sidx + (gj % TC_S) * TC_P), BAR(TC_BAR_RAW + gj % TC_S));
+                        issued = gj;
+                    }
+                }
+            }
+        } else if (nch > 0) {
+            // ---- screening warps.  Every wait outcome is made warp-uniform
+            // before the warp-collective steps that follow it.
+            // Rows of chunk gi: B from its raw points, A with the current -T.
+            auto build = [&](long long gi, int i) -> bool {
+                const int s = (int)(gi % TC_S), b = (int)(gi & 1);
+                const bool okw = mbar_wait(BAR(TC_BAR_RAW + s), (uint32_t)((gi / TC_S) & 1), s_err);
+                if (!__all_sync(FULLMASK, okw))
+                    return false;
+                int c_lo, c_hi;
+                tc_chunk(hi, i, c_lo, c_hi);
                 float bv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                if (t < cnt) {
-                    const float4 p = raw[b * TC_P + t];
-                    const float e[4] = {q0 * (p.x - c0), q1 * (p.y - c1), q2 * (p.z - c2), q3 * (p.w - c3)};
+                if (tq < c_hi - c_lo) {
+                    const float4 p = raw[s * TC_P + tq];
+                    const float e[4] = {q0 * (p.x - cc[0]), q1 * (p.y - cc[1]), q2 * (p.z - cc[2]),
+                                        q3 * (p.w - cc[3])};
                     float m2 = 0.f;
 #pragma unroll
                     for (int d = 0; d < 4; ++d)
                         m2 = fmaf(e[d], e[d], m2);
-                    bv[0] = -2.0f * e[0];
-                    bv[1] = -2.0f * e[1];
-                    bv[2] = -2.0f * e[2];
-                    bv[3] = -2.0f * e[3];
+                    bv[0] = tf32_rna(-2.0f * e[0]);
+                    bv[1] = tf32_rna(-2.0f * e[1]);
+                    bv[2] = tf32_rna(-2.0f * e[2]);
+                    bv[3] = tf32_rna(-2.0f * e[3]);
                     bv[4] = 1.0f;
-                    bv[5] = m2;
+                    bv[5] = tf32_rna((1.0f - TC_EPS) * m2);
+                    bv[6] = tf32_rna(-2.0f * sqrtf(m2));
+                    bv[7] = 1.0f;
                 }
-                write_split_row(sB, t, bv, false, false, true);
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            if (__syncthreads_or(bad_copy)) {
-                err = 1;
-                break;
-            }
-            if (t == 0) {
+                store_row(sB + b * 4096, tq, bv);
+                arow[7] = active ? tc_neg_T(tau) : 0.0f;
+                store_row(sA + b * 4096, tq, arow);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(BAR(TC_BAR_BFULL + b));
+                return true;
+            };
+            bool ok = build(g, 0);
+            for (int i = 0; ok && i < nch; ++i) {
+                const long long gi = g + i;
+                const int s = (int)(gi % TC_S), b = (int)(gi & 1);
+                if (i + 1 < nch && !build(gi + 1, i + 1))
+                    break;
+                const bool okw = mbar_wait(BAR(TC_BAR_ACC + b), (uint32_t)((gi >> 1) & 1), s_err);
+                if (!__all_sync(FULLMASK, okw))
+                    break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                int c_lo, c_hi;
+                tc_chunk(hi, i, c_lo, c_hi);
+                const int ncaus = max(0, min(c_hi - c_lo, hq - c_lo)); // causal columns of this lane
+                st.pairs += ncaus;
+                if (__any_sync(FULLMASK, ncaus > 0)) {
 #pragma unroll
-                for (int s = 0; s < TC_KS; ++s) {
-                    const uint64_t da = umma_desc(su32(sA + s * 4096));
-                    const uint64_t db = umma_desc(su32(sB + s * 4096));
-                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-                                 ::"r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(s));
-                }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             ::"r"(su32(bar + 2))
-                             : "memory");
-                if (i + 1 < nch) {
-                    const int nh = c_lo, nl = nh > TC_P ? nh - TC_P : 0;
-                    tma_load_1d(su32(raw + (b ^ 1) * TC_P), pts_t + nl, (uint32_t)(nh - nl) * 16u,
-                                su32(bar + (b ^ 1)));
-                }
-            }
-            const bool bad_mma = !mbar_wait_bounded(su32(bar + 2), phm);
-            phm ^= 1u;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (__syncthreads_or(bad_mma)) {
-                err = 2;
-                if (i + 1 < nch) // the copy of chunk i + 1 is in flight
-                    mbar_wait_bounded(su32(bar + (b ^ 1)), ph[b ^ 1]);
-                break;
-            }
-            // screen the row, score the survivors exactly
-            for (int col0 = 0; col0 < cnt; col0 += 32) {
-                uint32_t v[32];
-                tmem_ld32(taddr_row + (uint32_t)col0, v);
-                if (active) {
+                    for (int h = 0; h < 2; ++h) {
+                        uint32_t v[64];
+                        tmem_ld32_nowait(taddr_row + (uint32_t)(b * TC_P + h * 64), v);
+                        tmem_ld32_nowait(taddr_row + (uint32_t)(b * TC_P + h * 64 + 32), v + 32);
+                        tmem_wait_ld();
+                        uint32_t any = 0u;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = col0 + j;
-                        if (col < cnt && __uint_as_float(v[j]) <= thr) {
-                            const float4 p = raw[b * TC_P + col];
-                            const float d = dist32(c, s0, s1, s2, s3, p);
-                            st.lb++; // screened points scored again in FP32
-                            if (p.w < c.T32 && d <= tau) {
-                                const unsigned long long key = pack_key(d, __ldg(idx_t + c_lo + col));
-                                if (key < tauk) {
-                                    tauk = lane_push_s(K, Lw, nv, key, TC_Q);
-                                    tau = key_d(tauk);
-                                    thr = fmaf(tau, 0x1p-18f, tau) + marg;
+                        for (int j = 0; j < 64; ++j)
+                            any |= v[j];
+                        const int lim = ncaus - h * 64; // causal columns in this half
+                        if ((int)any < 0 && lim > 0) {
+                            uint32_t m0 = 0u, m1 = 0u;
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                m0 |= (v[j] >> 31) << j;
+                                m1 |= (v[32 + j] >> 31) << j;
+                            }
+                            if (lim <= 32) {
+                                m1 = 0u;
+                                if (lim < 32)
+                                    m0 &= (1u << lim) - 1u;
+                            } else if (lim < 64) {
+                                m1 &= (1u << (lim - 32)) - 1u;
+                            }
+#pragma unroll
+                            for (int part = 0; part < 2; ++part) {
+                                uint32_t msk = part ? m1 : m0;
+                                while (msk) {
+                                    const int col = h * 64 + part * 32 + __ffs(msk) - 1;
+                                    msk &= msk - 1u;
+                                    const float4 p = raw[s * TC_P + col];
+                                    const float d = dist32(c, s0, s1, s2, s3, p);
+                                    st.lb++; // screened points scored again in FP32
+                                    if (p.w < c.T32 && d <= tau) {
+                                        const unsigned long long key = pack_key(d, sidx[s * TC_P + col]);
+                                        if (key < tauk) {
+                                            tauk = tc_list_put(K, Lw, nv, key);
+                                            tau = key_d(tauk);
+                                        }
+                                    }
                                 }
                             }
                         }
                     }
                 }
+                // the TMEM reads and raw[s] are finished: release the
+                // accumulator and the slot
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(BAR(TC_BAR_USED + s));
             }
-            if (active)
-                st.pairs += cnt;
-            // The next chunk's barrier orders these reads of TMEM and of
-            // raw[b] before the MMA and the copy that overwrite them.
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         }
-        if (err)
+        g += nch;
+        __syncthreads();
+        if (*s_err)
             break;
         if (active) {
             st.q++;
+            tc_list_sort(K, nv);
             if (!finalize_query(W, q, K, Lw, cl_d, cl_i, qrow, st, TC_Q)) {
-                const unsigned slot = atomicAdd(&L.scr->n_fallback, 1u);
-                if (slot < (unsigned long long)L.fb_cap)
-                    L.fb_list[slot] = make_int2(-1, (int)qrow); // unsettled, window 0
+                const unsigned fslot = atomicAdd(&L.scr->n_fallback, 1u);
+                if (fslot < (unsigned long long)L.fb_cap)
+                    L.fb_list[fslot] = make_int2(-1, (int)qrow); // unsettled, window 0
                 else
                     atomicOr(&L.scr->status, 1u);
             }
         }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); // A, B, raw are refilled async
         __syncthreads();
     }
-    if (t == 0 && err)
+    if (*s_err && ctrl && lane == 0) {
+        // a wait timed out: let the copies and the MMA still in flight land
+        // (each wait bounded) before the memory they write is released
         atomicOr(&L.scr->status, 4u);
+        for (long long gj = issued; gj >= 0 && gj > issued - TC_S; --gj)
+            mbar_wait(BAR(TC_BAR_RAW + gj % TC_S), (uint32_t)((gj / TC_S) & 1), nullptr);
+        if (mma_last >= 0)
+            mbar_wait(BAR(TC_BAR_ACC + (mma_last & 1)), (uint32_t)((mma_last >> 1) & 1), nullptr);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_P));
-    flush_stats(L.scr, st);
+    if (ctrl)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_P));
+    else
+        flush_stats(L.scr, st);
+#undef BAR
 }
