@@ -34,6 +34,27 @@ OPS_PER_LB = 26
 OPS_PER_PAIR = 14
 OPS_PER_KEY = 20
 
+# DRAM bytes (read + write) of one search on the medium workload, summed over
+# k_tnn_grid_search + k_tnn_warp + k_fallback_exact, from the ncu capture
+# summarised in profiles/k_tnn_grid_search_medium.md, with a hash of the
+# kernel sources it was taken on: once they change the figure is stale and
+# is reported as null.
+SEARCH_TRAFFIC = {"bytes": 44539392 + 6872320 + 19712, "workload": "medium",
+                  "sources": ["tnn_device.cuh", "tnn_grid.cuh", "tnn_fallback.cuh", "tnn_internal.cuh",
+                              "tnn_knn.cu"],
+                  "sha256_16": "e94dc4d3ff2528b2"}
+
+
+def _search_traffic(workload):
+    import hashlib
+    h = hashlib.sha256()
+    for f in SEARCH_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, "paper_2112_10408_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if workload != SEARCH_TRAFFIC["workload"] or h.hexdigest()[:16] != SEARCH_TRAFFIC["sha256_16"]:
+        return None
+    return SEARCH_TRAFFIC["bytes"]
+
 
 def _args():
     ap = argparse.ArgumentParser()
@@ -259,7 +280,7 @@ def run_ours(a):
     alu_peak = nsm * 128 * sm_max * 1e6 / 1e12  # T FP32 lane-ops/s
     achieved = alg_ops / (kern_avg_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "T FP32 lane-ops/s",
-                "frac": achieved / alu_peak, "traffic": None,
+                "frac": achieved / alu_peak, "traffic": _search_traffic(a.workload),
                 "kernel": "search = k_tnn_grid_search + k_tnn_warp + k_fallback_exact",
                 "kernel_ms": kern_avg_ms,
                 "peak_note": f"{nsm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived, not measured)",
@@ -294,12 +315,13 @@ def run_ours(a):
                    "tnn_speedup": cmean / ms_step, "identical_neighbours": bool(torch.equal(bi, idx)),
                    "pairs": cst["pairs"], "rescored": cst["lb_evals"]}
             if not ffma:
-                # 3 TF32 MMAs of K = 8 per 128 x 128 tile: 48 flops per pair
-                tf = 48.0 * cst["pairs"] / (cmean / 1e3) / 1e12
+                # one TF32 MMA (M = N = 128, K = 8) per 128 x 128 tile
+                tiles = cst["segs_scanned"]
+                tf = 2.0 * 128 * 128 * 8 * tiles / (cmean / 1e3) / 1e12
                 tf32_peak = peaks.get("bf16_tflops", 1900.0) * (1.1 / 2.25)
-                ent["tensor"] = {"achieved_tflops": tf, "tf32_peak_tflops": tf32_peak,
+                ent["tensor"] = {"tiles": tiles, "achieved_tflops": tf, "tf32_peak_tflops": tf32_peak,
                                  "frac": tf / tf32_peak,
-                                 "peak_note": "measured bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"}
+                                 "peak_note": "of measured: bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"}
             comparator[name] = ent
 
     # end to end through the C ABI: pinned host points -> build -> search ->

@@ -191,7 +191,8 @@ tnn_status tnn_knn(const tnn_index *index, const float *d_q, int64_t m,
  * current k-th candidate plus a certified margin is scored again with the
  * exact FP32 distance, so the result is the one tnn_knn returns.
  * TNN_FLAG_FFMA computes every distance directly on the CUDA cores.
- * counters: lb_evals = points scored again, pairs = point pairs screened.
+ * counters: lb_evals = points scored again, pairs = causal point pairs
+ * screened, segs_scanned = 128 x 128 distance tiles multiplied.
  */
 tnn_status tnn_knn_bruteforce(const tnn_index *index, const float *d_q,
                               int64_t m, const tnn_knn_params *params,

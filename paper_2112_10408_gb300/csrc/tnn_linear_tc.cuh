@@ -524,6 +524,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const __grid_consta
                 tc_chunk(hi, i, c_lo, c_hi);
                 const int ncaus = max(0, min(c_hi - c_lo, hq - c_lo)); // causal columns of this lane
                 st.pairs += ncaus;
+                if (t == 0)
+                    st.segs++; // 128 x 128 tiles multiplied
                 if (__any_sync(FULLMASK, ncaus > 0)) {
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
