@@ -66,6 +66,8 @@ def _args():
     ap.add_argument("--comparator-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-window and nowcast measurements")
     ap.add_argument("--tuning", choices=["auto", "default"], default="auto",
                     help="autotune the seed/extra knobs (auto) or use the library defaults")
     return ap.parse_args()
@@ -195,6 +197,136 @@ def run_reference(a):
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
+
+
+def _timed(fn, steps, flush=None):
+    """Mean CUDA-event time (ms) of fn() over `steps` runs, L2 flushed before each."""
+    import torch
+    ms = []
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return sum(ms) / len(ms)
+
+
+def _extras(tnn, synth, flush, peaks, steps):
+    """The other rows of the path, each timed on its own: the persistent
+    batched driver over 64 windows (CUDA graph), and the learned form
+    (contexts with lag 1800 s, features + IDW, MLP training, nowcasts)."""
+    import numpy as np
+    import torch
+    sigma = (1.0, 1.0, 10.0, 0.01)
+    out = {}
+    # ---- batched windows
+    wins = synth.batched_windows(n_windows=64)
+    idxs = [tnn.tnn_build_segments(torch.from_numpy(wl.xyzt).cuda(), wl.traj_off, sigma, 20)
+            for wl, _ in wins]
+    b = tnn.Batch(idxs, [k for _, k in wins])
+    for _ in range(3):
+        b.run()
+    torch.cuda.synchronize()
+    ms = _timed(b.run, steps, flush)
+    nq = sum(wl.n for wl, _ in wins)
+    out["batched"] = {"metric": "causal k-NN contexts/s over 64 windows in one persistent launch",
+                      "value": nq / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "windows": len(wins),
+                      "queries": nq, "k_mix": {str(k): sum(1 for _, kk in wins if kk == k) for k in (16, 32, 64)},
+                      "launch": "tnn_batch_run: one CUDA graph (tile kernel + warp kernel + exact kernel)"}
+    b.destroy()
+    for ix in idxs:
+        ix.destroy()
+    del idxs, b
+    torch.cuda.empty_cache()
+
+    # ---- learned form: 5,000 flights x 200 = 1,000,000 points, lag 1800 s
+    wl = synth.learned()
+    k, lag = 32, 1800.0
+    ix = tnn.tnn_build_segments(torch.from_numpy(wl.xyzt).cuda(), wl.traj_off, sigma, 20)
+    wind = torch.from_numpy(wl.wind).cuda()
+    idx = torch.empty((wl.n, k), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((wl.n, k), dtype=torch.float32, device="cuda")
+    tune = tnn.tnn_autotune(ix, k, lag)
+    tnn.tnn_knn(ix, k, lag, out=(idx, d2), **tune)
+    torch.cuda.synchronize()
+    ms_knn = _timed(lambda: tnn.tnn_knn(ix, k, lag, out=(idx, d2), **tune), steps, flush)
+    full = (idx >= 0).all(dim=1).cpu().numpy()
+    train, test = synth.flight_split(wl)
+    tr = np.nonzero(train & full)[0]
+    te = np.nonzero(test & full)[0]
+    raw, idw = tnn.tnn_context_features(ix, wind, idx, d2)
+    f = raw.float()[torch.from_numpy(tr).cuda()].view(-1, k, 6)
+    mean = f.mean(dim=(0, 1)).cpu().numpy()
+    std = f.std(dim=(0, 1)).cpu().numpy() + 1e-6
+    del f, raw
+    feat, _ = tnn.tnn_context_features(ix, wind, idx, d2, mean=mean, std=std, want_idw=False)
+    ms_feat = _timed(lambda: tnn.tnn_context_features(ix, wind, idx, d2, mean=mean, std=std), steps, flush)
+    # bytes per context: idx + d2 (8 k), gathered point + wind (24 k), query
+    # point (16), features out (12 k bf16), IDW out (8)
+    feat_bytes = wl.n * (44 * k + 24)
+    mlp = tnn.MLP(k * 6, 256, seed=0)
+    opt = tnn.AdamW(lr=1e-3, weight_decay=1e-2)
+    rng = np.random.default_rng(0)
+    trd = torch.from_numpy(tr).cuda()
+    B = 4096
+    epochs = 3
+    batches = []
+    for _ in range(epochs):
+        perm = trd[torch.from_numpy(rng.permutation(tr.size)).cuda()]
+        for s0 in range(0, perm.numel() - B + 1, B):
+            sel = perm[s0:s0 + B]
+            batches.append((feat[sel].contiguous(), wind[sel].contiguous()))
+    mlp.train_step(*batches[0], opt)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for xb, yb in batches[1:]:
+        mlp.train_step(xb, yb, opt)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_train = e0.elapsed_time(e1) / (len(batches) - 1)
+    flops_step = 2.0 * B * (k * 6) * 256 * 2 + 2.0 * B * 256 * 2 * 3
+    ted = torch.from_numpy(te).cuda()
+    xte = feat[ted].contiguous()
+    mlp.forward(xte)  # sizes the workspace outside the timed runs
+    torch.cuda.synchronize()
+    ms_fwd = _timed(lambda: mlp.forward(xte), steps)
+    pred = mlp.forward(xte)
+    rmse_mlp = float(torch.sqrt(((pred - wind[ted]) ** 2).mean()))
+    rmse_idw = float(torch.sqrt(((idw[ted] - wind[ted]) ** 2).mean()))
+    qte = torch.from_numpy(wl.xyzt[te]).cuda()
+    tnn.tnn_nowcast(ix, wind, k, lag, q=qte, mlp=mlp, mean=mean, std=std, **tune)
+    torch.cuda.synchronize()
+    ms_now = _timed(lambda: tnn.tnn_nowcast(ix, wind, k, lag, q=qte, mlp=mlp, mean=mean, std=std, **tune),
+                    steps, flush)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    out["nowcast"] = {
+        "workload": "learned-1M: 5,000 flights x 200 samples, k = 32, lag 1800 s, 80/20 split by flight",
+        "contexts": {"value": wl.n / (ms_knn / 1e3), "unit": UNIT, "ms": ms_knn, "tuning": tune},
+        "features_idw": {"value": wl.n / (ms_feat / 1e3), "unit": "contexts/s", "ms": ms_feat,
+                         "roofline": {"bound": "hbm", "achieved": feat_bytes / (ms_feat / 1e3) / 1e9,
+                                      "peak": hbm, "unit": "GB/s",
+                                      "frac": feat_bytes / (ms_feat / 1e3) / 1e9 / hbm,
+                                      "bytes_per_context": 44 * k + 24, "peak_note": "of measured hbm_gbs"}},
+        "mlp_train": {"value": B / (ms_train / 1e3), "unit": "samples/s", "ms_per_step": ms_train,
+                      "batch": B, "steps": len(batches) - 1, "epochs": epochs,
+                      "roofline": {"bound": "tensor", "achieved": flops_step / (ms_train / 1e3) / 1e12,
+                                   "peak": bf16, "unit": "TFLOP/s",
+                                   "frac": flops_step / (ms_train / 1e3) / 1e12 / bf16,
+                                   "flops_per_step": flops_step, "peak_note": "of measured bf16 burst"}},
+        "mlp_forward": {"value": xte.shape[0] / (ms_fwd / 1e3), "unit": "samples/s", "ms": ms_fwd,
+                        "rows": int(xte.shape[0])},
+        "nowcast_e2e": {"value": qte.shape[0] / (ms_now / 1e3), "unit": "nowcasts/s", "ms": ms_now,
+                        "queries": int(qte.shape[0]), "includes": "tnn_nowcast: search + features + MLP"},
+        "rmse_ms": {"mlp": rmse_mlp, "idw": rmse_idw, "held_out_rows": int(te.size),
+                    "note": "synthetic wind field; noise floor 1 m/s per component (parity unpinned)"}}
+    ix.destroy()
+    return out
 
 
 def run_ours(a):
@@ -349,6 +481,11 @@ def run_ours(a):
            "h2d_bytes_per_step": int(h_x.numel() * 4), "d2h_bytes_per_step": int(m * k * 8),
            "ms_per_step": e2e_avg, "includes": "H2D points, tnn_build_segments, tnn_knn, D2H results"}
 
+    extras = None
+    if rank == 0 and world == 1 and not a.no_extras:
+        from paper_2112_10408_gb300 import synth
+        extras = _extras(tnn, synth, flush, _peaks(), max(3, min(a.steps, 20)))
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = _cpu_baseline(wl, k, 8192 if a.workload != "tiny" else wl.n)
@@ -362,6 +499,8 @@ def run_ours(a):
                "clocks": clocks, "e2e": e2e, "gpu_launches": 3 * a.steps,
                "roofline": roofline, "cpu_baseline": cpu, "comparator": comparator,
                "stats_per_step": st}
+        if extras:
+            out.update(extras)
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()

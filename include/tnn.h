@@ -140,6 +140,7 @@ typedef struct {
     int32_t flags;         /* TNN_FLAG_*                                      */
     float defer_cells;     /* grid order: a query whose k-th candidate after
                               seeding is farther than defer_cells grid cells
+                              (beyond the sigma_t lag^2 every key carries)
                               leaves its shared 32-query tile and is finished
                               by a warp of its own (Algorithm 2 puts finished
                               lines aside; here the slow ones are) -- 0 =
@@ -289,8 +290,10 @@ void tnn_batch_destroy(tnn_batch *batch);
 /*
  * Choose the segment order (TNN_FLAG_SWEEP), seed_segments, extra and
  * defer_cells for one index and k by timing
- * the search on a sample of `m_sample` self-queries spread over the index
- * (CUDA events).  Writes the best into *params (k, lag, flags untouched).
+ * the search on a sample of self-queries spread over the index (CUDA
+ * events): max(m_sample, 262,144) of them, at most all n, so that the
+ * sample fills the GPU.  Writes the best into *params (k, lag, flags
+ * untouched).
  * Synchronises `stream`.
  */
 tnn_status tnn_autotune(const tnn_index *index, tnn_knn_params *params,

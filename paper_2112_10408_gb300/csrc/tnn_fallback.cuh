@@ -6,7 +6,8 @@
 //     the whole warp works on one query (list of k + extra candidates);
 //   - unsettled (window id stored as -1 - w): the chain of FP32 keys that FP32
 //     cannot order reached the last candidate slot; here the list keeps
-//     k + 32 candidates.
+//     k + 32 candidates (a deferred query that ends the same way is run
+//     again at once with k + 32).
 //
 // k_tnn_warp: the 32 lanes split the grid keys, the member segments and the
 // member points of one query.  Candidates below the pruning key are sorted
@@ -18,7 +19,8 @@
 // fetch), so the pruning key is tight as soon as it exists.  The main phase
 // is the exclusion criterion and stop rule of Algorithm 2 over the other
 // keys, scanning the needed segments of a chunk 32 points at a time.
-// A query still unsettled goes to k_fallback_exact: the FP64 definition.
+// A query still unsettled goes to k_fallback_exact: the definition, with the
+// FP64 distance taken only for the points that FP32 cannot rule out.
 #pragma once
 #include "tnn_device.cuh"
 #include "tnn_grid.cuh"
@@ -142,17 +144,21 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
     (void)gw;
     (void)nw;
     LaneStats st = {0, 0, 0, 0, 0};
+    int2 ent = make_int2(0, 0);
+    bool retry = false; // the same query again with the larger list
     for (;;) {
-        // dynamic queue: query costs differ by orders of magnitude
-        unsigned e = 0;
-        if (lane == 0)
-            e = atomicAdd(&L.scr->fb_next, 1u);
-        e = __shfl_sync(FULLMASK, e, 0);
-        if (e >= nfb)
-            break;
-        const int2 ent = L.fb_list[e];
-        const bool unsettled = ent.x < 0;
-        const int wid = unsettled ? -1 - ent.x : ent.x;
+        if (!retry) {
+            // dynamic queue: query costs differ by orders of magnitude
+            unsigned e = 0;
+            if (lane == 0)
+                e = atomicAdd(&L.scr->fb_next, 1u);
+            e = __shfl_sync(FULLMASK, e, 0);
+            if (e >= nfb)
+                break;
+            ent = L.fb_list[e];
+        }
+        const bool unsettled = retry || ent.x < 0;
+        const int wid = ent.x < 0 ? -1 - ent.x : ent.x;
         const KnnWin *W = L.nwin <= 1 ? &L.w0 : L.wins + wid;
         const float4 q = W->q[ent.y];
         const QCtx c = make_qctx(W, q, true);
@@ -362,14 +368,19 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
             }
         }
         __syncwarp();
-        if (lane == 0) {
-            if (!finalize_query(W, q, wl.L, wl.C, cl_d, cl_i, ent.y, st, 1)) {
-                const unsigned slot = atomicAdd(&L.scr->n_fallback3, 1u);
-                if (slot < (unsigned long long)L.fb_cap)
-                    L.fb_list3[slot] = make_int2(wid, ent.y);
-                else
-                    atomicOr(&L.scr->status, 2u);
-            }
+        bool ok = true;
+        if (lane == 0)
+            ok = finalize_query(W, q, wl.L, wl.C, cl_d, cl_i, ent.y, st, 1);
+        ok = __shfl_sync(FULLMASK, ok, 0);
+        // a tie chain ran past the end of a k + extra list: once more with
+        // k + FB_EXTRA slots before the FP64 definition is used
+        retry = !ok && wl.C < W->k + FB_EXTRA;
+        if (!ok && !retry && lane == 0) {
+            const unsigned slot = atomicAdd(&L.scr->n_fallback3, 1u);
+            if (slot < (unsigned long long)L.fb_cap)
+                L.fb_list3[slot] = make_int2(wid, ent.y);
+            else
+                atomicOr(&L.scr->status, 2u);
         }
         __syncwarp();
     }
@@ -414,16 +425,63 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
         const int2 ent = L.fb_list3[e];
         const KnnWin *W = L.nwin <= 1 ? &L.w0 : L.wins + ent.x;
         const float4 q = W->q[ent.y];
-        const float T32 = __double2float_ru((double)q.w - W->lag);
+        const QCtx c = make_qctx(W, q, true);
+        const float s0 = W->sig[0], s1 = W->sig[1], s2 = W->sig[2], s3 = W->sig[3];
+        const float T32 = c.T32;
         const int k = W->k;
-        for (int r = 0; r < k; ++r) {
-            kd[r * 32] = INF64;
-            ki[r * 32] = 0x7fffffff;
-        }
+        // pass 1: the k-th smallest FP32 key over the valid points (each lane
+        // keeps its k smallest, then a k-round warp merge)
+        for (int r = 0; r < k; ++r)
+            kd[r * 32] = SENT;
         int cnt = 0;
         for (int j = lane; j < W->n; j += 32) {
             const float4 p = W->pts[j];
             if (!(p.w < T32))
+                continue;
+            const unsigned long long key = pack_key(dist32(c, s0, s1, s2, s3, p), j);
+            if (!(key < kd[(k - 1) * 32]))
+                continue;
+            int pos = cnt < k ? cnt : k - 1;
+            while (pos > 0) {
+                const unsigned long long pk = kd[(pos - 1) * 32];
+                if (pk < key)
+                    break;
+                kd[pos * 32] = pk;
+                --pos;
+            }
+            kd[pos * 32] = key;
+            if (cnt < k)
+                ++cnt;
+        }
+        unsigned long long kth = SENT;
+        {
+            int h = 0;
+            for (int r = 0; r < k; ++r) {
+                const unsigned long long v = h < cnt ? kd[h * 32] : SENT;
+                unsigned long long mv = v;
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long ov = shfl_xor_u64(mv, o);
+                    mv = ov < mv ? ov : mv;
+                }
+                if (v == mv && h < cnt)
+                    ++h;
+                kth = mv;
+            }
+        }
+        // Every point of the exact top k has d32 <= tau32 (1 + 2^-20): at
+        // least k points have d32 <= tau32, so d64 of the k-th is at most
+        // tau32 / (1 - 2^-21), and d32 <= d64 (1 + 2^-21).
+        const float tau32 = key_d(kth);
+        const float lim = fmaf(tau32, 0x1p-19f, tau32);
+        // pass 2: FP64 distances of the points within that bound only
+        for (int r = 0; r < k; ++r) {
+            kd[r * 32] = INF64;
+            ki[r * 32] = 0x7fffffff;
+        }
+        cnt = 0;
+        for (int j = lane; j < W->n; j += 32) {
+            const float4 p = W->pts[j];
+            if (!(p.w < T32) || !(dist32(c, s0, s1, s2, s3, p) <= lim))
                 continue;
             const unsigned long long db =
                 (unsigned long long)__double_as_longlong(dist64(W->sigd, q, p));

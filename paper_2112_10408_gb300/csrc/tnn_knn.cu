@@ -184,9 +184,13 @@ tnn_status tnn_fill_window(const tnn_index *ix, const float *d_q, int64_t m,
     w->F = F;
     w->W0 = W0;
     {
+        // Deferral: a key that still reaches beyond defer_cells grid cells
+        // in space.  Every valid point is at least lag before the query, so
+        // every key carries at least sigma_t lag^2 of temporal distance;
+        // that floor is added so that a lag does not defer every query.
         const double dc = p->defer_cells == 0.0f ? 1.5 : (double)p->defer_cells;
         const double side = dc * (double)ix->grid.cell;
-        w->tau_defer = dc > 0.0 ? (float)(side * side) : INFINITY;
+        w->tau_defer = dc > 0.0 ? (float)(side * side + ix->sigma[3] * p->lag * p->lag) : INFINITY;
     }
     w->flags = p->flags;
     return TNN_OK;
@@ -575,6 +579,9 @@ extern "C" tnn_status tnn_autotune(const tnn_index *ix, tnn_knn_params *params,
     TNN_ARG_CHECK(m_sample >= 32, "m_sample must be >= 32");
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = ix->n;
+    // A sample too small to fill the GPU times the slowest warp, not the
+    // throughput: at least 262,144 queries (or all of them).
+    m_sample = std::max<int64_t>(m_sample, 262144);
     int64_t nblk = std::max<int64_t>(1, std::min<int64_t>(m_sample / 32, n / 32));
     if (n < 32)
         nblk = 1;
@@ -612,7 +619,7 @@ extern "C" tnn_status tnn_autotune(const tnn_index *ix, tnn_knn_params *params,
     std::vector<Cand> cands;
     for (int F : {2, 3, 4})
         for (int E : {4, 8})
-            for (float dfr : {0.75f, 1.5f, 3.0f})
+            for (float dfr : {0.75f, 1.5f, 3.0f, 6.0f})
                 cands.push_back({F, E, 0, dfr});
     for (int F : {3, 4})
         cands.push_back({F, 4, TNN_FLAG_SWEEP, 0.0f});
