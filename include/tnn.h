@@ -332,9 +332,13 @@ typedef struct {
 /*
  * Two-layer GELU MLP aggregator, d_in -> d_hidden -> 2 (the MLP of Sec. 3.2
  * used here to map a context to the wind at the query).  FP32 master
- * weights and AdamW moments on the device; BF16 operands with FP32
- * accumulation in the kernels.  Kaiming-uniform initialisation from `seed`.
- * d_in a multiple of 16 (<= 1024), d_hidden a multiple of 64 (<= 512).
+ * weights and AdamW moments on the device; the two products with the batch
+ * (X W1 and dW1 = X^T dZ) run on the tensor cores (tcgen05, BF16 operands,
+ * FP32 accumulation in TMEM), the head and the gradient epilogue in FP32.
+ * Kaiming-uniform initialisation from `seed`.  d_in a multiple of 16
+ * (<= 1024), d_hidden a multiple of 64 (<= 512).  A device wait of these
+ * kernels that times out (1 s) is reported by the next tnn_mlp_get_params
+ * as TNN_ERR_TIMEOUT.
  */
 tnn_status tnn_mlp_create(int32_t d_in, int32_t d_hidden, uint64_t seed,
                           tnn_mlp **out);
@@ -349,7 +353,8 @@ tnn_status tnn_mlp_get_params(const tnn_mlp *mlp, float *h_params,
 tnn_status tnn_mlp_set_params(tnn_mlp *mlp, const float *h_params,
                               const float *h_m, const float *h_v,
                               int64_t step);
-/* y [B][2] = MLP(x), x [B][d_in] bf16 (device). */
+/* y [B][2] = MLP(x), x [B][d_in] bf16 (device, 16-byte aligned).  Needs no
+   workspace. */
 tnn_status tnn_mlp_forward(const tnn_mlp *mlp, const uint16_t *d_x, int64_t B,
                            float *d_y, tnn_stream_t stream);
 /* Loss mean((y - target)^2) over B x 2 and its gradient in the flat layout

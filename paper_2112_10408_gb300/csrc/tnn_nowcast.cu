@@ -5,8 +5,8 @@
 //
 // MLP layout (flat FP32 master parameters, row-major):
 //   W1 [d_in][d_h] | b1 [d_h] | W2 [d_h][2] | b2 [2]
-// Forward  Z = X W1 + b1 (X, W1 in BF16, FP32 accumulation), H = GELU(Z)
-//          (kept in BF16), Y = H W2 + b2 (FP32).
+// Forward  Z = X W1 + b1 (X, W1 in BF16, FP32 accumulation on the tensor
+//          cores), H = GELU(Z) (rounded to BF16), Y = H W2 + b2 (FP32).
 // Backward of mean((Y - T)^2) over B x 2:
 //          dY = (Y - T) / B, dW2 = H^T dY, db2 = sum dY,
 //          dZ = (dY W2^T) * GELU'(Z) (BF16), dW1 = X^T dZ, db1 = sum dZ.
@@ -132,170 +132,52 @@ extern "C" tnn_status tnn_context_features(const tnn_index *ix, const float *d_w
     return TNN_OK;
 }
 
-// --------------------------------------------------------------- SIMT GEMM
+// ------------------------------------------------------------------- MLP
 
-// C(m, n) = sum_k A(m, k) B(k, n) with A, B in BF16 (strided), FP32
-// accumulation.  64 x 64 output tile per block of 256 threads (4 x 4 per
-// thread), K staged 16 at a time through shared memory.  blockIdx.z splits K.
-enum { EPI_FWD = 0, EPI_PARTIAL = 1 };
-
-struct GemmArgs {
-    const uint16_t *A;
-    long long lda_m, lda_k;
-    const uint16_t *B;
-    long long ldb_k, ldb_n;
-    int M, N, K;
-    int k_per_split;
-    // EPI_FWD: Z = acc + bias[n] (FP32), H = bf16(GELU(Z))
-    const float *bias;
-    float *Z;
-    uint16_t *H;
-    // EPI_PARTIAL: P[split][m][n] = acc
-    float *P;
-};
-
+// GELU(z) = z Phi(z) and GELU'(z) = Phi(z) + z phi(z), with the normal CDF
+// Phi(z) = (1 + erf(z / sqrt 2)) / 2 and density phi(z) = exp(-z^2 / 2) /
+// sqrt(2 pi).  erf by Abramowitz & Stegun, Handbook of Mathematical
+// Functions, formula 7.1.26: erf(x) = 1 - (a1 t + ... + a5 t^5) exp(-x^2),
+// t = 1 / (1 + p x) for x >= 0, absolute error <= 1.5e-7 -- far below the
+// BF16 rounding that H and dZ receive.  The same exp(-x^2) = exp(-z^2 / 2)
+// serves phi.  Returns (Phi(z), exp(-z^2 / 2)).
+__device__ __forceinline__ float2 normal_cdf_and_gauss(float z)
+{
+    const float x = z * 0.70710678118654752f;
+    const float ax = fabsf(x);
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));
+    float poly = fmaf(t, 1.061405429f, -1.453152027f);
+    poly = fmaf(t, poly, 1.421413741f);
+    poly = fmaf(t, poly, -0.284496736f);
+    poly = fmaf(t, poly, 0.254829592f);
+    poly *= t;
+    const float g = __expf(-ax * ax);
+    const float erf_ax = fmaf(-poly, g, 1.0f);
+    const float erf_x = copysignf(erf_ax, x);
+    return make_float2(fmaf(0.5f, erf_x, 0.5f), g);
+}
 __device__ __forceinline__ float gelu_f(float z)
 {
-    return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+    return z * normal_cdf_and_gauss(z).x;
 }
 __device__ __forceinline__ float gelu_grad_f(float z)
 {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
-           z * expf(-0.5f * z * z) * 0.39894228040143268f;
+    const float2 pg = normal_cdf_and_gauss(z);
+    return fmaf(z * 0.39894228040143268f, pg.y, pg.x);
 }
 
-template <int EPI>
-__global__ void __launch_bounds__(256) k_gemm_bf16(const __grid_constant__ GemmArgs g)
-{
-    __shared__ float As[16][64 + 4];
-    __shared__ float Bs[16][64 + 4];
-    const int tid = threadIdx.x;
-    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-    const int kb = blockIdx.z * g.k_per_split;
-    const int ke = min(g.K, kb + g.k_per_split);
-    const int tm = (tid >> 4) * 4, tn = (tid & 15) * 4;
-    float acc[4][4] = {};
-    for (int k0 = kb; k0 < ke; k0 += 16) {
-        for (int e = tid; e < 16 * 64; e += 256) {
-            const int kk = e >> 6, mm = e & 63;
-            const int gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < g.M && gk < ke) ? bf2f(g.A[gm * g.lda_m + gk * g.lda_k]) : 0.f;
-            const int gn = n0 + mm;
-            Bs[kk][mm] = (gn < g.N && gk < ke) ? bf2f(g.B[gk * g.ldb_k + gn * g.ldb_n]) : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                a[i] = As[kk][tm + i];
-                b[i] = Bs[kk][tn + i];
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int gm = m0 + tm + i;
-        if (gm >= g.M)
-            continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int gn = n0 + tn + j;
-            if (gn >= g.N)
-                continue;
-            if (EPI == EPI_FWD) {
-                const float z = acc[i][j] + g.bias[gn];
-                g.Z[(long long)gm * g.N + gn] = z;
-                g.H[(long long)gm * g.N + gn] = f2bf(gelu_f(z));
-            } else {
-                g.P[((long long)blockIdx.z * g.M + gm) * g.N + gn] = acc[i][j];
-            }
-        }
-    }
-}
+#include "tnn_mlp_tc.cuh"
 
-// Output head and its backward, one warp per row: Y = H W2 + b2; with a
-// target, dY = (Y - T)/B, dZ = (dY W2^T) * GELU'(Z) (BF16) and the squared
-// error summed into *sse.
-__global__ void k_head(const uint16_t *__restrict__ H, const float *__restrict__ Z,
-                       const float *__restrict__ W2, const float *__restrict__ b2,
-                       int B, int dh, float *__restrict__ Y,
-                       const float *__restrict__ T, float *__restrict__ dY,
-                       uint16_t *__restrict__ dZ, float *sse)
+// Position of W1[f][h] in the BF16 W1^T operand: K step f / 16 holds
+// [dh rows][16] in core-matrix order.
+__device__ __forceinline__ long long w1t_index(int f, int h, int dh)
 {
-    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (r >= B)
-        return;
-    float y0 = 0.f, y1 = 0.f;
-    for (int h = lane; h < dh; h += 32) {
-        const float hv = bf2f(H[(long long)r * dh + h]);
-        y0 = fmaf(hv, W2[2 * h], y0);
-        y1 = fmaf(hv, W2[2 * h + 1], y1);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        y0 += __shfl_xor_sync(FULLMASK, y0, o);
-        y1 += __shfl_xor_sync(FULLMASK, y1, o);
-    }
-    y0 += b2[0];
-    y1 += b2[1];
-    if (lane == 0 && Y) {
-        Y[2 * r] = y0;
-        Y[2 * r + 1] = y1;
-    }
-    if (!T)
-        return;
-    const float e0 = y0 - T[2 * r], e1 = y1 - T[2 * r + 1];
-    const float g0 = e0 / (float)B, g1 = e1 / (float)B; // d mean over 2B of e^2
-    if (lane == 0) {
-        dY[2 * r] = g0;
-        dY[2 * r + 1] = g1;
-        atomicAdd(sse, e0 * e0 + e1 * e1);
-    }
-    for (int h = lane; h < dh; h += 32) {
-        const float dh_ = fmaf(g0, W2[2 * h], g1 * W2[2 * h + 1]);
-        dZ[(long long)r * dh + h] = f2bf(dh_ * gelu_grad_f(Z[(long long)r * dh + h]));
-    }
-}
-
-// Column sums over row slices: partials of db1 [dh], dW2 [dh][2], db2 [2].
-__global__ void k_colsums(const uint16_t *__restrict__ H, const uint16_t *__restrict__ dZ,
-                          const float *__restrict__ dY, int B, int dh, int rows_per,
-                          float *__restrict__ part) // [splits][dh*3 + 2]
-{
-    const int s = blockIdx.x;
-    const int r0 = s * rows_per, r1 = min(B, r0 + rows_per);
-    const int stride = dh * 3 + 2;
-    for (int h = threadIdx.x; h < dh; h += blockDim.x) {
-        float db1 = 0.f, w0 = 0.f, w1 = 0.f;
-        for (int r = r0; r < r1; ++r) {
-            db1 += bf2f(dZ[(long long)r * dh + h]);
-            const float hv = bf2f(H[(long long)r * dh + h]);
-            w0 = fmaf(hv, dY[2 * r], w0);
-            w1 = fmaf(hv, dY[2 * r + 1], w1);
-        }
-        part[(long long)s * stride + h] = db1;
-        part[(long long)s * stride + dh + 2 * h] = w0;
-        part[(long long)s * stride + dh + 2 * h + 1] = w1;
-    }
-    if (threadIdx.x < 2) {
-        float g = 0.f;
-        for (int r = r0; r < r1; ++r)
-            g += dY[2 * r + threadIdx.x];
-        part[(long long)s * stride + 3 * dh + threadIdx.x] = g;
-    }
+    return (long long)(f >> 4) * dh * 16 + (kmaj_off_bf16(h, f & 15) >> 1);
 }
 
 struct AdamArgs {
     float *w, *m, *v;
-    uint16_t *w1_bf16;
+    uint16_t *w1t;    // BF16 W1^T operand, refreshed after the update
     float *grad_out; // if non-null: write the reduced gradient, no update
     const float *pW1; // [splits1][d_in*dh]
     int splits1;
@@ -303,16 +185,26 @@ struct AdamArgs {
     int splits2;
     int d_in, dh;
     long long P;
-    float lr, b1, b2, eps, wd, bc1, bc2;
+    float lr, b1, b2, eps, wd;
+    const long long *step; // already advanced for this update
     const float *sse;
     float *loss_out;
     float inv_count;
 };
 
 // Reduce the gradient partials and apply AdamW (decoupled weight decay),
-// refreshing the BF16 copy of W1.
+// refreshing the BF16 W1^T operand.
 __global__ void k_adamw(const __grid_constant__ AdamArgs a)
 {
+    __shared__ float s_bc[2];
+    if (threadIdx.x == 0 && !a.grad_out) {
+        // 1 - beta^t = -expm1(t log1p(beta - 1)): beta - 1 is exact in FP32
+        // and neither step cancels, so no FP64 is needed
+        const float t = (float)*a.step;
+        s_bc[0] = -expm1f(t * log1pf(a.b1 - 1.0f));
+        s_bc[1] = -expm1f(t * log1pf(a.b2 - 1.0f));
+    }
+    __syncthreads();
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p == 0 && a.loss_out)
         *a.loss_out = *a.sse * a.inv_count;
@@ -320,15 +212,31 @@ __global__ void k_adamw(const __grid_constant__ AdamArgs a)
         return;
     const long long nW1 = (long long)a.d_in * a.dh;
     const int stride = a.dh * 3 + 2;
-    float g = 0.f;
+    // partial sums over the batch slices: four independent chains so that
+    // the loads overlap (the order is fixed, so the result is deterministic)
+    const float *src;
+    long long ld;
+    int ns;
     if (p < nW1) {
-        for (int s = 0; s < a.splits1; ++s)
-            g += a.pW1[(long long)s * nW1 + p];
+        src = a.pW1 + p;
+        ld = nW1;
+        ns = a.splits1;
     } else {
-        const long long q = p - nW1; // b1 | W2 | b2 in the same order as pCol
-        for (int s = 0; s < a.splits2; ++s)
-            g += a.pCol[(long long)s * stride + q];
+        src = a.pCol + (p - nW1); // b1 | W2 | b2 in the same order as pCol
+        ld = stride;
+        ns = a.splits2;
     }
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
+    int s = 0;
+    for (; s + 4 <= ns; s += 4) {
+        g0 += src[(long long)s * ld];
+        g1 += src[(long long)(s + 1) * ld];
+        g2 += src[(long long)(s + 2) * ld];
+        g3 += src[(long long)(s + 3) * ld];
+    }
+    for (; s < ns; ++s)
+        g0 += src[(long long)s * ld];
+    const float g = (g0 + g1) + (g2 + g3);
     if (a.grad_out) {
         a.grad_out[p] = g;
         return;
@@ -337,18 +245,19 @@ __global__ void k_adamw(const __grid_constant__ AdamArgs a)
     const float v = a.b2 * a.v[p] + (1.f - a.b2) * g * g;
     a.m[p] = m;
     a.v[p] = v;
-    const float mh = m / a.bc1, vh = v / a.bc2;
+    const float mh = m / s_bc[0], vh = v / s_bc[1];
     const float w = a.w[p] - a.lr * (mh / (sqrtf(vh) + a.eps) + a.wd * a.w[p]);
     a.w[p] = w;
     if (p < nW1)
-        a.w1_bf16[p] = f2bf(w);
+        a.w1t[w1t_index((int)(p / a.dh), (int)(p % a.dh), a.dh)] = f2bf(w);
 }
 
-__global__ void k_to_bf16(const float *__restrict__ x, uint16_t *__restrict__ y, long long n)
+// The BF16 W1^T operand from the FP32 master W1 [d_in][dh].
+__global__ void k_to_w1t(const float *__restrict__ w, uint16_t *__restrict__ w1t, int d_in, int dh)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n)
-        y[i] = f2bf(x[i]);
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < (long long)d_in * dh)
+        w1t[w1t_index((int)(p / dh), (int)(p % dh), dh)] = f2bf(w[p]);
 }
 
 // ---------------------------------------------------------------- objects
@@ -358,29 +267,28 @@ struct tnn_mlp {
     int d_in, dh;
     long long P;
     float *w, *m, *v;
-    uint16_t *w1b;
-    long long step;
-    // workspace, grown on demand
-    long long cap_B;
-    float *Z, *dY, *Y, *pW1, *pCol, *grad, *acc; // acc: [0] sse, [1] loss
-    uint16_t *H, *dZ;
-    int splits1, splits2;
+    uint16_t *w1t; // BF16 W1^T in the tensor-core operand order
+    float *acc;    // [0] squared error, [1] loss
+    int *err;      // set by a kernel whose device wait timed out
+    long long *step; // AdamW step count, on the device (CUDA-graph replays advance it)
+    // training workspace, grown on demand
+    long long cap_B, ldt;
+    float *dY, *Y, *pW1, *pCol, *grad;
+    uint16_t *Xt, *dZt;
 };
 
 static void mlp_free_ws(tnn_mlp *n)
 {
-    cudaFree(n->Z);
     cudaFree(n->dY);
     cudaFree(n->Y);
     cudaFree(n->pW1);
     cudaFree(n->pCol);
     cudaFree(n->grad);
-    cudaFree(n->acc);
-    cudaFree(n->H);
-    cudaFree(n->dZ);
-    n->Z = n->dY = n->Y = n->pW1 = n->pCol = n->grad = n->acc = nullptr;
-    n->H = n->dZ = nullptr;
-    n->cap_B = 0;
+    cudaFree(n->Xt);
+    cudaFree(n->dZt);
+    n->dY = n->Y = n->pW1 = n->pCol = n->grad = nullptr;
+    n->Xt = n->dZt = nullptr;
+    n->cap_B = n->ldt = 0;
 }
 
 extern "C" void tnn_mlp_destroy(tnn_mlp *n)
@@ -391,31 +299,45 @@ extern "C" void tnn_mlp_destroy(tnn_mlp *n)
     cudaFree(n->w);
     cudaFree(n->m);
     cudaFree(n->v);
-    cudaFree(n->w1b);
+    cudaFree(n->w1t);
+    cudaFree(n->acc);
+    cudaFree(n->err);
+    cudaFree(n->step);
     delete n;
 }
 
+#define MLP_MAX_SPLITS 64
+
+// Batch slices of the dW1 product: at most MLP_MAX_SPLITS, each a multiple
+// of 16 rows.
+static long long mlp_rows_per_split(long long B)
+{
+    const long long Bp = (B + 15) / 16 * 16;
+    long long rows = (Bp + MLP_MAX_SPLITS - 1) / MLP_MAX_SPLITS;
+    rows = std::max<long long>(128, (rows + 15) / 16 * 16);
+    return rows;
+}
+
+// Training workspace for batches of up to B rows (inference needs none).
 static tnn_status mlp_reserve(tnn_mlp *n, long long B)
 {
     if (B <= n->cap_B)
         return TNN_OK;
     mlp_free_ws(n);
     const long long cap = std::max<long long>(B, 256);
-    n->splits1 = (int)std::min<long long>(32, (cap + 127) / 128);
-    n->splits2 = (int)std::min<long long>(64, (cap + 63) / 64);
+    const long long ldt = (cap + 15) / 16 * 16;
+    const long long nW1 = (long long)n->d_in * n->dh;
     cudaError_t e = cudaSuccess;
 #define A_(p, bytes)                                                          \
     if (e == cudaSuccess)                                                     \
         e = cudaMalloc((void **)&(p), (bytes));
-    A_(n->Z, sizeof(float) * cap * n->dh);
-    A_(n->H, sizeof(uint16_t) * cap * n->dh);
-    A_(n->dZ, sizeof(uint16_t) * cap * n->dh);
     A_(n->dY, sizeof(float) * cap * 2);
     A_(n->Y, sizeof(float) * cap * 2);
-    A_(n->pW1, sizeof(float) * n->splits1 * (long long)n->d_in * n->dh);
-    A_(n->pCol, sizeof(float) * n->splits2 * (long long)(3 * n->dh + 2));
+    A_(n->pW1, sizeof(float) * MLP_MAX_SPLITS * nW1);
+    A_(n->pCol, sizeof(float) * ((cap + MLP_ROWS - 1) / MLP_ROWS) * (3LL * n->dh + 2));
     A_(n->grad, sizeof(float) * n->P);
-    A_(n->acc, sizeof(float) * 4);
+    A_(n->Xt, sizeof(uint16_t) * n->d_in * ldt);
+    A_(n->dZt, sizeof(uint16_t) * n->dh * ldt);
 #undef A_
     if (e != cudaSuccess) {
         mlp_free_ws(n);
@@ -423,6 +345,7 @@ static tnn_status mlp_reserve(tnn_mlp *n, long long B)
         return e == cudaErrorMemoryAllocation ? TNN_ERR_OOM : TNN_ERR_CUDA;
     }
     n->cap_B = cap;
+    n->ldt = ldt;
     return TNN_OK;
 }
 
@@ -466,7 +389,17 @@ extern "C" tnn_status tnn_mlp_create(int32_t d_in, int32_t d_hidden, uint64_t se
     if (e == cudaSuccess)
         e = cudaMalloc(&n->v, sizeof(float) * n->P);
     if (e == cudaSuccess)
-        e = cudaMalloc(&n->w1b, sizeof(uint16_t) * nW1);
+        e = cudaMalloc(&n->w1t, sizeof(uint16_t) * nW1);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&n->acc, sizeof(float) * 4);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&n->err, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&n->step, sizeof(long long));
+    if (e == cudaSuccess)
+        e = cudaMemset(n->step, 0, sizeof(long long));
+    if (e == cudaSuccess)
+        e = cudaMemset(n->err, 0, sizeof(int));
     if (e == cudaSuccess)
         e = cudaMemcpy(n->w, h.data(), sizeof(float) * n->P, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -474,7 +407,7 @@ extern "C" tnn_status tnn_mlp_create(int32_t d_in, int32_t d_hidden, uint64_t se
     if (e == cudaSuccess)
         e = cudaMemset(n->v, 0, sizeof(float) * n->P);
     if (e == cudaSuccess) {
-        k_to_bf16<<<(unsigned)((nW1 + 255) / 256), 256>>>(n->w, n->w1b, nW1);
+        k_to_w1t<<<(unsigned)((nW1 + 255) / 256), 256>>>(n->w, n->w1t, d_in, d_hidden);
         e = cudaDeviceSynchronize();
     }
     if (e != cudaSuccess) {
@@ -494,6 +427,12 @@ extern "C" tnn_status tnn_mlp_get_params(const tnn_mlp *n, float *h_params, floa
     tnn_clear_error();
     TNN_ARG_CHECK(n != nullptr, "mlp is NULL");
     TNN_CUDA_TRY(cudaDeviceSynchronize());
+    int derr = 0;
+    TNN_CUDA_TRY(cudaMemcpy(&derr, n->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (derr) {
+        tnn_set_error("a device wait of the MLP kernels timed out");
+        return TNN_ERR_TIMEOUT;
+    }
     if (h_params)
         TNN_CUDA_TRY(cudaMemcpy(h_params, n->w, sizeof(float) * n->P, cudaMemcpyDeviceToHost));
     if (h_m)
@@ -501,7 +440,7 @@ extern "C" tnn_status tnn_mlp_get_params(const tnn_mlp *n, float *h_params, floa
     if (h_v)
         TNN_CUDA_TRY(cudaMemcpy(h_v, n->v, sizeof(float) * n->P, cudaMemcpyDeviceToHost));
     if (h_step)
-        *h_step = n->step;
+        TNN_CUDA_TRY(cudaMemcpy(h_step, n->step, sizeof(long long), cudaMemcpyDeviceToHost));
     return TNN_OK;
 }
 
@@ -521,40 +460,72 @@ extern "C" tnn_status tnn_mlp_set_params(tnn_mlp *n, const float *h_params, cons
         TNN_CUDA_TRY(cudaMemcpy(n->v, h_v, sizeof(float) * n->P, cudaMemcpyHostToDevice));
     else
         TNN_CUDA_TRY(cudaMemset(n->v, 0, sizeof(float) * n->P));
-    n->step = step;
+    {
+        const long long hs = step;
+        TNN_CUDA_TRY(cudaMemcpy(n->step, &hs, sizeof(long long), cudaMemcpyHostToDevice));
+    }
     const long long nW1 = (long long)n->d_in * n->dh;
-    k_to_bf16<<<(unsigned)((nW1 + 255) / 256), 256>>>(n->w, n->w1b, nW1);
+    k_to_w1t<<<(unsigned)((nW1 + 255) / 256), 256>>>(n->w, n->w1t, n->d_in, n->dh);
     TNN_CUDA_TRY(cudaDeviceSynchronize());
+    return TNN_OK;
+}
+
+// Dynamic shared memory of a tensor-core kernel, raised so that no more CTAs
+// share an SM than its TMEM (512 columns) holds at once.
+static size_t tc_smem_request(size_t need, uint32_t cols)
+{
+    int dev = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const int max_ctas = (int)(512 / cols);
+    const size_t floor_ = (size_t)per_sm / (size_t)(max_ctas + 1); // (max_ctas + 1) x (smem + 1 KB) > per SM
+    return std::max(need, floor_);
+}
+
+static tnn_status mlp_setup()
+{
+    static bool done = false;
+    if (!done) {
+        TNN_CUDA_TRY(cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        TNN_CUDA_TRY(cudaFuncSetAttribute(k_mlp_dw1_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        done = true;
+    }
     return TNN_OK;
 }
 
 static tnn_status mlp_forward_impl(const tnn_mlp *n, const uint16_t *d_x, long long B,
                                    float *d_y, const float *d_t, cudaStream_t st)
 {
+    TNN_ARG_CHECK(((uintptr_t)d_x & 15) == 0, "X must be 16-byte aligned");
+    tnn_status s = mlp_setup();
+    if (s != TNN_OK)
+        return s;
     const long long nW1 = (long long)n->d_in * n->dh;
-    GemmArgs g;
-    memset(&g, 0, sizeof(g));
-    g.A = d_x;
-    g.lda_m = n->d_in;
-    g.lda_k = 1;
-    g.B = n->w1b;
-    g.ldb_k = n->dh;
-    g.ldb_n = 1;
-    g.M = (int)B;
-    g.N = n->dh;
-    g.K = n->d_in;
-    g.k_per_split = n->d_in;
-    g.bias = n->w + nW1;
-    g.Z = n->Z;
-    g.H = n->H;
-    dim3 grid((n->dh + 63) / 64, (unsigned)((B + 63) / 64), 1);
-    k_gemm_bf16<EPI_FWD><<<grid, 256, 0, st>>>(g);
-    const float *W2 = n->w + nW1 + n->dh;
-    const float *b2 = W2 + 2 * n->dh;
+    MlpFwdArgs a;
+    memset(&a, 0, sizeof(a));
+    a.X = d_x;
+    a.B = B;
+    a.d_in = n->d_in;
+    a.dh = n->dh;
+    a.w1t = n->w1t;
+    a.b1 = n->w + nW1;
+    a.W2 = a.b1 + n->dh;
+    a.b2 = a.W2 + 2 * n->dh;
+    a.Y = d_y;
+    a.T = d_t;
+    a.dY = n->dY;
+    a.dZt = n->dZt;
+    a.Xt = n->Xt;
+    a.ldt = n->ldt;
+    a.pCol = n->pCol;
+    a.sse = n->acc;
+    a.inv_B = 1.0f / (float)B;
+    a.tmem_cols = tmem_cols_for(n->dh);
+    a.err = n->err;
     if (d_t)
         TNN_CUDA_TRY(cudaMemsetAsync(n->acc, 0, sizeof(float) * 4, st));
-    k_head<<<(unsigned)((B * 32 + 255) / 256), 256, 0, st>>>(
-        n->H, n->Z, W2, b2, (int)B, n->dh, d_y, d_t, n->dY, n->dZ, n->acc);
+    const size_t smem = tc_smem_request(mlp_fwd_smem(n->dh), a.tmem_cols);
+    k_mlp_fwd_tc<<<(unsigned)((B + MLP_ROWS - 1) / MLP_ROWS), MLP_FWD_THREADS, smem, st>>>(a);
     TNN_CUDA_TRY(cudaGetLastError());
     return TNN_OK;
 }
@@ -565,9 +536,6 @@ extern "C" tnn_status tnn_mlp_forward(const tnn_mlp *n, const uint16_t *d_x, int
     tnn_clear_error();
     TNN_ARG_CHECK(n && d_x && d_y, "NULL argument");
     TNN_ARG_CHECK(B >= 1 && B < (1ll << 31) / 512, "B out of range");
-    tnn_status s = mlp_reserve(const_cast<tnn_mlp *>(n), B);
-    if (s != TNN_OK)
-        return s;
     return mlp_forward_impl(n, d_x, B, d_y, nullptr, (cudaStream_t)stream);
 }
 
@@ -578,38 +546,37 @@ static tnn_status mlp_backward_impl(tnn_mlp *n, const uint16_t *d_x, long long B
     tnn_status s = mlp_forward_impl(n, d_x, B, n->Y, d_t, st);
     if (s != TNN_OK)
         return s;
-    // dW1 partials: X^T dZ, split over the batch.
-    GemmArgs g;
-    memset(&g, 0, sizeof(g));
-    g.A = d_x;
-    g.lda_m = 1;
-    g.lda_k = n->d_in;
-    g.B = n->dZ;
-    g.ldb_k = n->dh;
-    g.ldb_n = 1;
-    g.M = n->d_in;
-    g.N = n->dh;
-    g.K = (int)B;
-    g.k_per_split = (int)((B + n->splits1 - 1) / n->splits1);
-    g.k_per_split = (g.k_per_split + 15) / 16 * 16;
-    g.P = n->pW1;
-    const int used1 = (int)((B + g.k_per_split - 1) / g.k_per_split);
-    dim3 grid((n->dh + 63) / 64, (n->d_in + 63) / 64, used1);
-    k_gemm_bf16<EPI_PARTIAL><<<grid, 256, 0, st>>>(g);
-    const int rows_per = (int)((B + n->splits2 - 1) / n->splits2);
-    const int used2 = (int)((B + rows_per - 1) / rows_per);
-    k_colsums<<<used2, 256, 0, st>>>(n->H, n->dZ, n->dY, (int)B, n->dh, rows_per, n->pCol);
+    // dW1^T = dZ^T X over batch slices
+    const long long rows_per = mlp_rows_per_split(B);
+    const long long Bp = (B + 15) / 16 * 16;
+    const int splits1 = (int)((Bp + rows_per - 1) / rows_per);
+    MlpDw1Args d;
+    memset(&d, 0, sizeof(d));
+    d.dZt = n->dZt;
+    d.Xt = n->Xt;
+    d.ldt = n->ldt;
+    d.Bp = Bp;
+    d.d_in = n->d_in;
+    d.dh = n->dh;
+    d.rows_per = rows_per;
+    d.pW1 = n->pW1;
+    d.tmem_cols = tmem_cols_for(std::min(256, n->d_in));
+    d.err = n->err;
+    d.step_inc = opt ? n->step : nullptr;
+    dim3 grid((unsigned)((n->dh + 127) / 128), (unsigned)((n->d_in + 255) / 256), (unsigned)splits1);
+    k_mlp_dw1_tc<<<grid, MLP_ROWS, tc_smem_request(mlp_dw1_smem(), d.tmem_cols), st>>>(d);
+    TNN_CUDA_TRY(cudaGetLastError());
     AdamArgs a;
     memset(&a, 0, sizeof(a));
     a.w = n->w;
     a.m = n->m;
     a.v = n->v;
-    a.w1_bf16 = n->w1b;
+    a.w1t = n->w1t;
     a.grad_out = d_grad;
     a.pW1 = n->pW1;
-    a.splits1 = used1;
+    a.splits1 = splits1;
     a.pCol = n->pCol;
-    a.splits2 = used2;
+    a.splits2 = (int)((B + MLP_ROWS - 1) / MLP_ROWS);
     a.d_in = n->d_in;
     a.dh = n->dh;
     a.P = n->P;
@@ -617,14 +584,12 @@ static tnn_status mlp_backward_impl(tnn_mlp *n, const uint16_t *d_x, long long B
     a.loss_out = d_loss;
     a.inv_count = 1.0f / (2.0f * (float)B);
     if (opt) {
-        n->step += 1;
         a.lr = opt->lr;
         a.b1 = opt->beta1;
         a.b2 = opt->beta2;
         a.eps = opt->eps;
         a.wd = opt->weight_decay;
-        a.bc1 = (float)(1.0 - pow((double)opt->beta1, (double)n->step));
-        a.bc2 = (float)(1.0 - pow((double)opt->beta2, (double)n->step));
+        a.step = n->step;
     }
     k_adamw<<<(unsigned)((n->P + 255) / 256), 256, 0, st>>>(a);
     TNN_CUDA_TRY(cudaGetLastError());

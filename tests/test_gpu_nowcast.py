@@ -170,3 +170,32 @@ def test_trained_mlp_beats_idw_on_held_out_flights():
     print(f"held-out RMSE (m/s): MLP {rmse_mlp:.3f}  IDW {rmse_idw:.3f}")
     assert rmse_mlp < rmse_idw
     assert rmse_mlp > 0.9  # the noise floor is 1 m/s per component
+
+
+def test_training_steps_replayed_from_a_cuda_graph_match_eager_steps():
+    # The AdamW step count lives on the device, so a captured sequence of
+    # train steps replays with the right bias corrections.
+    rng = np.random.default_rng(11)
+    xs = [torch.from_numpy(rng.normal(0, 1, size=(640, 96)).astype(np.float32)).to(torch.bfloat16).cuda()
+          for _ in range(4)]
+    ts = [torch.from_numpy(rng.normal(0, 1, size=(640, 2)).astype(np.float32)).cuda() for _ in range(4)]
+    opt = tnn.AdamW(lr=2e-3, weight_decay=1e-2)
+    eager = tnn.MLP(96, 128, seed=21)
+    for x, t in zip(xs, ts):
+        eager.train_step(x, t, opt)
+    graphed = tnn.MLP(96, 128, seed=21)
+    graphed.gradients(xs[0], ts[0])  # sizes the workspace; no update
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for x, t in zip(xs, ts):
+            graphed.train_step(x, t, opt)
+    g.replay()
+    torch.cuda.synchronize()
+    a = eager.get_params(with_moments=True)
+    b = graphed.get_params(with_moments=True)
+    for x, y in zip(a[:3], b[:3]):
+        np.testing.assert_array_equal(x, y)
+    assert a[3] == b[3] == 4
+    g.replay()  # four more steps
+    assert graphed.get_params(with_moments=True)[3] == 8
