@@ -39,10 +39,10 @@ OPS_PER_KEY = 20
 # summarised in profiles/k_tnn_grid_search_medium.md, with a hash of the
 # kernel sources it was taken on: once they change the figure is stale and
 # is reported as null.
-SEARCH_TRAFFIC = {"bytes": 44539392 + 6872320 + 19712, "workload": "medium",
+SEARCH_TRAFFIC = {"bytes": 44277760 + 6875648 + 113408, "workload": "medium",
                   "sources": ["tnn_device.cuh", "tnn_grid.cuh", "tnn_fallback.cuh", "tnn_internal.cuh",
                               "tnn_knn.cu"],
-                  "sha256_16": "e94dc4d3ff2528b2"}
+                  "sha256_16": "dd79ed4c7864b387"}
 
 
 def _search_traffic(workload):
@@ -199,6 +199,22 @@ def run_reference(a):
     return 0
 
 
+class _Range:
+    """NVTX range around a measured section (lets ncu select its kernels with
+    --nvtx --nvtx-include "<name>/")."""
+
+    def __init__(self, name):
+        self.name = name
+
+    def __enter__(self):
+        import torch
+        torch.cuda.nvtx.range_push(self.name)
+
+    def __exit__(self, *exc):
+        import torch
+        torch.cuda.nvtx.range_pop()
+
+
 def _timed(fn, steps, flush=None):
     """Mean CUDA-event time (ms) of fn() over `steps` runs, L2 flushed before each."""
     import torch
@@ -231,7 +247,8 @@ def _extras(tnn, synth, flush, peaks, steps):
     for _ in range(3):
         b.run()
     torch.cuda.synchronize()
-    ms = _timed(b.run, steps, flush)
+    with _Range("batched"):
+        ms = _timed(b.run, steps, flush)
     nq = sum(wl.n for wl, _ in wins)
     out["batched"] = {"metric": "causal k-NN contexts/s over 64 windows in one persistent launch",
                       "value": nq / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "windows": len(wins),
@@ -253,7 +270,8 @@ def _extras(tnn, synth, flush, peaks, steps):
     tune = tnn.tnn_autotune(ix, k, lag)
     tnn.tnn_knn(ix, k, lag, out=(idx, d2), **tune)
     torch.cuda.synchronize()
-    ms_knn = _timed(lambda: tnn.tnn_knn(ix, k, lag, out=(idx, d2), **tune), steps, flush)
+    with _Range("learned_contexts"):
+        ms_knn = _timed(lambda: tnn.tnn_knn(ix, k, lag, out=(idx, d2), **tune), steps, flush)
     full = (idx >= 0).all(dim=1).cpu().numpy()
     train, test = synth.flight_split(wl)
     tr = np.nonzero(train & full)[0]
@@ -264,7 +282,8 @@ def _extras(tnn, synth, flush, peaks, steps):
     std = f.std(dim=(0, 1)).cpu().numpy() + 1e-6
     del f, raw
     feat, _ = tnn.tnn_context_features(ix, wind, idx, d2, mean=mean, std=std, want_idw=False)
-    ms_feat = _timed(lambda: tnn.tnn_context_features(ix, wind, idx, d2, mean=mean, std=std), steps, flush)
+    with _Range("features"):
+        ms_feat = _timed(lambda: tnn.tnn_context_features(ix, wind, idx, d2, mean=mean, std=std), steps, flush)
     # bytes per context: idx + d2 (8 k), gathered point + wind (24 k), query
     # point (16), features out (12 k bf16), IDW out (8)
     feat_bytes = wl.n * (44 * k + 24)
@@ -305,12 +324,14 @@ def _extras(tnn, synth, flush, peaks, steps):
             mlp.train_step(xb, yb, opt)
     graph.replay()
     torch.cuda.synchronize()
-    ms_graph = _timed(graph.replay, steps) / G
+    with _Range("mlp_train"):
+        ms_graph = _timed(graph.replay, steps) / G
     ted = torch.from_numpy(te).cuda()
     xte = feat[ted].contiguous()
     mlp.forward(xte)  # sizes the workspace outside the timed runs
     torch.cuda.synchronize()
-    ms_fwd = _timed(lambda: mlp.forward(xte), steps)
+    with _Range("mlp_forward"):
+        ms_fwd = _timed(lambda: mlp.forward(xte), steps)
     pred = mlp.forward(xte)
     rmse_mlp = float(torch.sqrt(((pred - wind[ted]) ** 2).mean()))
     rmse_idw = float(torch.sqrt(((idw[ted] - wind[ted]) ** 2).mean()))
@@ -406,12 +427,13 @@ def run_ours(a):
     sampler.start()
     tnn.tnn_profile_read(reset=True)
     tnn.tnn_profile_enable(True)
-    for s in range(a.steps):
-        flush.zero_()
-        ev[s][0].record()
-        step()
-        ev[s][1].record()
-    torch.cuda.synchronize()
+    with _Range("tnn_search"):
+        for s in range(a.steps):
+            flush.zero_()
+            ev[s][0].record()
+            step()
+            ev[s][1].record()
+        torch.cuda.synchronize()
     tnn.tnn_profile_enable(False)
     kern_ms, launches = tnn.tnn_profile_read(reset=True)
     if world > 1:
@@ -457,6 +479,8 @@ def run_ours(a):
             torch.cuda.synchronize()
             _, _, cst = tnn.tnn_knn_bruteforce(ix, k, 0.0, out=(bi, bd), ffma=ffma, stats=True)
             cms = []
+            rng_ = _Range("linear_cuda_core" if ffma else "linear_tensor_core")
+            rng_.__enter__()
             for _ in range(a.comparator_steps):
                 flush.zero_()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -465,6 +489,7 @@ def run_ours(a):
                 e1.record()
                 torch.cuda.synchronize()
                 cms.append(e0.elapsed_time(e1))
+            rng_.__exit__(None, None, None)
             cmean = sum(cms) / len(cms)
             ent = {"kernel": "k_linear_search" if ffma else "k_linear_tc",
                    "value": m / (cmean / 1e3), "unit": UNIT, "ms_per_step": cmean,
