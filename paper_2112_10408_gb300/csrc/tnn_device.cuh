@@ -150,29 +150,109 @@ __device__ __forceinline__ int warp_count_less(Get get, int n, float T, int lane
     return lo + __popc(__ballot_sync(FULLMASK, lt));
 }
 
-__device__ __forceinline__ void lane_insert(unsigned long long *K, int L,
-                                            unsigned long long key)
+// Candidate list of one query held as a heap (used where one thread serves
+// one query without warp-wide divergence costs, e.g. the tensor-core linear
+// search): at most L keys in a shared-memory column whose slots are S keys
+// apart.  While fewer than L are kept a key is appended (slots beyond hold
+// SENT); at L keys the column becomes a binary max-heap, and from then on a
+// smaller key replaces the root and sinks (log2 L levels of two independent
+// loads).  list_sort restores ascending order for the settlement.
+template <int S>
+__device__ __forceinline__ void heap_sink(unsigned long long *K, int n, int i, unsigned long long v)
 {
-    int i = L - 1;
 #pragma unroll 1
-    while (i > 0) {
-        unsigned long long pv = K[(i - 1) * 32];
-        if (pv < key)
+    for (;;) {
+        const int l = 2 * i + 1;
+        if (l >= n)
             break;
-        K[i * 32] = pv;
-        --i;
+        unsigned long long cv = K[l * S];
+        int c = l;
+        if (l + 1 < n) {
+            const unsigned long long rv = K[(l + 1) * S];
+            if (rv > cv) {
+                cv = rv;
+                c = l + 1;
+            }
+        }
+        if (cv <= v)
+            break;
+        K[i * S] = cv;
+        i = c;
     }
-    K[i * 32] = key;
+    K[i * S] = v;
+}
+
+// Add `key` (the caller checked key < the returned bound) and return the new
+// pruning key: the L-th smallest key kept, SENT while fewer than L are kept.
+template <int S>
+__device__ __forceinline__ unsigned long long list_push(unsigned long long *K, int L, int &nv,
+                                                        unsigned long long key)
+{
+    if (nv < L) {
+        K[nv * S] = key;
+        if (++nv < L)
+            return SENT;
+#pragma unroll 1
+        for (int i = L / 2 - 1; i >= 0; --i)
+            heap_sink<S>(K, L, i, K[i * S]);
+    } else {
+        heap_sink<S>(K, L, 0, key);
+    }
+    return K[0];
+}
+
+// Ascending order of the nv kept keys (heapsort; slots nv.. keep SENT).
+template <int S>
+__device__ __forceinline__ void list_sort(unsigned long long *K, int nv)
+{
+#pragma unroll 1
+    for (int i = nv / 2 - 1; i >= 0; --i)
+        heap_sink<S>(K, nv, i, K[i * S]);
+#pragma unroll 1
+    for (int end = nv - 1; end > 0; --end) {
+        const unsigned long long top = K[0];
+        const unsigned long long last = K[end * S];
+        K[end * S] = top;
+        heap_sink<S>(K, end, 0, last);
+    }
 }
 
 // Sorted candidate list of one lane (stride 32 in shared memory) holding
-// nv <= L keys; slots nv..L-1 hold SENT.  Insert `key` (caller checked
-// key < tauk) and return the new pruning key: the L-th smallest key kept,
-// SENT while fewer than L are kept.
-__device__ __forceinline__ unsigned long long lane_push(unsigned long long *K, int L,
-                                                        int &nv, unsigned long long key)
+// nv <= L keys; slots nv..L-1 hold SENT.  Insert `key` (the caller checked
+// key < the returned bound) and return the new pruning key: the L-th smallest
+// key kept, SENT while fewer than L are kept.  The lanes of a warp insert at
+// different moments, so the cost that matters is the latency of one
+// insertion: the shift reads four slots ahead, so that its loads do not wait
+// on one another.  (A heap has a one-time build and data-dependent sift
+// depths that serialise across the warp's lanes.)
+__device__ __forceinline__ unsigned long long lane_push(unsigned long long *K, int L, int &nv,
+                                                        unsigned long long key)
 {
     int i = nv < L ? nv : L - 1;
+#pragma unroll 1
+    while (i >= 4) {
+        const unsigned long long a = K[(i - 1) * 32], b = K[(i - 2) * 32];
+        const unsigned long long c = K[(i - 3) * 32], d = K[(i - 4) * 32];
+        if (a < key)
+            goto place;
+        K[i * 32] = a;
+        if (b < key) {
+            i -= 1;
+            goto place;
+        }
+        K[(i - 1) * 32] = b;
+        if (c < key) {
+            i -= 2;
+            goto place;
+        }
+        K[(i - 2) * 32] = c;
+        if (d < key) {
+            i -= 3;
+            goto place;
+        }
+        K[(i - 3) * 32] = d;
+        i -= 4;
+    }
 #pragma unroll 1
     while (i > 0) {
         const unsigned long long pv = K[(i - 1) * 32];
@@ -181,6 +261,7 @@ __device__ __forceinline__ unsigned long long lane_push(unsigned long long *K, i
         K[i * 32] = pv;
         --i;
     }
+place:
     K[i * 32] = key;
     if (nv < L)
         ++nv;

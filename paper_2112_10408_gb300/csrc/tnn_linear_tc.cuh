@@ -120,66 +120,6 @@ __device__ __forceinline__ float tc_neg_T(float thr)
     return -tf32_rna(fmaf(thr, 0x1p-8f, thr) + 0x1p-100f);
 }
 
-// Candidate list of one query: at most Lw keys in a shared-memory column
-// (slots TC_Q keys apart).  Until it is full a key is appended; at Lw keys the
-// column becomes a binary max-heap, and from then on a smaller key replaces
-// the root and sinks (log2 Lw levels, two independent loads per level).
-// Returns the key a candidate must beat (SENT until the list is full).
-__device__ __forceinline__ void tc_heap_sink(unsigned long long *K, int Lw, int i, unsigned long long v)
-{
-    for (;;) {
-        const int l = 2 * i + 1;
-        if (l >= Lw)
-            break;
-        unsigned long long cv = K[l * TC_Q];
-        int c = l;
-        if (l + 1 < Lw) {
-            const unsigned long long rv = K[(l + 1) * TC_Q];
-            if (rv > cv) {
-                cv = rv;
-                c = l + 1;
-            }
-        }
-        if (cv <= v)
-            break;
-        K[i * TC_Q] = cv;
-        i = c;
-    }
-    K[i * TC_Q] = v;
-}
-
-__device__ __forceinline__ unsigned long long tc_list_put(unsigned long long *K, int Lw, int &nv,
-                                                          unsigned long long key)
-{
-    if (nv < Lw) {
-        K[nv * TC_Q] = key;
-        if (++nv < Lw)
-            return SENT;
-        for (int i = Lw / 2 - 1; i >= 0; --i)
-            tc_heap_sink(K, Lw, i, K[i * TC_Q]);
-    } else {
-        tc_heap_sink(K, Lw, 0, key);
-    }
-    return K[0];
-}
-
-// Ascending order of the nv keys of a column (insertion sort, once per tile).
-__device__ __forceinline__ void tc_list_sort(unsigned long long *K, int nv)
-{
-    for (int i = 1; i < nv; ++i) {
-        const unsigned long long v = K[i * TC_Q];
-        int j = i;
-        while (j > 0) {
-            const unsigned long long u = K[(j - 1) * TC_Q];
-            if (u <= v)
-                break;
-            K[j * TC_Q] = u;
-            --j;
-        }
-        K[j * TC_Q] = v;
-    }
-}
-
 __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const __grid_constant__ KnnLaunch L)
 {
     extern __shared__ __align__(16) unsigned char smem[]; // no-swizzle operands need 16 B
@@ -478,7 +418,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const __grid_consta
                                     if (p.w < c.T32 && d <= tau) {
                                         const unsigned long long key = pack_key(d, sidx[s * TC_P + col]);
                                         if (key < tauk) {
-                                            tauk = tc_list_put(K, Lw, nv, key);
+                                            tauk = list_push<TC_Q>(K, Lw, nv, key);
                                             tau = key_d(tauk);
                                         }
                                     }
@@ -501,7 +441,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const __grid_consta
             break;
         if (active) {
             st.q++;
-            tc_list_sort(K, nv);
+            list_sort<TC_Q>(K, nv);
             if (!finalize_query(W, q, K, Lw, cl_d, cl_i, qrow, st, TC_Q)) {
                 const unsigned fslot = atomicAdd(&L.scr->n_fallback, 1u);
                 if (fslot < (unsigned long long)L.fb_cap)
