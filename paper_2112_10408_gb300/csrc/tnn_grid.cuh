@@ -114,16 +114,32 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_GRID_MINB)
                 return;
             st.segs++;
             st.pairs += cnt;
-            for (int j = 0; j < cnt; ++j) {
-                const float4 p = pbuf[j];
-                const float d = dist32(c, s0, s1, s2, s3, p);
+            // newest member first: along a trajectory the members nearest a
+            // later query come last, and keys arriving in ascending order
+            // make the sorted insertion an append
+            auto consider = [&](const float4 &p, float d, int id) {
                 if (p.w < c.T32 && d <= tau) {
-                    const unsigned long long key = pack_key(d, first + j);
+                    const unsigned long long key = pack_key(d, id);
                     if (key < tauk) {
                         tauk = lane_push(K, Lw, nv, key);
                         tau = key_d(tauk);
                     }
                 }
+            };
+            int j = cnt - 1;
+            // four members per step: their loads and distance chains overlap
+            for (; j >= 3; j -= 4) {
+                const float4 pa = pbuf[j], pb = pbuf[j - 1], pc = pbuf[j - 2], pd = pbuf[j - 3];
+                const float da = dist32(c, s0, s1, s2, s3, pa), db = dist32(c, s0, s1, s2, s3, pb);
+                const float dc = dist32(c, s0, s1, s2, s3, pc), dd = dist32(c, s0, s1, s2, s3, pd);
+                consider(pa, da, first + j);
+                consider(pb, db, first + j - 1);
+                consider(pc, dc, first + j - 2);
+                consider(pd, dd, first + j - 3);
+            }
+            for (; j >= 0; --j) {
+                const float4 p = pbuf[j];
+                consider(p, dist32(c, s0, s1, s2, s3, p), first + j);
             }
         };
         auto scan_chunk = [&](unsigned any, unsigned need) {
