@@ -19,6 +19,10 @@ aggregators written here are the readings used by this project:
   error over the B x 2 outputs, and its exact gradient.
 * AdamW: Adam's moment estimates with bias correction and decoupled weight
   decay (w <- w - lr * (m_hat / (sqrt(v_hat) + eps) + wd * w)).
+* GKA (Eq. GKA, Sec. 3.2): s_hat = sum_k w_k s_k / sum_k w_k over the valid
+  neighbours with w_k = exp(-(s_xy ((x - x_k)^2 + (y - y_k)^2)
+  + s_z (z - z_k)^2 + s_t (t - t_k)^2)); the parameters are theta = log(s)
+  (s_xy, s_z, s_t > 0), trained with Adam on the same mean squared error.
 """
 from __future__ import annotations
 
@@ -114,3 +118,56 @@ def adamw_step(w, g, m, v, t: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, wd
     vhat = v / (1.0 - beta2 ** t)
     w = w - lr * (mhat / (np.sqrt(vhat) + eps) + wd * w)
     return w, m, v
+
+
+def gka_forward(pts, wind, queries, idx, theta):
+    """GKA estimate [m, 2] (float64) and the per-neighbour weights [m, k].
+
+    The exponent is evaluated relative to its smallest value over the
+    context (the common factor cancels in the ratio); NaN for an empty
+    context."""
+    pts = np.asarray(pts, dtype=np.float32).astype(np.float64)
+    wind = np.asarray(wind, dtype=np.float32).astype(np.float64)
+    q = np.asarray(queries, dtype=np.float32).astype(np.float64)
+    idx = np.asarray(idx)
+    sxy, sz, st = np.exp(np.asarray(theta, dtype=np.float64))
+    valid = idx >= 0
+    j = np.where(valid, idx, 0)
+    d = pts[j] - q[:, None, :]
+    e = sxy * (d[..., 0] ** 2 + d[..., 1] ** 2) + sz * d[..., 2] ** 2 + st * d[..., 3] ** 2
+    e = np.where(valid, e, np.inf)
+    emin = np.min(e, axis=1, keepdims=True)
+    w = np.where(valid, np.exp(-(e - np.where(np.isinf(emin), 0.0, emin))), 0.0)
+    W = w.sum(axis=1)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        out = (w[..., None] * wind[j]).sum(axis=1) / W[:, None]
+    return out, w
+
+
+def gka_loss_grad(pts, wind, rows, idx, theta):
+    """Self-query GKA over the dataset rows `rows` (query = the point, target
+    = its wind): (loss = mean over B x 2 of (s_hat - s)^2, dloss/dtheta [3])."""
+    pts = np.asarray(pts, dtype=np.float32)
+    wind64 = np.asarray(wind, dtype=np.float32).astype(np.float64)
+    rows = np.asarray(rows)
+    idx = np.asarray(idx)[rows]
+    q = pts[rows]
+    pred, w = gka_forward(pts, wind, q, idx, theta)
+    t = wind64[rows]
+    err = pred - t
+    B = rows.shape[0]
+    loss = float((err ** 2).sum() / (2 * B))
+    p64 = pts.astype(np.float64)
+    valid = idx >= 0
+    j = np.where(valid, idx, 0)
+    d = p64[j] - p64[rows][:, None, :]
+    sq = [d[..., 0] ** 2 + d[..., 1] ** 2, d[..., 2] ** 2, d[..., 3] ** 2]
+    W = w.sum(axis=1)
+    dev = wind64[j] - pred[:, None, :]  # s_k - s_hat
+    sig = np.exp(np.asarray(theta, dtype=np.float64))
+    g = np.zeros(3)
+    for f in range(3):
+        # d s_hat / d s_f = -sum_k w_k D_kf (s_k - s_hat) / W
+        ds = -(w[..., None] * sq[f][..., None] * dev).sum(axis=1) / W[:, None]
+        g[f] = sig[f] * (err * ds).sum() / B  # d/dtheta = s_f d/ds_f; d loss / d s_hat = err / B
+    return loss, g

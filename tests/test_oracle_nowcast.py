@@ -87,3 +87,61 @@ def test_features_hand_row():
                     mean=np.ones(6), std=np.full(6, 2.0))
     np.testing.assert_allclose(g[0, 0], [0.5, -3.5, 1.0, -2.5, 2.0, -2.0], rtol=1e-7)
     np.testing.assert_array_equal(g[0, 1], np.zeros(6))
+
+
+def _gka_case(seed=3, n=120, k=6):
+    rng = np.random.default_rng(seed)
+    pts = np.column_stack([rng.uniform(0, 5, n), rng.uniform(0, 5, n), rng.uniform(8, 11, n),
+                           rng.uniform(0, 300, n)]).astype(np.float32)
+    wind = rng.normal(0, 10, size=(n, 2)).astype(np.float32)
+    idx = np.array([rng.choice(n, k, replace=False) for _ in range(n)], dtype=np.int32)
+    return pts, wind, idx
+
+
+def test_gka_equal_weights_give_the_plain_average():
+    # every neighbour at the same offset pattern -> equal weights
+    pts = np.array([[0, 0, 10, 100], [1, 0, 10, 90], [-1, 0, 10, 90], [0, 1, 10, 90], [0, -1, 10, 90]],
+                   np.float32)
+    wind = np.array([[0, 0], [1, 2], [3, 4], [5, 6], [7, 8]], np.float32)
+    idx = np.array([[1, 2, 3, 4]], np.int32)
+    out, w = nc.gka_forward(pts, wind, pts[:1], idx, np.log([0.7, 2.0, 0.01]))
+    np.testing.assert_allclose(w, 1.0)
+    np.testing.assert_allclose(out, [[4.0, 5.0]], rtol=1e-12)
+
+
+def test_gka_two_neighbours_closed_form():
+    # two neighbours: s_hat = (s1 + r s2) / (1 + r), r = exp(-(e2 - e1))
+    pts = np.array([[0, 0, 0, 0], [1, 0, 0, 0], [0, 2, 1, -3]], np.float32)
+    wind = np.array([[0, 0], [2, -1], [6, 3]], np.float32)
+    th = np.log([0.5, 3.0, 0.2])
+    out, _ = nc.gka_forward(pts, wind, pts[:1], np.array([[1, 2]], np.int32), th)
+    e1 = 0.5 * 1.0
+    e2 = 0.5 * 4.0 + 3.0 * 1.0 + 0.2 * 9.0
+    r = math.exp(-(e2 - e1))
+    np.testing.assert_allclose(out[0], (np.array([2, -1]) + r * np.array([6, 3])) / (1 + r), rtol=1e-12)
+
+
+def test_gka_large_scale_tends_to_the_nearest_neighbour_and_ignores_missing():
+    pts, wind, idx = _gka_case()
+    idx[:, -1] = -1  # a missing neighbour changes nothing
+    out, _ = nc.gka_forward(pts, wind, pts, idx, np.log([1e4, 1e4, 1e4]))
+    d = pts[np.where(idx >= 0, idx, 0)].astype(np.float64) - pts[:, None, :].astype(np.float64)
+    e = 1e4 * (d ** 2).sum(axis=2)
+    e[idx < 0] = np.inf
+    nearest = idx[np.arange(len(idx)), np.argmin(e, axis=1)]
+    np.testing.assert_allclose(out, wind[nearest], rtol=1e-6, atol=1e-6)
+
+
+def test_gka_gradient_matches_central_differences():
+    pts, wind, idx = _gka_case(seed=8)
+    rows = np.arange(0, 120, 3)
+    th = np.log([0.3, 0.8, 1e-3])
+    _, g = nc.gka_loss_grad(pts, wind, rows, idx, th)
+    h = 1e-6
+    for f in range(3):
+        tp = th.copy()
+        tp[f] += h
+        tm = th.copy()
+        tm[f] -= h
+        fd = (nc.gka_loss_grad(pts, wind, rows, idx, tp)[0] - nc.gka_loss_grad(pts, wind, rows, idx, tm)[0]) / (2 * h)
+        assert abs(fd - g[f]) <= 1e-6 * max(1.0, abs(fd)), (f, fd, g[f])
