@@ -342,6 +342,29 @@ def _extras(tnn, synth, flush, peaks, steps):
                     steps, flush)
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    # GKA-TNN (Eq. GKA): scales trained by Adam on the training rows
+    gka = tnn.GKA((1.0, 10.0, 0.01))
+    gopt = tnn.AdamW(lr=0.05, weight_decay=0.0)
+    gbatches = [trd[torch.from_numpy(rng.permutation(tr.size)[:B]).cuda()].to(torch.int32).contiguous()
+                for _ in range(200)]
+    gka.train_step(ix, wind, gbatches[0], idx, gopt)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for rb in gbatches[1:]:
+        gka.train_step(ix, wind, rb, idx, gopt)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_gka_train = e0.elapsed_time(e1) / (len(gbatches) - 1)
+    idx_te = idx[ted].contiguous()
+    gka.forward(ix, wind, idx_te, q=qte)
+    torch.cuda.synchronize()
+    with _Range("gka_forward"):
+        ms_gka = _timed(lambda: gka.forward(ix, wind, idx_te, q=qte), steps)
+    gpred = gka.forward(ix, wind, idx_te, q=qte)
+    rmse_gka = float(torch.sqrt(((gpred - wind[ted]) ** 2).mean()))
+    gsig, gstep = gka.get_params()
+    gka_bytes = qte.shape[0] * (28 * k + 24)
     out["nowcast"] = {
         "workload": "learned-1M: 5,000 flights x 200 samples, k = 32, lag 1800 s, 80/20 split by flight",
         "contexts": {"value": wl.n / (ms_knn / 1e3), "unit": UNIT, "ms": ms_knn, "tuning": tune},
@@ -368,7 +391,15 @@ def _extras(tnn, synth, flush, peaks, steps):
                                      "peak_note": "of measured bf16 burst; hbm_frac: X read + Y written over measured hbm_gbs"}},
         "nowcast_e2e": {"value": qte.shape[0] / (ms_now / 1e3), "unit": "nowcasts/s", "ms": ms_now,
                         "queries": int(qte.shape[0]), "includes": "tnn_nowcast: search + features + MLP"},
-        "rmse_ms": {"mlp": rmse_mlp, "idw": rmse_idw, "held_out_rows": int(te.size),
+        "gka": {"forward": {"value": qte.shape[0] / (ms_gka / 1e3), "unit": "nowcasts/s", "ms": ms_gka,
+                            "roofline": {"bound": "hbm", "achieved": gka_bytes / (ms_gka / 1e3) / 1e9,
+                                         "peak": hbm, "unit": "GB/s",
+                                         "frac": gka_bytes / (ms_gka / 1e3) / 1e9 / hbm,
+                                         "bytes_per_context": 28 * k + 24, "peak_note": "of measured hbm_gbs"}},
+                "train_step": {"value": B / (ms_gka_train / 1e3), "unit": "samples/s", "ms": ms_gka_train,
+                               "batch": B, "steps": gstep},
+                "sigma": [float(x) for x in gsig]},
+        "rmse_ms": {"mlp": rmse_mlp, "idw": rmse_idw, "gka": rmse_gka, "held_out_rows": int(te.size),
                     "note": "synthetic wind field; noise floor 1 m/s per component (parity unpinned)"}}
     ix.destroy()
     return out

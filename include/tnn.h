@@ -368,6 +368,51 @@ tnn_status tnn_mlp_train_step(tnn_mlp *mlp, const uint16_t *d_x,
                               const tnn_adamw_params *opt, float *d_loss,
                               tnn_stream_t stream);
 
+/* ------------------------------------------------------------------- GKA */
+
+typedef struct tnn_gka tnn_gka;
+
+/*
+ * Gaussian kernel averaging over the TNN context (Sec. 3.2, Eq. GKA; the
+ * GKA-TNN model of Sec. 4.1): the nowcast at q is
+ *     s_hat(q) = sum_k w_k s_k / sum_k w_k,
+ *     w_k = exp(-(s_xy ((x - x_k)^2 + (y - y_k)^2) + s_z (z - z_k)^2
+ *                 + s_t (t - t_k)^2))
+ * over the valid neighbours k of q (NaN for an empty context).  The three
+ * scales are kept on the device as theta = log(s) (so they stay positive)
+ * and trained with Adam on the mean squared error of the nowcast.
+ *   h_sigma  [3] floats (s_xy, s_z, s_t) > 0, host.
+ */
+tnn_status tnn_gka_create(const float *h_sigma, tnn_gka **out);
+void tnn_gka_destroy(tnn_gka *gka);
+/* Current scales (host) and Adam step count.  Synchronous. */
+tnn_status tnn_gka_get_params(const tnn_gka *gka, float *h_sigma, int64_t *h_step);
+/* Set the scales and restart Adam (moments and step zeroed).  Synchronous. */
+tnn_status tnn_gka_set_params(tnn_gka *gka, const float *h_sigma);
+/*
+ * d_uv [m][2] float (device) = GKA nowcast at the queries d_q [m][4] (or the
+ * indexed points when d_q is NULL, m == n_points) from their neighbour
+ * lists d_idx [m][k] (int32, -1 = missing, as tnn_knn writes them) and the
+ * measured wind d_wind [n_points][2] (device, in the index's point order).
+ */
+tnn_status tnn_gka_forward(const tnn_gka *gka, const tnn_index *index, const float *d_wind,
+                           const float *d_q, int64_t m, const int32_t *d_idx, int32_t k,
+                           float *d_uv, tnn_stream_t stream);
+/*
+ * One training step on the batch of dataset rows d_rows [B] (int32,
+ * device): each row is its own query (self-query contexts d_idx
+ * [n_points][k], target its measured wind).  Loss = mean over B x 2 of
+ * (s_hat - s)^2 into d_loss (optional, device float); its gradient with
+ * respect to theta into d_grad (optional, device [3]).  With opt non-NULL
+ * one Adam step (weight_decay acts on theta) follows on the device;
+ * opt == NULL requires d_grad.  Rows with an empty context contribute
+ * nothing.
+ */
+tnn_status tnn_gka_train_step(tnn_gka *gka, const tnn_index *index, const float *d_wind,
+                              const int32_t *d_rows, int64_t B, const int32_t *d_idx, int32_t k,
+                              const tnn_adamw_params *opt, float *d_loss, float *d_grad,
+                              tnn_stream_t stream);
+
 /*
  * Nowcast wind at the queries: TNN context (tnn_knn), features and IDW
  * (tnn_context_features), then the MLP when `mlp` is non-NULL (its input

@@ -1,0 +1,377 @@
+// Gaussian kernel averaging over the TNN context (Sec. 3.2, Eq. GKA):
+//   s_hat(q) = sum_k w_k s_k / sum_k w_k,
+//   w_k = exp(-(s_xy ((x - x_k)^2 + (y - y_k)^2) + s_z (z - z_k)^2 + s_t (t - t_k)^2)),
+// with the parameters kept as theta = log(s) and trained with Adam on the mean
+// squared error of the nowcast (GKA-TNN, Sec. 4.1).
+//
+// k_gka: one warp per query, lane = neighbour (k <= 64, two per lane).  The
+// exponent is taken relative to its warp minimum (the factor cancels), the
+// sums are warp reductions; for training the same warp forms the gradient
+//   d s_hat / d s_f = -sum_k w_k D_kf (s_k - s_hat) / W
+// (D_kf the squared offsets of group f) and the block sums its warps in a
+// fixed order into one partial per block.  k_gka_adam sums the partials in a
+// fixed order and applies Adam to theta with the step count on the device.
+#include <math.h>
+#include <string.h>
+
+#include "tnn_internal.cuh"
+
+#define FULLMASK 0xffffffffu
+#define GKA_WARPS 8
+
+struct tnn_gka {
+    int device;
+    float *theta; // [3] log s_xy, log s_z, log s_t
+    float *m, *v; // Adam moments [3]
+    long long *step;
+    float *part;  // [cap][4]: gradient (3) and squared error per block
+    float *acc;   // [4] reduced gradient and loss
+    long long cap;
+};
+
+struct GkaArgs {
+    const float4 *pts;
+    const float2 *wind;
+    const float4 *q;     // queries (forward), NULL = the indexed points
+    const int32_t *rows; // training: dataset rows of the batch (query = point)
+    long long m;
+    const int32_t *idx;  // [.. ][k] neighbours (row-indexed when training)
+    int k;
+    const float *theta;
+    float2 *out;         // forward: [m] estimate (NaN for an empty context)
+    float *part;         // training: [blocks][4]
+    float inv_B;
+};
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(FULLMASK, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(GKA_WARPS * 32) k_gka(const __grid_constant__ GkaArgs a)
+{
+    __shared__ float s_part[GKA_WARPS][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long r = (long long)blockIdx.x * GKA_WARPS + warp;
+    const bool train = a.rows != nullptr;
+    const float sxy = __expf(a.theta[0]), sz = __expf(a.theta[1]), st = __expf(a.theta[2]);
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f, se = 0.f;
+    if (r < a.m) {
+        const long long row = train ? (long long)a.rows[r] : r;
+        const float4 q = train ? a.pts[row] : (a.q ? a.q[r] : a.pts[r]);
+        float e[2], du[2][3], su[2], sv[2];
+        bool ok[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = lane + 32 * h;
+            const int id = j < a.k ? a.idx[row * a.k + j] : -1;
+            ok[h] = id >= 0;
+            e[h] = INFINITY;
+            su[h] = sv[h] = 0.f;
+            du[h][0] = du[h][1] = du[h][2] = 0.f;
+            if (ok[h]) {
+                const float4 p = a.pts[id];
+                const float2 s = a.wind[id];
+                const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z, dt = p.w - q.w;
+                du[h][0] = fmaf(dx, dx, dy * dy);
+                du[h][1] = dz * dz;
+                du[h][2] = dt * dt;
+                e[h] = fmaf(sxy, du[h][0], fmaf(sz, du[h][1], st * du[h][2]));
+                su[h] = s.x;
+                sv[h] = s.y;
+            }
+        }
+        float emin = fminf(e[0], e[1]);
+        for (int o = 16; o > 0; o >>= 1)
+            emin = fminf(emin, __shfl_xor_sync(FULLMASK, emin, o));
+        float w[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            w[h] = ok[h] ? expf(emin - e[h]) : 0.f;
+        const float W = warp_sum(w[0] + w[1]);
+        const float U = warp_sum(fmaf(w[0], su[0], w[1] * su[1]));
+        const float V = warp_sum(fmaf(w[0], sv[0], w[1] * sv[1]));
+        const float pu = U / W, pv = V / W; // NaN for an empty context
+        if (!train) {
+            if (lane == 0)
+                a.out[r] = make_float2(pu, pv);
+        } else if (W > 0.f) {
+            const float2 t = a.wind[row];
+            const float eu = pu - t.x, ev = pv - t.y;
+            se = eu * eu + ev * ev;
+            // sum_k w_k D_kf ((s_k - s_hat) . err)
+            float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float proj = w[h] * fmaf(su[h] - pu, eu, (sv[h] - pv) * ev);
+                c0 = fmaf(proj, du[h][0], c0);
+                c1 = fmaf(proj, du[h][1], c1);
+                c2 = fmaf(proj, du[h][2], c2);
+            }
+            c0 = warp_sum(c0);
+            c1 = warp_sum(c1);
+            c2 = warp_sum(c2);
+            // d loss / d theta_f = s_f (1/B) sum err . d s_hat / d s_f
+            const float f = -a.inv_B / W;
+            g0 = sxy * f * c0;
+            g1 = sz * f * c1;
+            g2 = st * f * c2;
+        }
+    }
+    if (!train)
+        return;
+    if (lane == 0) {
+        s_part[warp][0] = g0;
+        s_part[warp][1] = g1;
+        s_part[warp][2] = g2;
+        s_part[warp][3] = se;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        float acc = 0.f;
+        for (int w = 0; w < GKA_WARPS; ++w)
+            acc += s_part[w][threadIdx.x];
+        a.part[(long long)blockIdx.x * 4 + threadIdx.x] = acc;
+    }
+}
+
+struct GkaAdamArgs {
+    const float *part;
+    long long nblocks;
+    float *theta, *m, *v;
+    long long *step;
+    float *acc;      // [4] reduced gradient, loss
+    float *grad_out; // optional [3]
+    float *loss_out; // optional
+    float inv_2B;
+    int update;
+    float lr, b1, b2, eps, wd;
+};
+
+// One block of 128 threads: fixed-order reduction of the partials, then
+// Adam on theta.
+__global__ void k_gka_adam(const __grid_constant__ GkaAdamArgs a)
+{
+    __shared__ float s[4][32];
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31; // warp c sums component c
+    float v = 0.f;
+    for (long long b = lane; b < a.nblocks; b += 32)
+        v += a.part[b * 4 + c];
+    s[c][lane] = v;
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        float t = 0.f;
+        for (int i = 0; i < 32; ++i)
+            t += s[threadIdx.x][i];
+        a.acc[threadIdx.x] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (a.loss_out)
+            *a.loss_out = a.acc[3] * a.inv_2B;
+        if (a.grad_out)
+            for (int i = 0; i < 3; ++i)
+                a.grad_out[i] = a.acc[i];
+        if (a.update) {
+            const long long st = *a.step + 1;
+            *a.step = st;
+            const float bc1 = -expm1f((float)st * log1pf(a.b1 - 1.0f));
+            const float bc2 = -expm1f((float)st * log1pf(a.b2 - 1.0f));
+            for (int i = 0; i < 3; ++i) {
+                const float g = a.acc[i];
+                const float m = a.b1 * a.m[i] + (1.f - a.b1) * g;
+                const float vv = a.b2 * a.v[i] + (1.f - a.b2) * g * g;
+                a.m[i] = m;
+                a.v[i] = vv;
+                const float th = a.theta[i];
+                a.theta[i] = th - a.lr * ((m / bc1) / (sqrtf(vv / bc2) + a.eps) + a.wd * th);
+            }
+        }
+    }
+}
+
+extern "C" tnn_status tnn_gka_create(const float *h_sigma, tnn_gka **out)
+{
+    tnn_clear_error();
+    TNN_ARG_CHECK(out != nullptr && h_sigma != nullptr, "NULL argument");
+    *out = nullptr;
+    for (int i = 0; i < 3; ++i)
+        TNN_ARG_CHECK(h_sigma[i] > 0.f && isfinite(h_sigma[i]), "sigma[%d] must be finite and > 0", i);
+    tnn_gka *g = new tnn_gka();
+    memset(g, 0, sizeof(*g));
+    cudaGetDevice(&g->device);
+    float th[3] = {logf(h_sigma[0]), logf(h_sigma[1]), logf(h_sigma[2])};
+    cudaError_t e = cudaMalloc(&g->theta, 3 * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&g->m, 3 * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&g->v, 3 * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&g->step, sizeof(long long));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&g->acc, 4 * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->theta, th, sizeof(th), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemset(g->m, 0, 3 * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMemset(g->v, 0, 3 * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMemset(g->step, 0, sizeof(long long));
+    if (e != cudaSuccess) {
+        tnn_gka_destroy(g);
+        tnn_set_error("GKA allocation failed: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? TNN_ERR_OOM : TNN_ERR_CUDA;
+    }
+    *out = g;
+    return TNN_OK;
+}
+
+extern "C" void tnn_gka_destroy(tnn_gka *g)
+{
+    if (!g)
+        return;
+    cudaFree(g->theta);
+    cudaFree(g->m);
+    cudaFree(g->v);
+    cudaFree(g->step);
+    cudaFree(g->part);
+    cudaFree(g->acc);
+    delete g;
+}
+
+extern "C" tnn_status tnn_gka_get_params(const tnn_gka *g, float *h_sigma, int64_t *h_step)
+{
+    tnn_clear_error();
+    TNN_ARG_CHECK(g != nullptr && h_sigma != nullptr, "NULL argument");
+    TNN_CUDA_TRY(cudaDeviceSynchronize());
+    float th[3];
+    TNN_CUDA_TRY(cudaMemcpy(th, g->theta, sizeof(th), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 3; ++i)
+        h_sigma[i] = expf(th[i]);
+    if (h_step) {
+        long long s = 0;
+        TNN_CUDA_TRY(cudaMemcpy(&s, g->step, sizeof(s), cudaMemcpyDeviceToHost));
+        *h_step = s;
+    }
+    return TNN_OK;
+}
+
+extern "C" tnn_status tnn_gka_set_params(tnn_gka *g, const float *h_sigma)
+{
+    tnn_clear_error();
+    TNN_ARG_CHECK(g != nullptr && h_sigma != nullptr, "NULL argument");
+    for (int i = 0; i < 3; ++i)
+        TNN_ARG_CHECK(h_sigma[i] > 0.f && isfinite(h_sigma[i]), "sigma[%d] must be finite and > 0", i);
+    float th[3] = {logf(h_sigma[0]), logf(h_sigma[1]), logf(h_sigma[2])};
+    TNN_CUDA_TRY(cudaDeviceSynchronize());
+    TNN_CUDA_TRY(cudaMemcpy(g->theta, th, sizeof(th), cudaMemcpyHostToDevice));
+    TNN_CUDA_TRY(cudaMemset(g->m, 0, 3 * sizeof(float)));
+    TNN_CUDA_TRY(cudaMemset(g->v, 0, 3 * sizeof(float)));
+    TNN_CUDA_TRY(cudaMemset(g->step, 0, sizeof(long long)));
+    return TNN_OK;
+}
+
+static tnn_status gka_check(const tnn_gka *g, const tnn_index *ix, const float *d_wind,
+                            const int32_t *d_idx, int32_t k)
+{
+    TNN_ARG_CHECK(g && ix && d_wind && d_idx, "NULL argument");
+    TNN_ARG_CHECK(k >= 1 && k <= 64, "k must be in [1, 64]");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    TNN_ARG_CHECK(dev == g->device && dev == ix->device, "GKA, index and current device differ");
+    return TNN_OK;
+}
+
+extern "C" tnn_status tnn_gka_forward(const tnn_gka *g, const tnn_index *ix, const float *d_wind,
+                                      const float *d_q, int64_t m, const int32_t *d_idx, int32_t k,
+                                      float *d_uv, tnn_stream_t stream)
+{
+    tnn_clear_error();
+    tnn_status s = gka_check(g, ix, d_wind, d_idx, k);
+    if (s != TNN_OK)
+        return s;
+    TNN_ARG_CHECK(d_uv != nullptr, "d_uv is NULL");
+    TNN_ARG_CHECK(m >= 0 && m < (1ll << 31), "m out of range");
+    TNN_ARG_CHECK(d_q != nullptr || m == ix->n, "self-query needs m == n_points");
+    if (m == 0)
+        return TNN_OK;
+    GkaArgs a;
+    memset(&a, 0, sizeof(a));
+    a.pts = ix->pts;
+    a.wind = (const float2 *)d_wind;
+    a.q = (const float4 *)d_q;
+    a.m = m;
+    a.idx = d_idx;
+    a.k = k;
+    a.theta = g->theta;
+    a.out = (float2 *)d_uv;
+    k_gka<<<(unsigned)((m + GKA_WARPS - 1) / GKA_WARPS), GKA_WARPS * 32, 0, (cudaStream_t)stream>>>(a);
+    TNN_CUDA_TRY(cudaGetLastError());
+    return TNN_OK;
+}
+
+extern "C" tnn_status tnn_gka_train_step(tnn_gka *g, const tnn_index *ix, const float *d_wind,
+                                         const int32_t *d_rows, int64_t B, const int32_t *d_idx,
+                                         int32_t k, const tnn_adamw_params *opt, float *d_loss,
+                                         float *d_grad, tnn_stream_t stream)
+{
+    tnn_clear_error();
+    tnn_status s = gka_check(g, ix, d_wind, d_idx, k);
+    if (s != TNN_OK)
+        return s;
+    TNN_ARG_CHECK(d_rows != nullptr, "d_rows is NULL");
+    TNN_ARG_CHECK(B >= 1 && B < (1ll << 31), "B out of range");
+    if (opt)
+        TNN_ARG_CHECK(opt->lr >= 0.f && opt->beta1 >= 0.f && opt->beta1 < 1.f && opt->beta2 >= 0.f &&
+                          opt->beta2 < 1.f && opt->eps > 0.f && opt->weight_decay >= 0.f,
+                      "invalid Adam parameters");
+    TNN_ARG_CHECK(opt != nullptr || d_grad != nullptr, "nothing to do: no optimiser and no gradient output");
+    const long long nb = (B + GKA_WARPS - 1) / GKA_WARPS;
+    if (nb > g->cap) {
+        cudaFree(g->part);
+        g->part = nullptr;
+        g->cap = 0;
+        TNN_CUDA_TRY(cudaMalloc(&g->part, (size_t)nb * 4 * sizeof(float)));
+        g->cap = nb;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    GkaArgs a;
+    memset(&a, 0, sizeof(a));
+    a.pts = ix->pts;
+    a.wind = (const float2 *)d_wind;
+    a.rows = d_rows;
+    a.m = B;
+    a.idx = d_idx;
+    a.k = k;
+    a.theta = g->theta;
+    a.part = g->part;
+    a.inv_B = 1.0f / (float)B;
+    k_gka<<<(unsigned)nb, GKA_WARPS * 32, 0, st>>>(a);
+    TNN_CUDA_TRY(cudaGetLastError());
+    GkaAdamArgs d;
+    memset(&d, 0, sizeof(d));
+    d.part = g->part;
+    d.nblocks = nb;
+    d.theta = g->theta;
+    d.m = g->m;
+    d.v = g->v;
+    d.step = g->step;
+    d.acc = g->acc;
+    d.grad_out = d_grad;
+    d.loss_out = d_loss;
+    d.inv_2B = 1.0f / (2.0f * (float)B);
+    d.update = opt != nullptr;
+    if (opt) {
+        d.lr = opt->lr;
+        d.b1 = opt->beta1;
+        d.b2 = opt->beta2;
+        d.eps = opt->eps;
+        d.wd = opt->weight_decay;
+    }
+    k_gka_adam<<<1, 128, 0, st>>>(d);
+    TNN_CUDA_TRY(cudaGetLastError());
+    return TNN_OK;
+}

@@ -99,6 +99,13 @@ _SIGNATURES = [
     ("tnn_mlp_gradients", c_i32, [c_p, c_p, c_p, c_i64, c_p, c_p, c_p]),
     ("tnn_mlp_train_step", c_i32, [c_p, c_p, c_p, c_i64, ctypes.POINTER(tnn_adamw_params), c_p,
                                    c_p]),
+    ("tnn_gka_create", c_i32, [c_p, ctypes.POINTER(c_p)]),
+    ("tnn_gka_destroy", None, [c_p]),
+    ("tnn_gka_get_params", c_i32, [c_p, c_p, ctypes.POINTER(c_i64)]),
+    ("tnn_gka_set_params", c_i32, [c_p, c_p]),
+    ("tnn_gka_forward", c_i32, [c_p, c_p, c_p, c_p, c_i64, c_p, c_i32, c_p, c_p]),
+    ("tnn_gka_train_step", c_i32, [c_p, c_p, c_p, c_p, c_i64, c_p, c_i32,
+                                   ctypes.POINTER(tnn_adamw_params), c_p, c_p, c_p]),
     ("tnn_nowcast", c_i32, [c_p, c_p, c_p, c_i64, ctypes.POINTER(tnn_knn_params), c_p, c_p, c_p,
                             c_f32, c_p, c_p]),
 ]
@@ -499,6 +506,79 @@ class MLP:
     def destroy(self):
         if getattr(self, "_h", None) is not None and _lib is not None:
             _lib.tnn_mlp_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class GKA:
+    """tnn_gka: Gaussian kernel averaging over TNN contexts (Eq. GKA) with
+    scales (s_xy, s_z, s_t) trained by Adam."""
+
+    def __init__(self, sigma=(1.0, 10.0, 0.01)):
+        h = c_p()
+        sig = np.ascontiguousarray(np.asarray(sigma, np.float32))
+        _check(_L().tnn_gka_create(sig.ctypes.data_as(c_p), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def tnn_gka_get_params(self):
+        """(sigma [3] float32, Adam step)."""
+        sig = np.empty(3, np.float32)
+        step = c_i64()
+        _check(_L().tnn_gka_get_params(self._h, sig.ctypes.data_as(c_p), ctypes.byref(step)))
+        return sig, int(step.value)
+
+    get_params = tnn_gka_get_params
+
+    def tnn_gka_set_params(self, sigma):
+        sig = np.ascontiguousarray(np.asarray(sigma, np.float32))
+        _check(_L().tnn_gka_set_params(self._h, sig.ctypes.data_as(c_p)))
+
+    set_params = tnn_gka_set_params
+
+    def tnn_gka_forward(self, index: Index, wind: torch.Tensor, idx: torch.Tensor, q=None):
+        wind = _dev(wind, torch.float32, (2,), "wind")
+        m, k = idx.shape
+        _dev(idx, torch.int32, (k,), "idx")
+        if q is not None:
+            q = _dev(q, torch.float32, (4,), "q")
+        uv = torch.empty((m, 2), dtype=torch.float32, device="cuda")
+        _check(_L().tnn_gka_forward(self._h, index.handle, _ptr(wind), _ptr(q), m, _ptr(idx), k,
+                                    _ptr(uv), _stream()))
+        return uv
+
+    forward = tnn_gka_forward
+
+    def tnn_gka_train_step(self, index: Index, wind: torch.Tensor, rows: torch.Tensor,
+                           idx: torch.Tensor, opt: "AdamW | None" = None, loss=None, grad=None):
+        wind = _dev(wind, torch.float32, (2,), "wind")
+        rows = _dev(rows, torch.int32, None, "rows")
+        _dev(idx, torch.int32, (idx.shape[1],), "idx")
+        o = opt.c() if opt is not None else None
+        _check(_L().tnn_gka_train_step(self._h, index.handle, _ptr(wind), _ptr(rows), rows.shape[0],
+                                       _ptr(idx), idx.shape[1], ctypes.byref(o) if o is not None else None,
+                                       _ptr(loss), _ptr(grad), _stream()))
+
+    train_step = tnn_gka_train_step
+
+    def gradients(self, index: Index, wind, rows, idx):
+        """(loss, d loss / d log sigma [3]) on the batch; no update."""
+        loss = torch.empty((1,), dtype=torch.float32, device="cuda")
+        grad = torch.empty((3,), dtype=torch.float32, device="cuda")
+        self.tnn_gka_train_step(index, wind, rows, idx, None, loss, grad)
+        return loss, grad
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.tnn_gka_destroy(self._h)
         self._h = None
 
     def __del__(self):

@@ -199,3 +199,73 @@ def test_training_steps_replayed_from_a_cuda_graph_match_eager_steps():
     assert a[3] == b[3] == 4
     g.replay()  # four more steps
     assert graphed.get_params(with_moments=True)[3] == 8
+
+
+def _gka_setup(n_flights=60, k=16, lag=600.0):
+    wl = synth.flights(n_flights, 80, seed=synth.SEED_LEARNED + 3, n_routes=6)
+    ix = tnn.tnn_build_segments(torch.from_numpy(wl.xyzt).cuda(), wl.traj_off, SIG, 16)
+    idx, _ = tnn.tnn_knn(ix, k, lag)
+    return wl, ix, idx, torch.from_numpy(wl.wind).cuda()
+
+
+def test_gka_forward_matches_oracle():
+    wl, ix, idx, wind = _gka_setup()
+    sig = np.array([0.05, 4.0, 1e-4], np.float32)
+    g = tnn.GKA(sig)
+    uv = g.forward(ix, wind, idx).cpu().numpy()
+    ref, _ = nc.gka_forward(wl.xyzt, wl.wind, wl.xyzt, idx.cpu().numpy(), np.log(sig.astype(np.float64)))
+    nan = np.isnan(ref).any(axis=1)
+    assert nan.any() and not nan.all()  # some queries have no causal point
+    assert np.isnan(uv[nan]).all()
+    np.testing.assert_allclose(uv[~nan], ref[~nan], rtol=1e-4, atol=1e-4)
+    # external queries
+    q = wl.xyzt[::7].copy()
+    q[:, 0] += 0.3
+    qi, _ = tnn.tnn_knn(ix, 16, 600.0, q=torch.from_numpy(q).cuda())
+    uq = g.forward(ix, wind, qi, q=torch.from_numpy(q).cuda()).cpu().numpy()
+    rq, _ = nc.gka_forward(wl.xyzt, wl.wind, q, qi.cpu().numpy(), np.log(sig.astype(np.float64)))
+    ok = ~np.isnan(rq).any(axis=1)
+    np.testing.assert_allclose(uq[ok], rq[ok], rtol=1e-4, atol=1e-4)
+
+
+def test_gka_gradient_and_adam_step_match_oracle():
+    wl, ix, idx, wind = _gka_setup()
+    idx_h = idx.cpu().numpy()
+    full = (idx_h >= 0).all(axis=1)
+    rows = np.nonzero(full)[0][:1500].astype(np.int32)
+    rows_d = torch.from_numpy(rows).cuda()
+    sig = np.array([0.05, 4.0, 1e-4], np.float32)
+    g = tnn.GKA(sig)
+    loss, grad = g.gradients(ix, wind, rows_d, idx)
+    th = np.log(sig.astype(np.float64))
+    rl, rg = nc.gka_loss_grad(wl.xyzt, wl.wind, rows, idx_h, th)
+    assert float(loss.item()) == pytest.approx(rl, rel=1e-4)
+    np.testing.assert_allclose(grad.cpu().numpy(), rg, rtol=2e-3, atol=1e-6 * np.abs(rg).max())
+    opt = tnn.AdamW(lr=0.05, weight_decay=0.0)
+    mm = np.zeros(3)
+    vv = np.zeros(3)
+    tk = th.copy()
+    for t in range(1, 4):
+        _, gt = nc.gka_loss_grad(wl.xyzt, wl.wind, rows, idx_h, tk)
+        g.train_step(ix, wind, rows_d, idx, opt)
+        tk, mm, vv = nc.adamw_step(tk, gt, mm, vv, t, lr=opt.lr, beta1=opt.beta1, beta2=opt.beta2,
+                                   eps=opt.eps, wd=0.0)
+        got, step = g.get_params()
+        assert step == t
+        np.testing.assert_allclose(np.log(got.astype(np.float64)), tk, rtol=0, atol=2e-4)
+
+
+def test_gka_training_lowers_the_loss():
+    wl, ix, idx, wind = _gka_setup(n_flights=120, k=32, lag=1800.0)
+    full = (idx >= 0).all(dim=1).nonzero().flatten().to(torch.int32)
+    g = tnn.GKA((1.0, 10.0, 0.01))
+    l0, _ = g.gradients(ix, wind, full, idx)
+    opt = tnn.AdamW(lr=0.05, weight_decay=0.0)
+    for _ in range(150):
+        g.train_step(ix, wind, full, idx, opt)
+    l1, g1 = g.gradients(ix, wind, full, idx)
+    # the context is at least 30 min old: the scales gain little, but they
+    # must gain something and approach a stationary point
+    assert float(l1.item()) < (1 - 1e-3) * float(l0.item())
+    _, g0 = tnn.GKA((1.0, 10.0, 0.01)).gradients(ix, wind, full, idx)
+    assert float(g1.norm()) < float(g0.norm())
