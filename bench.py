@@ -56,6 +56,23 @@ def _search_traffic(workload):
     return SEARCH_TRAFFIC["bytes"]
 
 
+def _max_over_ranks(x, world, device="cuda"):
+    """The job's time is the slowest rank's (a MAX all-reduce; the only
+    collective of the run: each rank answers its own window)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _throughput(world, m, steps, total_ms):
+    """Whole-job contexts/s: every rank answers m queries per step."""
+    return world * m * steps / (total_ms / 1e3)
+
+
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -470,13 +487,9 @@ def run_ours(a):
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    total_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = _max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in ev), world)
     ms_step = total_ms / max(a.steps, 1)
-    value = world * m * a.steps / (total_ms / 1e3)
+    value = _throughput(world, m, a.steps, total_ms)
 
     # executed and necessary work of one pass (outside the timed region)
     _, _, st = tnn.tnn_knn(ix, k, 0.0, stats=True, out=(idx, d2), **tune)
