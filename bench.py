@@ -382,10 +382,33 @@ def _extras(tnn, synth, flush, peaks, steps):
     rmse_gka = float(torch.sqrt(((gpred - wind[ted]) ** 2).mean()))
     gsig, gstep = gka.get_params()
     gka_bytes = qte.shape[0] * (28 * k + 24)
+    # the float64 oracle of each stage on a bounded sample (host cores)
+    from oracle import nowcast as ncr
+    ns = 20000
+    smp = te[:ns]
+    idx_s = idx[torch.from_numpy(smp).cuda()].cpu().numpy()
+    d2_s = d2[torch.from_numpy(smp).cuda()].cpu().numpy()
+    c0 = time.perf_counter()
+    ncr.features(wl.xyzt, wl.wind, wl.xyzt[smp], idx_s, sigma, mean=mean, std=std)
+    ncr.idw(d2_s, idx_s, wl.wind)
+    c_feat = time.perf_counter() - c0
+    W1, b1m, W2, b2m = mlp.unflatten(mlp.get_params())
+    xs = xte[:ns].float().cpu().numpy().astype(np.float64)
+    c0 = time.perf_counter()
+    ncr.mlp_forward(xs, W1, b1m, W2, b2m)
+    c_mlp = time.perf_counter() - c0
+    c0 = time.perf_counter()
+    ncr.gka_forward(wl.xyzt, wl.wind, wl.xyzt[smp], idx_s, np.log(gsig.astype(np.float64)))
+    c_gka = time.perf_counter() - c0
+
+    def _cpu(sec, unit):
+        return {"value": ns / sec, "unit": unit, "cores": os.cpu_count(), "kind": "oracle",
+                "sample": f"{ns} held-out contexts, float64 numpy"}
     out["nowcast"] = {
         "workload": "learned-1M: 5,000 flights x 200 samples, k = 32, lag 1800 s, 80/20 split by flight",
         "contexts": {"value": wl.n / (ms_knn / 1e3), "unit": UNIT, "ms": ms_knn, "tuning": tune},
         "features_idw": {"value": wl.n / (ms_feat / 1e3), "unit": "contexts/s", "ms": ms_feat,
+                         "cpu_baseline": _cpu(c_feat, "contexts/s"),
                          "roofline": {"bound": "hbm", "achieved": feat_bytes / (ms_feat / 1e3) / 1e9,
                                       "peak": hbm, "unit": "GB/s",
                                       "frac": feat_bytes / (ms_feat / 1e3) / 1e9 / hbm,
@@ -399,7 +422,7 @@ def _extras(tnn, synth, flush, peaks, steps):
                                    "frac": flops_step / (ms_graph / 1e3) / 1e12 / bf16,
                                    "flops_per_step": flops_step, "peak_note": "of measured bf16 burst"}},
         "mlp_forward": {"value": xte.shape[0] / (ms_fwd / 1e3), "unit": "samples/s", "ms": ms_fwd,
-                        "rows": int(xte.shape[0]),
+                        "rows": int(xte.shape[0]), "cpu_baseline": _cpu(c_mlp, "samples/s"),
                         "roofline": {"bound": "tensor",
                                      "achieved": 2.0 * xte.shape[0] * (k * 6 * 256 + 256 * 2) / (ms_fwd / 1e3) / 1e12,
                                      "peak": bf16, "unit": "TFLOP/s",
@@ -409,6 +432,7 @@ def _extras(tnn, synth, flush, peaks, steps):
         "nowcast_e2e": {"value": qte.shape[0] / (ms_now / 1e3), "unit": "nowcasts/s", "ms": ms_now,
                         "queries": int(qte.shape[0]), "includes": "tnn_nowcast: search + features + MLP"},
         "gka": {"forward": {"value": qte.shape[0] / (ms_gka / 1e3), "unit": "nowcasts/s", "ms": ms_gka,
+                            "cpu_baseline": _cpu(c_gka, "nowcasts/s"),
                             "roofline": {"bound": "hbm", "achieved": gka_bytes / (ms_gka / 1e3) / 1e9,
                                          "peak": hbm, "unit": "GB/s",
                                          "frac": gka_bytes / (ms_gka / 1e3) / 1e9 / hbm,

@@ -23,6 +23,10 @@ aggregators written here are the readings used by this project:
   neighbours with w_k = exp(-(s_xy ((x - x_k)^2 + (y - y_k)^2)
   + s_z (z - z_k)^2 + s_t (t - t_k)^2)); the parameters are theta = log(s)
   (s_xy, s_z, s_t > 0), trained with Adam on the same mean squared error.
+* GKA-MLP (Sec. 3.2: the scales as a function of the location): per query
+  theta(q) = tanh(u W1 + b1) W2 + b2 with u = (q_xyz - lo) / (hi - lo) the
+  location normalised by the points' bounding box, then GKA with
+  s = exp(theta(q)); trained end to end with Adam.
 """
 from __future__ import annotations
 
@@ -121,7 +125,8 @@ def adamw_step(w, g, m, v, t: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, wd
 
 
 def gka_forward(pts, wind, queries, idx, theta):
-    """GKA estimate [m, 2] (float64) and the per-neighbour weights [m, k].
+    """GKA estimate [m, 2] (float64) and the per-neighbour weights [m, k];
+    theta is [3] (one set of scales) or [m, 3] (per query).
 
     The exponent is evaluated relative to its smallest value over the
     context (the common factor cancels in the ratio); NaN for an empty
@@ -130,7 +135,10 @@ def gka_forward(pts, wind, queries, idx, theta):
     wind = np.asarray(wind, dtype=np.float32).astype(np.float64)
     q = np.asarray(queries, dtype=np.float32).astype(np.float64)
     idx = np.asarray(idx)
-    sxy, sz, st = np.exp(np.asarray(theta, dtype=np.float64))
+    sig = np.exp(np.asarray(theta, dtype=np.float64))
+    if sig.ndim == 1:
+        sig = np.broadcast_to(sig, (q.shape[0], 3))
+    sxy, sz, st = sig[:, 0:1], sig[:, 1:2], sig[:, 2:3]
     valid = idx >= 0
     j = np.where(valid, idx, 0)
     d = pts[j] - q[:, None, :]
@@ -171,3 +179,65 @@ def gka_loss_grad(pts, wind, rows, idx, theta):
         ds = -(w[..., None] * sq[f][..., None] * dev).sum(axis=1) / W[:, None]
         g[f] = sig[f] * (err * ds).sum() / B  # d/dtheta = s_f d/ds_f; d loss / d s_hat = err / B
     return loss, g
+
+
+def gkamlp_unflatten(params, hidden: int):
+    """Flat layout W1 [3][H] | b1 [H] | W2 [H][3] | b2 [3] -> arrays."""
+    p = np.asarray(params, dtype=np.float64)
+    H = hidden
+    o = 0
+    W1 = p[o:o + 3 * H].reshape(3, H); o += 3 * H
+    b1 = p[o:o + H]; o += H
+    W2 = p[o:o + 3 * H].reshape(H, 3); o += 3 * H
+    b2 = p[o:o + 3]
+    return W1, b1, W2, b2
+
+
+def gkamlp_theta(queries, params, hidden: int, lo, hi):
+    """Per-query log-scales [m, 3], hidden activations [m, H] and u [m, 3]."""
+    W1, b1, W2, b2 = gkamlp_unflatten(params, hidden)
+    q = np.asarray(queries, dtype=np.float32).astype(np.float64)
+    lo = np.asarray(lo, dtype=np.float32).astype(np.float64)[:3]
+    hi = np.asarray(hi, dtype=np.float32).astype(np.float64)[:3]
+    u = (q[:, :3] - lo) / np.where(hi > lo, hi - lo, 1.0)
+    h = np.tanh(u @ W1 + b1)
+    return h @ W2 + b2, h, u
+
+
+def gkamlp_forward(pts, wind, queries, idx, params, hidden: int, lo, hi):
+    theta, _, _ = gkamlp_theta(queries, params, hidden, lo, hi)
+    return gka_forward(pts, wind, queries, idx, theta)[0]
+
+
+def gkamlp_loss_grad(pts, wind, rows, idx, params, hidden: int, lo, hi):
+    """Self-query GKA-MLP on dataset rows: (loss, gradient in the flat layout)."""
+    pts = np.asarray(pts, dtype=np.float32)
+    wind64 = np.asarray(wind, dtype=np.float32).astype(np.float64)
+    rows = np.asarray(rows)
+    idx = np.asarray(idx)[rows]
+    q = pts[rows]
+    theta, h, u = gkamlp_theta(q, params, hidden, lo, hi)
+    pred, w = gka_forward(pts, wind, q, idx, theta)
+    t = wind64[rows]
+    err = pred - t
+    B = rows.shape[0]
+    loss = float((err ** 2).sum() / (2 * B))
+    p64 = pts.astype(np.float64)
+    valid = idx >= 0
+    j = np.where(valid, idx, 0)
+    d = p64[j] - p64[rows][:, None, :]
+    sq = [d[..., 0] ** 2 + d[..., 1] ** 2, d[..., 2] ** 2, d[..., 3] ** 2]
+    W = w.sum(axis=1)
+    dev = wind64[j] - pred[:, None, :]
+    sig = np.exp(theta)
+    dth = np.zeros_like(theta)  # d loss / d theta(q)
+    for f in range(3):
+        ds = -(w[..., None] * sq[f][..., None] * dev).sum(axis=1) / W[:, None]
+        dth[:, f] = sig[:, f] * (err * ds).sum(axis=1) / B
+    W1, b1, W2, b2 = gkamlp_unflatten(params, hidden)
+    gW2 = h.T @ dth
+    gb2 = dth.sum(axis=0)
+    da = (dth @ W2.T) * (1.0 - h ** 2)
+    gW1 = u.T @ da
+    gb1 = da.sum(axis=0)
+    return loss, np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2])

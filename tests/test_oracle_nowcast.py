@@ -145,3 +145,37 @@ def test_gka_gradient_matches_central_differences():
         tm[f] -= h
         fd = (nc.gka_loss_grad(pts, wind, rows, idx, tp)[0] - nc.gka_loss_grad(pts, wind, rows, idx, tm)[0]) / (2 * h)
         assert abs(fd - g[f]) <= 1e-6 * max(1.0, abs(fd)), (f, fd, g[f])
+
+
+def _gkamlp_params(H, seed, w2_scale=0.3):
+    rng = np.random.default_rng(seed)
+    return np.concatenate([rng.uniform(-1, 1, 3 * H), rng.uniform(-1, 1, H),
+                           w2_scale * rng.normal(size=3 * H), np.log([0.3, 0.8, 1e-3])])
+
+
+def test_gkamlp_with_zero_output_weights_is_plain_gka():
+    pts, wind, idx = _gka_case(seed=5)
+    H = 8
+    p = _gkamlp_params(H, 1, w2_scale=0.0)
+    lo, hi = pts.min(axis=0), pts.max(axis=0)
+    out = nc.gkamlp_forward(pts, wind, pts, idx, p, H, lo, hi)
+    ref, _ = nc.gka_forward(pts, wind, pts, idx, np.log([0.3, 0.8, 1e-3]))
+    np.testing.assert_allclose(out, ref, rtol=1e-12)
+
+
+def test_gkamlp_gradient_matches_central_differences():
+    pts, wind, idx = _gka_case(seed=9)
+    H = 6
+    p = _gkamlp_params(H, 2)
+    lo, hi = pts.min(axis=0), pts.max(axis=0)
+    rows = np.arange(0, 120, 2)
+    _, g = nc.gkamlp_loss_grad(pts, wind, rows, idx, p, H, lo, hi)
+    h = 1e-6
+    for i in range(0, p.size, 3):
+        pp = p.copy()
+        pp[i] += h
+        pm = p.copy()
+        pm[i] -= h
+        fd = (nc.gkamlp_loss_grad(pts, wind, rows, idx, pp, H, lo, hi)[0]
+              - nc.gkamlp_loss_grad(pts, wind, rows, idx, pm, H, lo, hi)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
