@@ -382,6 +382,27 @@ def _extras(tnn, synth, flush, peaks, steps):
     rmse_gka = float(torch.sqrt(((gpred - wind[ted]) ** 2).mean()))
     gsig, gstep = gka.get_params()
     gka_bytes = qte.shape[0] * (28 * k + 24)
+    # GKA-MLP-TNN: scales from an MLP of the location, started from the GKA
+    # scales and trained end to end
+    gm = tnn.GKAMLP(gsig, hidden=32, seed=0)
+    mopt = tnn.AdamW(lr=0.01, weight_decay=0.0)
+    mbatches = [trd[torch.from_numpy(rng.permutation(tr.size)[:B]).cuda()].to(torch.int32).contiguous()
+                for _ in range(600)]
+    gm.train_step(ix, wind, mbatches[0], idx, mopt)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for rb in mbatches[1:]:
+        gm.train_step(ix, wind, rb, idx, mopt)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_gm_train = e0.elapsed_time(e1) / (len(mbatches) - 1)
+    gm.forward(ix, wind, idx_te, q=qte)
+    torch.cuda.synchronize()
+    with _Range("gkamlp_forward"):
+        ms_gm = _timed(lambda: gm.forward(ix, wind, idx_te, q=qte), steps)
+    gmpred = gm.forward(ix, wind, idx_te, q=qte)
+    rmse_gm = float(torch.sqrt(((gmpred - wind[ted]) ** 2).mean()))
     # the float64 oracle of each stage on a bounded sample (host cores)
     from oracle import nowcast as ncr
     ns = 20000
@@ -440,7 +461,16 @@ def _extras(tnn, synth, flush, peaks, steps):
                 "train_step": {"value": B / (ms_gka_train / 1e3), "unit": "samples/s", "ms": ms_gka_train,
                                "batch": B, "steps": gstep},
                 "sigma": [float(x) for x in gsig]},
-        "rmse_ms": {"mlp": rmse_mlp, "idw": rmse_idw, "gka": rmse_gka, "held_out_rows": int(te.size),
+        "gka_mlp": {"forward": {"value": qte.shape[0] / (ms_gm / 1e3), "unit": "nowcasts/s", "ms": ms_gm,
+                                "roofline": {"bound": "hbm", "achieved": gka_bytes / (ms_gm / 1e3) / 1e9,
+                                             "peak": hbm, "unit": "GB/s",
+                                             "frac": gka_bytes / (ms_gm / 1e3) / 1e9 / hbm,
+                                             "bytes_per_context": 28 * k + 24,
+                                             "peak_note": "of measured hbm_gbs"}},
+                    "train_step": {"value": B / (ms_gm_train / 1e3), "unit": "samples/s", "ms": ms_gm_train,
+                                   "batch": B, "steps": len(mbatches), "hidden": 32}},
+        "rmse_ms": {"mlp": rmse_mlp, "idw": rmse_idw, "gka": rmse_gka, "gka_mlp": rmse_gm,
+                    "held_out_rows": int(te.size),
                     "note": "synthetic wind field; noise floor 1 m/s per component (parity unpinned)"}}
     ix.destroy()
     return out

@@ -413,6 +413,42 @@ tnn_status tnn_gka_train_step(tnn_gka *gka, const tnn_index *index, const float 
                               const tnn_adamw_params *opt, float *d_loss, float *d_grad,
                               tnn_stream_t stream);
 
+/* --------------------------------------------------------------- GKA-MLP */
+
+typedef struct tnn_gkamlp tnn_gkamlp;
+
+/*
+ * GKA with scales that depend on the location (Sec. 3.2: the scales as a
+ * function of space, modelled by an MLP; the GKA-MLP-TNN model of Table 2):
+ *     theta(q) = tanh(u W1 + b1) W2 + b2,  u = (q_xyz - lo) / (hi - lo),
+ *     s(q) = exp(theta(q)) = (s_xy, s_z, s_t) at q,
+ * then the nowcast of tnn_gka_forward with s(q).  lo and hi are the bounding
+ * box of the index's points.  Flat parameters (float32):
+ *     W1 [3][H] | b1 [H] | W2 [H][3] | b2 [3],  H = hidden in [1, 32].
+ * Initialisation from `seed`: W1, b1 ~ U(-1/sqrt(3), 1/sqrt(3)), W2 = 0 and
+ * b2 = log(h_sigma), so the model starts as tnn_gka with h_sigma.
+ */
+tnn_status tnn_gkamlp_create(const float *h_sigma, int32_t hidden, uint64_t seed,
+                             tnn_gkamlp **out);
+void tnn_gkamlp_destroy(tnn_gkamlp *model);
+int64_t tnn_gkamlp_num_params(const tnn_gkamlp *model);
+/* Host copy of the flat parameters and the Adam step.  Synchronous. */
+tnn_status tnn_gkamlp_get_params(const tnn_gkamlp *model, float *h_params, int64_t *h_step);
+/* Set the parameters and restart Adam.  Synchronous. */
+tnn_status tnn_gkamlp_set_params(tnn_gkamlp *model, const float *h_params);
+/* Arguments and results as tnn_gka_forward. */
+tnn_status tnn_gkamlp_forward(const tnn_gkamlp *model, const tnn_index *index,
+                              const float *d_wind, const float *d_q, int64_t m,
+                              const int32_t *d_idx, int32_t k, float *d_uv,
+                              tnn_stream_t stream);
+/* Arguments and results as tnn_gka_train_step; d_grad (optional) receives
+   tnn_gkamlp_num_params floats in the flat layout. */
+tnn_status tnn_gkamlp_train_step(tnn_gkamlp *model, const tnn_index *index,
+                                 const float *d_wind, const int32_t *d_rows, int64_t B,
+                                 const int32_t *d_idx, int32_t k,
+                                 const tnn_adamw_params *opt, float *d_loss, float *d_grad,
+                                 tnn_stream_t stream);
+
 /*
  * Nowcast wind at the queries: TNN context (tnn_knn), features and IDW
  * (tnn_context_features), then the MLP when `mlp` is non-NULL (its input

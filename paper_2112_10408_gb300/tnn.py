@@ -106,6 +106,14 @@ _SIGNATURES = [
     ("tnn_gka_forward", c_i32, [c_p, c_p, c_p, c_p, c_i64, c_p, c_i32, c_p, c_p]),
     ("tnn_gka_train_step", c_i32, [c_p, c_p, c_p, c_p, c_i64, c_p, c_i32,
                                    ctypes.POINTER(tnn_adamw_params), c_p, c_p, c_p]),
+    ("tnn_gkamlp_create", c_i32, [c_p, c_i32, ctypes.c_uint64, ctypes.POINTER(c_p)]),
+    ("tnn_gkamlp_destroy", None, [c_p]),
+    ("tnn_gkamlp_num_params", c_i64, [c_p]),
+    ("tnn_gkamlp_get_params", c_i32, [c_p, c_p, ctypes.POINTER(c_i64)]),
+    ("tnn_gkamlp_set_params", c_i32, [c_p, c_p]),
+    ("tnn_gkamlp_forward", c_i32, [c_p, c_p, c_p, c_p, c_i64, c_p, c_i32, c_p, c_p]),
+    ("tnn_gkamlp_train_step", c_i32, [c_p, c_p, c_p, c_p, c_i64, c_p, c_i32,
+                                      ctypes.POINTER(tnn_adamw_params), c_p, c_p, c_p]),
     ("tnn_nowcast", c_i32, [c_p, c_p, c_p, c_i64, ctypes.POINTER(tnn_knn_params), c_p, c_p, c_p,
                             c_f32, c_p, c_p]),
 ]
@@ -579,6 +587,83 @@ class GKA:
     def destroy(self):
         if getattr(self, "_h", None) is not None and _lib is not None:
             _lib.tnn_gka_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class GKAMLP:
+    """tnn_gkamlp: GKA whose scales are an MLP of the normalised location."""
+
+    def __init__(self, sigma=(1.0, 10.0, 0.01), hidden: int = 32, seed: int = 0):
+        h = c_p()
+        sig = np.ascontiguousarray(np.asarray(sigma, np.float32))
+        _check(_L().tnn_gkamlp_create(sig.ctypes.data_as(c_p), int(hidden), ctypes.c_uint64(seed),
+                                      ctypes.byref(h)))
+        self._h = h
+        self.hidden = int(hidden)
+        self.n_params = int(_L().tnn_gkamlp_num_params(h))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def tnn_gkamlp_get_params(self):
+        """(flat parameters float32, Adam step)."""
+        w = np.empty(self.n_params, np.float32)
+        step = c_i64()
+        _check(_L().tnn_gkamlp_get_params(self._h, w.ctypes.data_as(c_p), ctypes.byref(step)))
+        return w, int(step.value)
+
+    get_params = tnn_gkamlp_get_params
+
+    def tnn_gkamlp_set_params(self, w):
+        w = np.ascontiguousarray(np.asarray(w, np.float32))
+        if w.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {w.size}")
+        _check(_L().tnn_gkamlp_set_params(self._h, w.ctypes.data_as(c_p)))
+
+    set_params = tnn_gkamlp_set_params
+
+    def tnn_gkamlp_forward(self, index: Index, wind: torch.Tensor, idx: torch.Tensor, q=None):
+        wind = _dev(wind, torch.float32, (2,), "wind")
+        m, k = idx.shape
+        _dev(idx, torch.int32, (k,), "idx")
+        if q is not None:
+            q = _dev(q, torch.float32, (4,), "q")
+        uv = torch.empty((m, 2), dtype=torch.float32, device="cuda")
+        _check(_L().tnn_gkamlp_forward(self._h, index.handle, _ptr(wind), _ptr(q), m, _ptr(idx), k,
+                                       _ptr(uv), _stream()))
+        return uv
+
+    forward = tnn_gkamlp_forward
+
+    def tnn_gkamlp_train_step(self, index: Index, wind: torch.Tensor, rows: torch.Tensor,
+                              idx: torch.Tensor, opt: "AdamW | None" = None, loss=None, grad=None):
+        wind = _dev(wind, torch.float32, (2,), "wind")
+        rows = _dev(rows, torch.int32, None, "rows")
+        _dev(idx, torch.int32, (idx.shape[1],), "idx")
+        o = opt.c() if opt is not None else None
+        _check(_L().tnn_gkamlp_train_step(self._h, index.handle, _ptr(wind), _ptr(rows), rows.shape[0],
+                                          _ptr(idx), idx.shape[1], ctypes.byref(o) if o is not None else None,
+                                          _ptr(loss), _ptr(grad), _stream()))
+
+    train_step = tnn_gkamlp_train_step
+
+    def gradients(self, index: Index, wind, rows, idx):
+        """(loss, gradient in the flat layout) on the batch; no update."""
+        loss = torch.empty((1,), dtype=torch.float32, device="cuda")
+        grad = torch.empty((self.n_params,), dtype=torch.float32, device="cuda")
+        self.tnn_gkamlp_train_step(index, wind, rows, idx, None, loss, grad)
+        return loss, grad
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.tnn_gkamlp_destroy(self._h)
         self._h = None
 
     def __del__(self):

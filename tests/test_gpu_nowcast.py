@@ -269,3 +269,57 @@ def test_gka_training_lowers_the_loss():
     assert float(l1.item()) < (1 - 1e-3) * float(l0.item())
     _, g0 = tnn.GKA((1.0, 10.0, 0.01)).gradients(ix, wind, full, idx)
     assert float(g1.norm()) < float(g0.norm())
+
+
+def test_gkamlp_starts_as_gka_and_matches_oracle():
+    wl, ix, idx, wind = _gka_setup()
+    sig = np.array([0.05, 4.0, 1e-4], np.float32)
+    g = tnn.GKAMLP(sig, hidden=16, seed=3)
+    plain = tnn.GKA(sig)
+    a = g.forward(ix, wind, idx).cpu().numpy()
+    b = plain.forward(ix, wind, idx).cpu().numpy()
+    ok = ~np.isnan(b).any(axis=1)
+    np.testing.assert_allclose(a[ok], b[ok], rtol=2e-5, atol=2e-5)
+    # a model with non-zero output weights against the oracle
+    rng = np.random.default_rng(4)
+    w, _ = g.get_params()
+    H = 16
+    w[4 * H:7 * H] = (0.5 * rng.normal(size=3 * H)).astype(np.float32)
+    g.set_params(w)
+    lo, hi = wl.xyzt.min(axis=0), wl.xyzt.max(axis=0)
+    got = g.forward(ix, wind, idx).cpu().numpy()
+    ref = nc.gkamlp_forward(wl.xyzt, wl.wind, wl.xyzt, idx.cpu().numpy(), w, H, lo, hi)
+    ok = ~np.isnan(ref).any(axis=1)
+    assert np.isnan(got[~ok]).all()
+    np.testing.assert_allclose(got[ok], ref[ok], rtol=2e-4, atol=2e-4)
+
+
+def test_gkamlp_gradient_and_adam_steps_match_oracle():
+    wl, ix, idx, wind = _gka_setup()
+    idx_h = idx.cpu().numpy()
+    rows = np.nonzero((idx_h >= 0).all(axis=1))[0][:1500].astype(np.int32)
+    rows_d = torch.from_numpy(rows).cuda()
+    H = 8
+    g = tnn.GKAMLP((0.05, 4.0, 1e-4), hidden=H, seed=5)
+    w, _ = g.get_params()
+    w[4 * H:7 * H] = (0.3 * np.random.default_rng(6).normal(size=3 * H)).astype(np.float32)
+    g.set_params(w)
+    lo, hi = wl.xyzt.min(axis=0), wl.xyzt.max(axis=0)
+    loss, grad = g.gradients(ix, wind, rows_d, idx)
+    rl, rg = nc.gkamlp_loss_grad(wl.xyzt, wl.wind, rows, idx_h, w, H, lo, hi)
+    assert float(loss.item()) == pytest.approx(rl, rel=1e-4)
+    np.testing.assert_allclose(grad.cpu().numpy(), rg, rtol=5e-3, atol=2e-3 * np.abs(rg).max())
+    opt = tnn.AdamW(lr=0.02, weight_decay=0.0)
+    wk = w.astype(np.float64)
+    mm = np.zeros_like(wk)
+    vv = np.zeros_like(wk)
+    for t in range(1, 3):
+        _, gt = nc.gkamlp_loss_grad(wl.xyzt, wl.wind, rows, idx_h, wk, H, lo, hi)
+        g.train_step(ix, wind, rows_d, idx, opt)
+        wk, mm, vv = nc.adamw_step(wk, gt, mm, vv, t, lr=opt.lr, beta1=opt.beta1, beta2=opt.beta2,
+                                   eps=opt.eps, wd=0.0)
+        got, step = g.get_params()
+        assert step == t
+        # Adam normalises each coordinate: compare where the gradient is not tiny
+        big = np.abs(gt) > 1e-3 * np.abs(gt).max()
+        np.testing.assert_allclose(got[big], wk[big], rtol=0, atol=3e-3)
