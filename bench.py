@@ -194,7 +194,7 @@ def run_reference(a):
     oracle.build()
     wl, k, K = _workload(a.workload, 0)
     cores = os.cpu_count() or 1
-    per_step = 64 if a.workload != "tiny" else 2048
+    per_step = 2048  # ~0.1 s of the 16-thread oracle per step at 400,000 points
     for w in range(a.warmup):
         oracle.knn(wl.xyzt, k, (1.0, 1.0, 10.0, 0.01), qsel=synth.query_sample(wl.n, per_step, seed=w),
                    nthreads=cores)
