@@ -368,10 +368,35 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
             }
         }
         __syncwarp();
+        // Settle.  When no two of the first k keys are close enough to need
+        // FP64 (no chain), the answer is the first k keys as they are and the
+        // warp writes it; otherwise lane 0 settles the chains.
         bool ok = true;
-        if (lane == 0)
-            ok = finalize_query(W, q, wl.L, wl.C, cl_d, cl_i, ent.y, st, 1);
-        ok = __shfl_sync(FULLMASK, ok, 0);
+        {
+            const int k = W->k;
+            bool chain = (W->flags & TNN_FLAG_EXACT_D2) != 0;
+            for (int i = lane; i < k; i += 32) {
+                const unsigned long long ki = wl.L[i];
+                if (ki != SENT && i + 1 < wl.C) {
+                    const unsigned long long kn = wl.L[i + 1];
+                    const float de = key_d(ki);
+                    chain |= kn != SENT && key_d(kn) <= fmaf(de, 0x1p-17f, de) + 0x1p-100f;
+                }
+            }
+            if (!__any_sync(FULLMASK, chain)) {
+                int32_t *oi = W->out_idx + (int64_t)ent.y * k;
+                float *od = W->out_d2 + (int64_t)ent.y * k;
+                for (int i = lane; i < k; i += 32) {
+                    const unsigned long long ki = wl.L[i];
+                    oi[i] = ki == SENT ? -1 : key_i(ki);
+                    od[i] = ki == SENT ? INFINITY : key_d(ki);
+                }
+            } else {
+                if (lane == 0)
+                    ok = finalize_query(W, q, wl.L, wl.C, cl_d, cl_i, ent.y, st, 1);
+                ok = __shfl_sync(FULLMASK, ok, 0);
+            }
+        }
         // a tie chain ran past the end of a k + extra list: once more with
         // k + FB_EXTRA slots before the FP64 definition is used
         retry = !ok && wl.C < W->k + FB_EXTRA;
