@@ -119,7 +119,10 @@ __device__ __forceinline__ void wl_merge(WarpList &w, unsigned long long ck, int
     w.tauk = w.nv == w.C ? w.L[w.C - 1] : SENT;
 }
 
-__global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
+#ifndef TNN_WARP_MINB
+#define TNN_WARP_MINB 8 // 8 CTAs (32 warps) per SM: this kernel waits on chains of dependent loads
+#endif
+__global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_WARP_MINB)
     k_tnn_warp(const __grid_constant__ KnnLaunch L)
 {
     extern __shared__ __align__(16) unsigned char smem[];
