@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_WARP_MINB)
                         else
                             z = mid - 1;
                     }
-                    const float4 *src = seg + 4 * (size_t)__ldg(G.ids + Klo[a] + (g - Kstart[a]));
+                    const float4 *src = G.gseg + 4 * (size_t)(Klo[a] + (g - Kstart[a]));
                     meta = __ldg(src + 3);
                     lb = seg_lb(c, s3, __ldg(src), __ldg(src + 1), __ldg(src + 2));
                     st.lb++;

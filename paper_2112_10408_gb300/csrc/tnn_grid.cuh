@@ -86,7 +86,6 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_GRID_MINB)
         const float4 *__restrict__ pts = W->pts;
         const GridDesc &G = W->grid;
         const int32_t *__restrict__ goff = G.off;
-        const int32_t *__restrict__ gids = G.ids;
         const int Lw = W->L, F = W->F;
 
         const float tmax = warp_maxf(c.T32);
@@ -185,12 +184,13 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_GRID_MINB)
                 __syncwarp();
                 int mypos = -1;
                 if (lane < cnt) {
-                    mypos = __ldg(gids + base + lane);
-                    const float4 *src = seg + 4 * (size_t)mypos;
+                    const float4 *src = G.gseg + 4 * (size_t)(base + lane);
                     segbuf[4 * lane] = __ldg(src);
                     segbuf[4 * lane + 1] = __ldg(src + 1);
                     segbuf[4 * lane + 2] = __ldg(src + 2);
-                    segbuf[4 * lane + 3] = __ldg(src + 3);
+                    const float4 r3 = __ldg(src + 3);
+                    segbuf[4 * lane + 3] = r3;
+                    mypos = __float_as_int(r3.z);
                 }
                 __syncwarp();
                 if (seed_mode) {

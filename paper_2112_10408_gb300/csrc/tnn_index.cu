@@ -451,6 +451,24 @@ __global__ void k_grid_ids(const unsigned long long *__restrict__ keys, int S,
         ids[i] = (int32_t)(keys[i] & 0xffffffffu);
 }
 
+// Segment records in grid-key order (record 3's trajectory field replaced by
+// the t_A position), so that the search reads a key's segments without an
+// indirection.
+__global__ void k_grid_records(const float4 *__restrict__ seg, const int32_t *__restrict__ ids, int S,
+                               float4 *__restrict__ gseg)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S)
+        return;
+    const int p = ids[i];
+    gseg[4 * (size_t)i] = seg[4 * (size_t)p];
+    gseg[4 * (size_t)i + 1] = seg[4 * (size_t)p + 1];
+    gseg[4 * (size_t)i + 2] = seg[4 * (size_t)p + 2];
+    float4 r3 = seg[4 * (size_t)p + 3];
+    r3.z = __int_as_float(p);
+    gseg[4 * (size_t)i + 3] = r3;
+}
+
 __global__ void k_decode_ord(unsigned int *__restrict__ v, int n)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -486,6 +504,7 @@ static void free_index(tnn_index *ix)
     cudaFree(ix->idx_t);
     cudaFree(ix->g_off);
     cudaFree(ix->g_ids);
+    cudaFree(ix->g_seg);
     cudaFree(ix->g_ext);
     cudaFree(ix->g_tB);
     cudaFree(ix->g_bpm);
@@ -574,6 +593,7 @@ static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
     const int nkeys = nb * g.ncell;
     TNN_CUDA_TRY(cudaMalloc(&ix->g_off, sizeof(int32_t) * (nkeys + 1)));
     TNN_CUDA_TRY(cudaMalloc(&ix->g_ids, sizeof(int32_t) * S));
+    TNN_CUDA_TRY(cudaMalloc(&ix->g_seg, sizeof(float4) * 4 * (size_t)S));
     TNN_CUDA_TRY(cudaMalloc(&ix->g_ext, sizeof(float) * nkeys));
     TNN_CUDA_TRY(cudaMalloc(&ix->g_tB, sizeof(float) * nkeys));
     TNN_CUDA_TRY(cudaMalloc(&ix->g_bpm, sizeof(float) * nb));
@@ -588,6 +608,7 @@ static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
     tnn_bitonic_sort(keys, s2, st);
     k_grid_offsets<<<(nkeys + 1 + tb - 1) / tb, tb, 0, st>>>(keys, S, nkeys, ix->g_off);
     k_grid_ids<<<(S + tb - 1) / tb, tb, 0, st>>>(keys, S, ix->g_ids);
+    k_grid_records<<<(S + tb - 1) / tb, tb, 0, st>>>(ix->seg, ix->g_ids, S, ix->g_seg);
     k_decode_ord<<<(nkeys + tb - 1) / tb, tb, 0, st>>>((unsigned int *)ix->g_tB, nkeys);
     k_decode_ord<<<(nb + tb - 1) / tb, tb, 0, st>>>((unsigned int *)ix->g_bpm, nb);
     k_prefix_max<<<1, 32, 0, st>>>(ix->g_bpm, nb);
@@ -615,6 +636,7 @@ static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
     G.nb = nb;
     G.off = ix->g_off;
     G.ids = ix->g_ids;
+    G.gseg = ix->g_seg;
     G.ext = ix->g_ext;
     G.tB = ix->g_tB;
     G.bpm = ix->g_bpm;

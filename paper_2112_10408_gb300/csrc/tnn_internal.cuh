@@ -48,6 +48,8 @@ struct GridDesc {
     int32_t nx, ny, ncell, nb;
     const int32_t *off; // [nb * ncell + 1]
     const int32_t *ids; // [S] segment positions (t_A order) grouped by key
+    const float4 *gseg; // [S][4] the same segments' records in that key order;
+                        // record 3 carries the t_A position in .z
     const float *ext;   // [nb * ncell]
     const float *tB;    // [nb * ncell]
     const float *bpm;   // [nb] running max over buckets <= b of the max t_B
@@ -72,6 +74,7 @@ struct tnn_index {
     int32_t *idx_t;  // [n] their input index
     GridDesc grid;   // views of the arrays below
     int32_t *g_off, *g_ids;
+    float4 *g_seg;
     float *g_ext, *g_tB, *g_bpm;
     float bb_lo[4], bb_hi[4]; // bounding box of the points (x, y, z, t)
 };
