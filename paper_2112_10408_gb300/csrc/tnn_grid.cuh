@@ -176,51 +176,60 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_GRID_MINB)
         float wF = INFINITY;
         int nu = 0;
 
-        // Consider the member segments ids[lo, hi) of one key: seed mode keeps
-        // the F smallest bounds, main mode scans where the bound allows.
-        auto visit = [&](int lo, int hi, bool seed_mode) {
-            for (int base = lo; base < hi; base += 32) {
-                const int cnt = min(32, hi - base);
-                __syncwarp();
-                int mypos = -1;
-                if (lane < cnt) {
-                    const float4 *src = G.gseg + 4 * (size_t)(base + lane);
-                    segbuf[4 * lane] = __ldg(src);
-                    segbuf[4 * lane + 1] = __ldg(src + 1);
-                    segbuf[4 * lane + 2] = __ldg(src + 2);
-                    const float4 r3 = __ldg(src + 3);
-                    segbuf[4 * lane + 3] = r3;
-                    mypos = __float_as_int(r3.z);
-                }
-                __syncwarp();
-                if (seed_mode) {
-                    for (int i = 0; i < cnt; ++i) {
-                        const int pos = __shfl_sync(FULLMASK, mypos, i);
-                        const float lb = seg_lb(c, s3, segbuf[4 * i], segbuf[4 * i + 1],
-                                                segbuf[4 * i + 2]);
-                        if (active && lb < wF) {
-                            float cur = lb;
-                            int cp = pos;
+        // Records of up to 32 segments into segbuf (lane j loads gseg[src_j]);
+        // returns this lane's segment position in the t_A order.
+        auto load_records = [&](int src, bool have) -> int {
+            __syncwarp();
+            int mypos = -1;
+            if (have) {
+                const float4 *r = G.gseg + 4 * (size_t)src;
+                segbuf[4 * lane] = __ldg(r);
+                segbuf[4 * lane + 1] = __ldg(r + 1);
+                segbuf[4 * lane + 2] = __ldg(r + 2);
+                const float4 r3 = __ldg(r + 3);
+                segbuf[4 * lane + 3] = r3;
+                mypos = __float_as_int(r3.z);
+            }
+            __syncwarp();
+            return mypos;
+        };
+        // Seed selection over the cnt staged segments: every lane keeps its F
+        // smallest cylinder bounds.
+        auto seed_pick = [&](int cnt, int mypos) {
+            for (int i = 0; i < cnt; ++i) {
+                const int pos = __shfl_sync(FULLMASK, mypos, i);
+                const float lb = seg_lb(c, s3, segbuf[4 * i], segbuf[4 * i + 1], segbuf[4 * i + 2]);
+                if (active && lb < wF) {
+                    float cur = lb;
+                    int cp = pos;
 #pragma unroll
-                            for (int f = 0; f < TNN_GMAX_F; ++f) {
-                                if (f < F && cur < bl[f]) {
-                                    const float tf = bl[f];
-                                    bl[f] = cur;
-                                    cur = tf;
-                                    const int tp = bp[f];
-                                    bp[f] = cp;
-                                    cp = tp;
-                                }
-                            }
-#pragma unroll
-                            for (int f = 0; f < TNN_GMAX_F; ++f)
-                                if (f == F - 1)
-                                    wF = bl[f];
+                    for (int f = 0; f < TNN_GMAX_F; ++f) {
+                        if (f < F && cur < bl[f]) {
+                            const float tf = bl[f];
+                            bl[f] = cur;
+                            cur = tf;
+                            const int tp = bp[f];
+                            bp[f] = cp;
+                            cp = tp;
                         }
                     }
-                    if (active)
-                        st.lb += cnt;
-                } else {
+#pragma unroll
+                    for (int f = 0; f < TNN_GMAX_F; ++f)
+                        if (f == F - 1)
+                            wF = bl[f];
+                }
+            }
+            if (active)
+                st.lb += cnt;
+        };
+
+        // Main mode over the member segments [lo, hi) (key order) of one key:
+        // scan those whose bound allows.
+        auto visit = [&](int lo, int hi) {
+            for (int base = lo; base < hi; base += 32) {
+                const int cnt = min(32, hi - base);
+                const int mypos = load_records(base + lane, lane < cnt);
+                {
                     bool sd = false;
                     if (lane < cnt)
                         for (int u = 0; u < nu; ++u)
@@ -247,21 +256,39 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_GRID_MINB)
         if (bhi >= 0) {
             const int hx = min(max((int)floorf((0.5f * (bx0 + bx1) - G.x0) * G.inv_cell), 0), G.nx - 1);
             const int hy = min(max((int)floorf((0.5f * (by0 + by1) - G.y0) * G.inv_cell), 0), G.ny - 1);
-            for (int b = bhi; b >= 0 && b >= bhi - 1; --b) {
-                const int cx = hx + lane % 3 - 1, cy = hy + lane / 3 - 1;
-                const bool ok = lane < 9 && cx >= 0 && cx < G.nx && cy >= 0 && cy < G.ny;
-                int lo = 0, hi = 0;
-                if (ok) {
-                    const int key = b * G.ncell + cy * G.nx + cx;
-                    lo = __ldg(goff + key);
-                    hi = __ldg(goff + key + 1);
+            // lanes 0..17 hold the 3 x 3 cells of buckets bhi and bhi - 1; the
+            // member segments of all 18 keys are staged 32 at a time
+            const int bq = bhi - lane / 9, cl = lane % 9;
+            const int cx = hx + cl % 3 - 1, cy = hy + cl / 3 - 1;
+            const bool ok = lane < 18 && bq >= 0 && cx >= 0 && cx < G.nx && cy >= 0 && cy < G.ny;
+            int lo = 0, n = 0;
+            if (ok) {
+                const int key = bq * G.ncell + cy * G.nx + cx;
+                lo = __ldg(goff + key);
+                n = __ldg(goff + key + 1) - lo;
+            }
+            int inc = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(FULLMASK, inc, o);
+                if (lane >= o)
+                    inc += v;
+            }
+            const int total = __shfl_sync(FULLMASK, inc, 31);
+            const int rel = lo - (inc - n); // record index = rel_j + position in the batch
+            for (int base = 0; base < total; base += 32) {
+                const int t = base + lane;
+                int src = 0;
+#pragma unroll
+                for (int j = 0; j < 18; ++j) {
+                    const int ij = __shfl_sync(FULLMASK, inc, j);
+                    const int rj = __shfl_sync(FULLMASK, rel, j);
+                    if (src == 0 && t < ij)
+                        src = rj + t + 1; // +1 keeps 0 as "unset"
                 }
-                unsigned m = __ballot_sync(FULLMASK, hi > lo);
-                while (m) {
-                    const int j = __ffs(m) - 1;
-                    m &= m - 1;
-                    visit(__shfl_sync(FULLMASK, lo, j), __shfl_sync(FULLMASK, hi, j), true);
-                }
+                const int cnt = min(32, total - base);
+                const int mypos = load_records(src - 1, lane < cnt);
+                seed_pick(cnt, mypos);
             }
         }
 
@@ -351,7 +378,7 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_GRID_MINB)
                         const float rx0 = G.x0 + (float)(cxb + j) * G.cell, rx1 = rx0 + G.cell;
                         const bool want = !done && cell_lb(c, s3, rx0, rx1, ry0, ry1, jex, jtk) <= tau;
                         if (__any_sync(FULLMASK, want))
-                            visit(jlo, jhi, false);
+                            visit(jlo, jhi);
                     }
                 }
             }
