@@ -79,7 +79,8 @@ struct WarpList {
     unsigned long long *tmp; // [C]
     unsigned long long *B;   // [32]
     int C, nv;
-    unsigned long long tauk; // largest key kept once full, else SENT
+    unsigned long long tauk; // largest key kept once full, else bound0
+    unsigned long long bound0; // no key above it can enter the list
 };
 
 // Merge the keys below the pruning key (at most one per lane) into the list.
@@ -116,7 +117,7 @@ __device__ __forceinline__ void wl_merge(WarpList &w, unsigned long long ck, int
         w.L[p] = w.tmp[p];
     __syncwarp();
     w.nv = min(na + nb, w.C);
-    w.tauk = w.nv == w.C ? w.L[w.C - 1] : SENT;
+    w.tauk = w.nv == w.C ? w.L[w.C - 1] : w.bound0;
 }
 
 #ifndef TNN_WARP_MINB
@@ -149,6 +150,7 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_WARP_MINB)
     LaneStats st = {0, 0, 0, 0, 0};
     int2 ent = make_int2(0, 0);
     bool retry = false; // the same query again with the larger list
+    float tau0 = INFINITY;
     for (;;) {
         if (!retry) {
             // dynamic queue: query costs differ by orders of magnitude
@@ -159,6 +161,7 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_WARP_MINB)
             if (e >= nfb)
                 break;
             ent = L.fb_list[e];
+            tau0 = L.fb_tau[e];
         }
         const bool unsettled = retry || ent.x < 0;
         const int wid = ent.x < 0 ? -1 - ent.x : ent.x;
@@ -171,7 +174,13 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_WARP_MINB)
         const GridDesc &G = W->grid;
         wl.C = unsettled ? W->k + FB_EXTRA : W->L;
         wl.nv = 0;
-        wl.tauk = SENT;
+        // A deferred query arrives with the pruning key tau0 of the tile
+        // kernel's list of the same length (the same FP32 keys): its final
+        // list holds no key with a distance above tau0.
+        wl.bound0 = (unsettled || !(tau0 < INFINITY))
+                        ? SENT
+                        : (((unsigned long long)__float_as_uint(tau0) << 32) | 0xffffffffull);
+        wl.tauk = wl.bound0;
         for (int p = lane; p < wl.C; p += 32)
             wl.L[p] = SENT;
         __syncwarp();
@@ -334,9 +343,13 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_WARP_MINB)
             }
             // ---- main: buckets backwards, keys within reach, by bound
             if (rs < rcover) {
+                float bpm_next = __ldg(G.bpm + bhi); // one bucket ahead
                 for (int b = bhi; b >= 0; --b) {
                     const float tau = key_d(wl.tauk);
-                    if (!(time_lb(c, s3, __ldg(G.bpm + b)) <= tau))
+                    const float bpm_b = bpm_next;
+                    if (b > 0)
+                        bpm_next = __ldg(G.bpm + b - 1);
+                    if (!(time_lb(c, s3, bpm_b) <= tau))
                         break;
                     const float R = sqrtf(tau) * (1.0f + 0x1p-18f) + G.ext_max + c.delta;
                     const int cx0 = max((int)floorf(fmaxf((c.sx - R - G.x0) * G.inv_cell, -1.0f)) - 1, 0);
@@ -353,12 +366,13 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_WARP_MINB)
                             const bool seeded = bseed && abs(cx - hx) <= rs && abs(cy - hy) <= rs;
                             if (!seeded) {
                                 const int k2 = b * G.ncell + cy * G.nx + cx;
-                                const int a0 = __ldg(G.off + k2), a1 = __ldg(G.off + k2 + 1);
+                                const int4 kr = __ldg(G.krec + k2);
+                                const int a0 = kr.x, a1 = kr.y;
                                 if (a1 > a0) {
                                     const float rx0 = G.x0 + (float)cx * G.cell;
                                     const float ry0 = G.y0 + (float)cy * G.cell;
                                     if (cell_lb(c, s3, rx0, rx0 + G.cell, ry0, ry0 + G.cell,
-                                                __ldg(G.ext + k2), __ldg(G.tB + k2)) <= key_d(wl.tauk)) {
+                                                __int_as_float(kr.z), __int_as_float(kr.w)) <= key_d(wl.tauk)) {
                                         klo = a0;
                                         khi = a1;
                                     }

@@ -332,9 +332,10 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_GRID_MINB)
         const bool deferred = active && !(tau <= W->tau_defer);
         if (deferred) {
             const unsigned slot = atomicAdd(&L.scr->n_fallback, 1u);
-            if (slot < (unsigned long long)L.fb_cap)
+            if (slot < (unsigned long long)L.fb_cap) {
                 L.fb_list[slot] = make_int2(window_id(L, W), (int)qrow);
-            else
+                L.fb_tau[slot] = tau;
+            } else
                 atomicOr(&L.scr->status, 1u);
         }
 
@@ -362,10 +363,11 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_GRID_MINB)
                     float ex = 0.f, tk = 0.f;
                     if (cx <= cx1) {
                         const int key = kb + cy * G.nx + cx;
-                        lo = __ldg(goff + key);
-                        hi = __ldg(goff + key + 1);
-                        ex = __ldg(G.ext + key);
-                        tk = __ldg(G.tB + key);
+                        const int4 kr = __ldg(G.krec + key);
+                        lo = kr.x;
+                        hi = kr.y;
+                        ex = __int_as_float(kr.z);
+                        tk = __int_as_float(kr.w);
                     }
                     unsigned m = __ballot_sync(FULLMASK, hi > lo);
                     while (m) {

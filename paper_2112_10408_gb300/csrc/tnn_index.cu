@@ -478,6 +478,15 @@ __global__ void k_decode_ord(unsigned int *__restrict__ v, int n)
     }
 }
 
+// Per key, its CSR range, extent and largest t_B packed in one record.
+__global__ void k_key_records(const int32_t *__restrict__ off, const float *__restrict__ ext,
+                              const float *__restrict__ tB, int nkeys, int4 *__restrict__ kr)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nkeys)
+        kr[i] = make_int4(off[i], off[i + 1], __float_as_int(ext[i]), __float_as_int(tB[i]));
+}
+
 // Running maximum over buckets (one block).
 __global__ void k_prefix_max(float *__restrict__ v, int n)
 {
@@ -507,6 +516,7 @@ static void free_index(tnn_index *ix)
     cudaFree(ix->g_seg);
     cudaFree(ix->g_ext);
     cudaFree(ix->g_tB);
+    cudaFree(ix->g_krec);
     cudaFree(ix->g_bpm);
     delete ix;
 }
@@ -597,6 +607,7 @@ static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
     TNN_CUDA_TRY(cudaMalloc(&ix->g_ext, sizeof(float) * nkeys));
     TNN_CUDA_TRY(cudaMalloc(&ix->g_tB, sizeof(float) * nkeys));
     TNN_CUDA_TRY(cudaMalloc(&ix->g_bpm, sizeof(float) * nb));
+    TNN_CUDA_TRY(cudaMalloc(&ix->g_krec, sizeof(int4) * (size_t)nkeys));
     TNN_CUDA_TRY(cudaMemsetAsync(ix->g_ext, 0, sizeof(float) * nkeys, st));
     TNN_CUDA_TRY(cudaMemsetAsync(ix->g_tB, 0, sizeof(float) * nkeys, st));
     TNN_CUDA_TRY(cudaMemsetAsync(ix->g_bpm, 0, sizeof(float) * nb, st));
@@ -612,6 +623,8 @@ static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
     k_decode_ord<<<(nkeys + tb - 1) / tb, tb, 0, st>>>((unsigned int *)ix->g_tB, nkeys);
     k_decode_ord<<<(nb + tb - 1) / tb, tb, 0, st>>>((unsigned int *)ix->g_bpm, nb);
     k_prefix_max<<<1, 32, 0, st>>>(ix->g_bpm, nb);
+    k_key_records<<<(nkeys + tb - 1) / tb, tb, 0, st>>>(ix->g_off, ix->g_ext, ix->g_tB, nkeys,
+                                                       ix->g_krec);
     TNN_CUDA_TRY(cudaGetLastError());
     // largest extent (for the search region)
     std::vector<float> hext(nkeys);
@@ -640,6 +653,7 @@ static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
     G.ext = ix->g_ext;
     G.tB = ix->g_tB;
     G.bpm = ix->g_bpm;
+    G.krec = ix->g_krec;
     return TNN_OK;
 }
 

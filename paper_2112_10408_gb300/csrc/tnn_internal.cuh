@@ -53,6 +53,8 @@ struct GridDesc {
     const float *ext;   // [nb * ncell]
     const float *tB;    // [nb * ncell]
     const float *bpm;   // [nb] running max over buckets <= b of the max t_B
+    const int4 *krec;   // [nb * ncell] (off[k], off[k + 1], ext bits, tB bits):
+                        // one 16-byte load per key in the search
 };
 
 struct tnn_index {
@@ -76,6 +78,7 @@ struct tnn_index {
     int32_t *g_off, *g_ids;
     float4 *g_seg;
     float *g_ext, *g_tB, *g_bpm;
+    int4 *g_krec;
     float bb_lo[4], bb_hi[4]; // bounding box of the points (x, y, z, t)
 };
 
@@ -135,6 +138,8 @@ struct KnnLaunch {
     int2 *fb_list;        // (window, query) for the FP32 warp scan
     int2 *fb_list3;       // (window, query) for the exact FP64 warp scan
     int64_t fb_cap;       // capacity of each list
+    float *fb_tau;        // [fb_cap] pruning key of a deferred query when the
+                          // tile kernel handed it over (parallel to fb_list)
     const unsigned long long *qorder; // tensor-core linear search: sorted
                                       // (space-time key << 32 | query row)
 };

@@ -357,10 +357,11 @@ static tnn_status run_single(const tnn_index *ix, const float *d_q, int64_t m,
     L.fb_cap = m;
     const size_t hdr = 256;
     void *buf = nullptr;
-    TNN_CUDA_TRY(cudaMallocAsync(&buf, hdr + 2 * sizeof(int2) * (size_t)m, st));
+    TNN_CUDA_TRY(cudaMallocAsync(&buf, hdr + (2 * sizeof(int2) + sizeof(float)) * (size_t)m, st));
     L.scr = (KnnScratch *)buf;
     L.fb_list = (int2 *)((char *)buf + hdr);
     L.fb_list3 = L.fb_list + m;
+    L.fb_tau = (float *)(L.fb_list3 + m);
     cudaError_t e = cudaMemsetAsync(buf, 0, sizeof(KnnScratch), st);
     if (e != cudaSuccess) {
         cudaFreeAsync(buf, st);
@@ -492,7 +493,7 @@ extern "C" tnn_status tnn_batch_create(const tnn_index *const *indexes,
     cudaGetDevice(&b->device);
     cudaError_t e = cudaMalloc(&b->d_wins, sizeof(KnnWin) * n_windows);
     if (e == cudaSuccess)
-        e = cudaMalloc(&b->scratch, 256 + 2 * sizeof(int2) * (size_t)std::max(fb, 1ll));
+        e = cudaMalloc(&b->scratch, 256 + (2 * sizeof(int2) + sizeof(float)) * (size_t)std::max(fb, 1ll));
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_wins, wins.data(), sizeof(KnnWin) * n_windows, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -511,6 +512,7 @@ extern "C" tnn_status tnn_batch_create(const tnn_index *const *indexes,
     L.scr = (KnnScratch *)b->scratch;
     L.fb_list = (int2 *)((char *)b->scratch + 256);
     L.fb_list3 = L.fb_list + std::max(fb, 1ll);
+    L.fb_tau = (float *)(L.fb_list3 + std::max(fb, 1ll));
     L.fb_cap = fb;
     if (n_windows == 1)
         L.nwin = 1;

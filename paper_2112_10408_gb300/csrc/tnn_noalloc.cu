@@ -15,7 +15,7 @@
 // scratch header and the two fallback lists for that many queries.
 #define TNN_NOALLOC_MAX_QUERIES 65536
 #define TNN_NOALLOC_HEADER 256
-#define TNN_NOALLOC_BYTES (TNN_NOALLOC_HEADER + 2 * 8 * TNN_NOALLOC_MAX_QUERIES)
+#define TNN_NOALLOC_BYTES (TNN_NOALLOC_HEADER + (2 * 8 + 4) * TNN_NOALLOC_MAX_QUERIES)
 
 // Resident on every device that loads the library, until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[TNN_NOALLOC_BYTES];
@@ -75,6 +75,7 @@ extern "C" tnn_status tnn_knn_noalloc(const tnn_index *index, const float *d_q, 
     L.scr = (KnnScratch *)scr;
     L.fb_list = (int2 *)((char *)scr + TNN_NOALLOC_HEADER);
     L.fb_list3 = L.fb_list + m;
+    L.fb_tau = (float *)(L.fb_list3 + m);
     // The array keeps the previous call's contents: the queue counter, the
     // counters and the list lengths must start at zero.
     TNN_CUDA_TRY(cudaMemsetAsync(scr, 0, sizeof(KnnScratch), st));
