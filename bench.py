@@ -37,21 +37,24 @@ OPS_PER_KEY = 20
 # DRAM bytes (read + write) of one search on the medium workload, summed over
 # k_tnn_grid_search + k_tnn_warp + k_fallback_exact, from the ncu capture
 # summarised in profiles/k_tnn_grid_search_medium.md, with a hash of the
-# kernel sources it was taken on: once they change the figure is stale and
-# is reported as null.
-SEARCH_TRAFFIC = {"bytes": 44277760 + 6875648 + 113408, "workload": "medium",
+# kernel sources and the tuning it was taken on: once either differs the
+# figure is stale and is reported as null.
+SEARCH_TRAFFIC = {"bytes": (10436352 + 32720384) + (7972352 + 82944) + 113664, "workload": "medium",
                   "sources": ["tnn_device.cuh", "tnn_grid.cuh", "tnn_fallback.cuh", "tnn_internal.cuh",
-                              "tnn_knn.cu"],
-                  "sha256_16": "dd79ed4c7864b387"}
+                              "tnn_knn.cu", "tnn_index.cu"],
+                  "tuning": {"seed_segments": 3, "extra": 4, "defer_cells": 0.75},
+                  "sha256_16": "51a4030fefe40a62"}
 
 
-def _search_traffic(workload):
+def _search_traffic(workload, tune):
     import hashlib
     h = hashlib.sha256()
     for f in SEARCH_TRAFFIC["sources"]:
         with open(os.path.join(ROOT, "paper_2112_10408_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     if workload != SEARCH_TRAFFIC["workload"] or h.hexdigest()[:16] != SEARCH_TRAFFIC["sha256_16"]:
+        return None
+    if any(tune.get(k) != v for k, v in SEARCH_TRAFFIC["tuning"].items()):
         return None
     return SEARCH_TRAFFIC["bytes"]
 
@@ -556,7 +559,7 @@ def run_ours(a):
     alu_peak = nsm * 128 * sm_max * 1e6 / 1e12  # T FP32 lane-ops/s
     achieved = alg_ops / (kern_avg_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "T FP32 lane-ops/s",
-                "frac": achieved / alu_peak, "traffic": _search_traffic(a.workload),
+                "frac": achieved / alu_peak, "traffic": _search_traffic(a.workload, tune),
                 "kernel": "search = k_tnn_grid_search + k_tnn_warp + k_fallback_exact",
                 "kernel_ms": kern_avg_ms,
                 "peak_note": f"{nsm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived, not measured)",
