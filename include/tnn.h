@@ -260,6 +260,23 @@ tnn_status tnn_knn_work(const tnn_index *index, const float *d_q, int64_t m,
 tnn_status tnn_profile_enable(int32_t on);
 tnn_status tnn_profile_read(double *ms, int64_t *launches, int32_t reset);
 
+/* ----------------------------------------------------------------- memory */
+
+/*
+ * Device memory.  The index arrays and every call's scratch are taken, in
+ * stream order, from a memory pool private to the library (one per device)
+ * that keeps freed memory reserved for the next call: a build or a search
+ * maps no new pages and does not synchronise the device.  Destroying an
+ * index waits for the device (as cudaFree does) and returns its arrays to
+ * the pool.
+ * tnn_memory_trim: wait for the device, then release reserved memory not in
+ *   use down to keep_bytes (0: all of it).  keep_bytes < 0 is an error.
+ * tnn_memory_reserved: bytes the pool of the current device holds
+ *   (*h_reserved) and hands out (*h_used, may be NULL).
+ */
+tnn_status tnn_memory_trim(int64_t keep_bytes);
+tnn_status tnn_memory_reserved(int64_t *h_reserved, int64_t *h_used);
+
 /* ---------------------------------------------------------------- batched */
 
 typedef struct tnn_batch tnn_batch;

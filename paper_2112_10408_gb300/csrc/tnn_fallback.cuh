@@ -344,6 +344,7 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_WARP_MINB)
             // ---- main: buckets backwards, keys within reach, by bound
             if (rs < rcover) {
                 float bpm_next = __ldg(G.bpm + bhi); // one bucket ahead
+                const float ext_max = __ldg(G.ext_max);
                 for (int b = bhi; b >= 0; --b) {
                     const float tau = key_d(wl.tauk);
                     const float bpm_b = bpm_next;
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_WARP_MINB)
                         bpm_next = __ldg(G.bpm + b - 1);
                     if (!(time_lb(c, s3, bpm_b) <= tau))
                         break;
-                    const float R = sqrtf(tau) * (1.0f + 0x1p-18f) + G.ext_max + c.delta;
+                    const float R = sqrtf(tau) * (1.0f + 0x1p-18f) + ext_max + c.delta;
                     const int cx0 = max((int)floorf(fmaxf((c.sx - R - G.x0) * G.inv_cell, -1.0f)) - 1, 0);
                     const int cx1 = min((int)floorf(fminf((c.sx + R - G.x0) * G.inv_cell, (float)G.nx)) + 1, G.nx - 1);
                     const int cy0 = max((int)floorf(fmaxf((c.sy - R - G.y0) * G.inv_cell, -1.0f)) - 1, 0);

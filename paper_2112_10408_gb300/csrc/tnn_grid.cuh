@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_GRID_MINB)
         const float by0 = warp_minf(active ? c.sy : INFINITY);
         const float by1 = warp_maxf(active ? c.sy : -INFINITY);
         const float dmax = warp_maxf(active ? c.delta : 0.0f);
+        const float ext_max = __ldg(G.ext_max);
         int bhi = -1;
         {
             const float fb = (tmax - G.t0) * G.inv_dt;
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_GRID_MINB)
             int cx0 = 0, cx1 = G.nx - 1, cy0 = 0, cy1 = G.ny - 1;
             if (tmx < INFINITY) {
                 // any key outside this reach has a bound above every key
-                const float R = sqrtf(tmx) * (1.0f + 0x1p-18f) + G.ext_max + dmax;
+                const float R = sqrtf(tmx) * (1.0f + 0x1p-18f) + ext_max + dmax;
                 cx0 = max((int)floorf(fmaxf((bx0 - R - G.x0) * G.inv_cell, -1.0f)) - 1, 0);
                 cx1 = min((int)floorf(fminf((bx1 + R - G.x0) * G.inv_cell, (float)G.nx)) + 1, G.nx - 1);
                 cy0 = max((int)floorf(fmaxf((by0 - R - G.y0) * G.inv_cell, -1.0f)) - 1, 0);

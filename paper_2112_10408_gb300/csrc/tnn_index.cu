@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "tnn_internal.cuh"
@@ -74,20 +75,20 @@ __global__ void k_validate_points(const float4 *__restrict__ p, int n,
         atomicMax(cmax_bits, __float_as_uint(m)); // m >= 0: bits are monotone
 }
 
-// Times non-decreasing inside each trajectory.
+// Times non-decreasing inside each trajectory (one warp per trajectory).
 __global__ void k_validate_order(const float4 *__restrict__ p,
                                  const int32_t *__restrict__ traj_off,
                                  int n_traj, unsigned int *flag)
 {
-    int tr = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tr = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (tr >= n_traj)
         return;
-    int b = traj_off[tr], e = traj_off[tr + 1];
-    for (int i = b + 1; i < e; ++i)
-        if (!(p[i].w >= p[i - 1].w)) {
-            atomicOr(flag, (unsigned)BAD_ORDER);
-            return;
-        }
+    const int b = traj_off[tr], e = traj_off[tr + 1];
+    bool bad = false;
+    for (int i = b + 1 + lane; i < e; i += 32)
+        bad |= !(p[i].w >= p[i - 1].w);
+    if (__any_sync(0xffffffffu, bad) && lane == 0)
+        atomicOr(flag, (unsigned)BAD_ORDER);
 }
 
 // One thread per segment (build order).  FP64 throughout, rounded once to
@@ -285,47 +286,46 @@ __global__ void k_gather_segments(const unsigned long long *__restrict__ keys,
     tA[i] = a.w;
 }
 
-// Running maximum of t_B over the t_A order (one block).
+// Running maximum of t_B over the t_A order (one block of 1024 threads;
+// thread t owns a contiguous run of ceil(S / 1024) segments).
 __global__ void k_prefix_max_tB(const float4 *__restrict__ seg, int S,
                                 float *__restrict__ pm)
 {
     __shared__ float wmax[32];
-    __shared__ float carry;
-    if (threadIdx.x == 0)
-        carry = -INFINITY;
-    __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int base = 0; base < S; base += 1024) {
-        int i = base + threadIdx.x;
-        float v = i < S ? seg[4 * i + 1].w : -INFINITY;
+    const int run = (S + 1023) / 1024;
+    const int b = min(S, threadIdx.x * run), e = min(S, b + run);
+    float v = -INFINITY;
+    for (int i = b; i < e; ++i)
+        v = fmaxf(v, seg[4 * i + 1].w);
+    // exclusive scan of the run maxima
+    float x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const float u = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o)
+            x = fmaxf(x, u);
+    }
+    if (lane == 31)
+        wmax[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        float y = wmax[lane];
         for (int o = 1; o < 32; o <<= 1) {
-            float u = __shfl_up_sync(0xffffffffu, v, o);
+            const float u = __shfl_up_sync(0xffffffffu, y, o);
             if (lane >= o)
-                v = fmaxf(v, u);
+                y = fmaxf(y, u);
         }
-        if (lane == 31)
-            wmax[w] = v;
-        __syncthreads();
-        if (w == 0) {
-            float x = wmax[lane];
-            for (int o = 1; o < 32; o <<= 1) {
-                float u = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o)
-                    x = fmaxf(x, u);
-            }
-            wmax[lane] = x;
-        }
-        __syncthreads();
-        float c = carry;
-        if (w > 0)
-            v = fmaxf(v, wmax[w - 1]);
-        v = fmaxf(v, c);
-        if (i < S)
-            pm[i] = v;
-        __syncthreads();
-        if (threadIdx.x == 1023)
-            carry = v;
-        __syncthreads();
+        wmax[lane] = y;
+    }
+    __syncthreads();
+    float carry = __shfl_up_sync(0xffffffffu, x, 1);
+    if (lane == 0)
+        carry = -INFINITY;
+    if (w > 0)
+        carry = fmaxf(carry, wmax[w - 1]);
+    for (int i = b; i < e; ++i) {
+        carry = fmaxf(carry, seg[4 * i + 1].w);
+        pm[i] = carry;
     }
 }
 
@@ -351,35 +351,55 @@ __device__ __forceinline__ float ord2f(uint32_t u)
 
 // Extremes of the segment midpoints (scaled x, y) and of t_A, and the sum of
 // the segment durations, for choosing the grid.
+// Warp-level minimum / maximum of ordered values, then one atomic per warp.
+__device__ __forceinline__ void warp_minmax_atomic(unsigned int lo, unsigned int hi,
+                                                   unsigned int *out_lo, unsigned int *out_hi)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(out_lo, lo);
+        atomicMax(out_hi, hi);
+    }
+}
+
 __global__ void k_seg_extremes(const float4 *__restrict__ seg, int S,
                                unsigned int *ext_ord, double *dur_sum)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S)
-        return;
-    const float4 a = seg[4 * s], u = seg[4 * s + 1], b = seg[4 * s + 2];
-    const float mx = fmaf(0.5f, b.x, a.x), my = fmaf(0.5f, b.y, a.y);
-    atomicMin(ext_ord + 0, f2ord(mx));
-    atomicMax(ext_ord + 1, f2ord(mx));
-    atomicMin(ext_ord + 2, f2ord(my));
-    atomicMax(ext_ord + 3, f2ord(my));
-    atomicMin(ext_ord + 4, f2ord(a.w));
-    atomicMax(ext_ord + 5, f2ord(a.w));
-    atomicAdd(dur_sum, (double)u.w - (double)a.w);
+    unsigned int o[6] = {0xffffffffu, 0u, 0xffffffffu, 0u, 0xffffffffu, 0u};
+    double dur = 0.0;
+    if (s < S) {
+        const float4 a = seg[4 * s], u = seg[4 * s + 1], b = seg[4 * s + 2];
+        const float mx = fmaf(0.5f, b.x, a.x), my = fmaf(0.5f, b.y, a.y);
+        o[0] = o[1] = f2ord(mx);
+        o[2] = o[3] = f2ord(my);
+        o[4] = o[5] = f2ord(a.w);
+        dur = (double)u.w - (double)a.w;
+    }
+    for (int d = 0; d < 3; ++d)
+        warp_minmax_atomic(o[2 * d], o[2 * d + 1], ext_ord + 2 * d, ext_ord + 2 * d + 1);
+    for (int k = 16; k > 0; k >>= 1)
+        dur += __shfl_xor_sync(0xffffffffu, dur, k);
+    if ((threadIdx.x & 31) == 0)
+        atomicAdd(dur_sum, dur);
 }
 
 // Bounding box of the raw points (x, y, z, t): ordered min/max per axis.
 __global__ void k_point_bbox(const float4 *__restrict__ p, int n, unsigned int *ord)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n)
-        return;
-    const float4 v = p[i];
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool in = i < n;
+    if (in)
+        v = p[i];
     const float c[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
-        atomicMin(ord + 2 * d, f2ord(c[d]));
-        atomicMax(ord + 2 * d + 1, f2ord(c[d]));
+        const unsigned int u = f2ord(c[d]);
+        warp_minmax_atomic(in ? u : 0xffffffffu, in ? u : 0u, ord + 2 * d, ord + 2 * d + 1);
     }
 }
 
@@ -487,6 +507,18 @@ __global__ void k_key_records(const int32_t *__restrict__ off, const float *__re
         kr[i] = make_int4(off[i], off[i + 1], __float_as_int(ext[i]), __float_as_int(tB[i]));
 }
 
+// Maximum of non-negative floats given as their bits (the bits order them).
+__global__ void k_max_bits(const unsigned int *__restrict__ v, int n, unsigned int *out)
+{
+    unsigned int m = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        m = max(m, v[i]);
+    for (int o = 16; o > 0; o >>= 1)
+        m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m)
+        atomicMax(out, m);
+}
+
 // Running maximum over buckets (one block).
 __global__ void k_prefix_max(float *__restrict__ v, int n)
 {
@@ -501,29 +533,31 @@ __global__ void k_prefix_max(float *__restrict__ v, int n)
 
 // ---------------------------------------------------------------- host API
 
+// The index may still be read by work queued on any stream: wait for the
+// device (as cudaFree would), then return the arrays to the pool.
 static void free_index(tnn_index *ix)
 {
     if (!ix)
         return;
-    cudaFree(ix->pts);
-    cudaFree(ix->seg);
-    cudaFree(ix->segTA);
-    cudaFree(ix->segPM);
-    cudaFree(ix->pts_t);
-    cudaFree(ix->idx_t);
-    cudaFree(ix->g_off);
-    cudaFree(ix->g_ids);
-    cudaFree(ix->g_seg);
-    cudaFree(ix->g_ext);
-    cudaFree(ix->g_tB);
-    cudaFree(ix->g_krec);
-    cudaFree(ix->g_bpm);
+    cudaDeviceSynchronize();
+    void *arrays[] = {ix->pts,   ix->seg,   ix->segTA, ix->segPM, ix->pts_t,
+                      ix->idx_t, ix->g_off, ix->g_ids, ix->g_seg, ix->g_ext,
+                      ix->g_tB,  ix->g_krec, ix->g_bpm, ix->g_ext_max};
+    for (void *p : arrays)
+        tnn_free(p, 0);
     delete ix;
 }
 
+// Build-time scratch, returned to the pool in stream order.
 struct DevBuf {
     void *p = nullptr;
-    ~DevBuf() { cudaFree(p); }
+    cudaStream_t st = 0;
+    cudaError_t alloc(size_t bytes, cudaStream_t s)
+    {
+        st = s;
+        return tnn_alloc(&p, bytes, s);
+    }
+    ~DevBuf() { tnn_free(p, st); }
 };
 
 static float host_ord2f(uint32_t u)
@@ -539,18 +573,19 @@ static float host_ord2f(uint32_t u)
 // cells are square, about two segments per (bucket, cell) on average, at most
 // 65,536 cells and 2^22 keys.
 static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
+                             const unsigned int *d_flag, unsigned int *h_flag,
                              cudaStream_t st)
 {
     const int S = (int)ix->S, tb = 256;
     DevBuf sb;
-    TNN_CUDA_TRY(cudaMalloc(&sb.p, 64));
+    TNN_CUDA_TRY(sb.alloc(64, st));
     unsigned int init[8] = {0xffffffffu, 0u, 0xffffffffu, 0u, 0xffffffffu, 0u, 0u, 0u};
     TNN_CUDA_TRY(cudaMemcpyAsync(sb.p, init, sizeof(init), cudaMemcpyHostToDevice, st));
     TNN_CUDA_TRY(cudaMemsetAsync((char *)sb.p + 32, 0, 8, st));
     k_seg_extremes<<<(S + tb - 1) / tb, tb, 0, st>>>(ix->seg, S, (unsigned int *)sb.p,
                                                     (double *)((char *)sb.p + 32));
     DevBuf bb;
-    TNN_CUDA_TRY(cudaMalloc(&bb.p, 32));
+    TNN_CUDA_TRY(bb.alloc(32, st));
     const unsigned int binit[8] = {0xffffffffu, 0u, 0xffffffffu, 0u, 0xffffffffu, 0u, 0xffffffffu, 0u};
     TNN_CUDA_TRY(cudaMemcpyAsync(bb.p, binit, sizeof(binit), cudaMemcpyHostToDevice, st));
     k_point_bbox<<<(int)((ix->n + tb - 1) / tb), tb, 0, st>>>(ix->pts, (int)ix->n, (unsigned int *)bb.p);
@@ -559,7 +594,19 @@ static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
     TNN_CUDA_TRY(cudaMemcpyAsync(h, sb.p, sizeof(h), cudaMemcpyDeviceToHost, st));
     TNN_CUDA_TRY(cudaMemcpyAsync(&dur, (char *)sb.p + 32, 8, cudaMemcpyDeviceToHost, st));
     TNN_CUDA_TRY(cudaMemcpyAsync(hb, bb.p, sizeof(hb), cudaMemcpyDeviceToHost, st));
+    // the validation flags, the largest coordinate and the largest radius
+    // are complete by now: the build's only synchronisation reads them too
+    TNN_CUDA_TRY(cudaMemcpyAsync(h_flag, d_flag, 3 * sizeof(unsigned int),
+                                 cudaMemcpyDeviceToHost, st));
     TNN_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h_flag[0] & BAD_VALUE) {
+        tnn_set_error("non-finite or too large (|v| > 1e15) coordinate in input");
+        return TNN_ERR_INVALID_ARG;
+    }
+    if (h_flag[0] & BAD_ORDER) {
+        tnn_set_error("times are not sorted inside a trajectory");
+        return TNN_ERR_INVALID_ARG;
+    }
     // bounding box of the points (orders the queries of the tensor-core
     // linear search)
     for (int d = 0; d < 4; ++d) {
@@ -601,13 +648,15 @@ static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
     g.ncell = nx * ny;
     g.nb = nb;
     const int nkeys = nb * g.ncell;
-    TNN_CUDA_TRY(cudaMalloc(&ix->g_off, sizeof(int32_t) * (nkeys + 1)));
-    TNN_CUDA_TRY(cudaMalloc(&ix->g_ids, sizeof(int32_t) * S));
-    TNN_CUDA_TRY(cudaMalloc(&ix->g_seg, sizeof(float4) * 4 * (size_t)S));
-    TNN_CUDA_TRY(cudaMalloc(&ix->g_ext, sizeof(float) * nkeys));
-    TNN_CUDA_TRY(cudaMalloc(&ix->g_tB, sizeof(float) * nkeys));
-    TNN_CUDA_TRY(cudaMalloc(&ix->g_bpm, sizeof(float) * nb));
-    TNN_CUDA_TRY(cudaMalloc(&ix->g_krec, sizeof(int4) * (size_t)nkeys));
+    TNN_CUDA_TRY(tnn_alloc((void **)&ix->g_off, sizeof(int32_t) * (nkeys + 1), st));
+    TNN_CUDA_TRY(tnn_alloc((void **)&ix->g_ids, sizeof(int32_t) * S, st));
+    TNN_CUDA_TRY(tnn_alloc((void **)&ix->g_seg, sizeof(float4) * 4 * (size_t)S, st));
+    TNN_CUDA_TRY(tnn_alloc((void **)&ix->g_ext, sizeof(float) * nkeys, st));
+    TNN_CUDA_TRY(tnn_alloc((void **)&ix->g_tB, sizeof(float) * nkeys, st));
+    TNN_CUDA_TRY(tnn_alloc((void **)&ix->g_bpm, sizeof(float) * nb, st));
+    TNN_CUDA_TRY(tnn_alloc((void **)&ix->g_krec, sizeof(int4) * (size_t)nkeys, st));
+    TNN_CUDA_TRY(tnn_alloc((void **)&ix->g_ext_max, sizeof(float), st));
+    TNN_CUDA_TRY(cudaMemsetAsync(ix->g_ext_max, 0, sizeof(float), st));
     TNN_CUDA_TRY(cudaMemsetAsync(ix->g_ext, 0, sizeof(float) * nkeys, st));
     TNN_CUDA_TRY(cudaMemsetAsync(ix->g_tB, 0, sizeof(float) * nkeys, st));
     TNN_CUDA_TRY(cudaMemsetAsync(ix->g_bpm, 0, sizeof(float) * nb, st));
@@ -625,15 +674,10 @@ static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
     k_prefix_max<<<1, 32, 0, st>>>(ix->g_bpm, nb);
     k_key_records<<<(nkeys + tb - 1) / tb, tb, 0, st>>>(ix->g_off, ix->g_ext, ix->g_tB, nkeys,
                                                        ix->g_krec);
+    // largest extent (for the search region), read back with the build's flags
+    k_max_bits<<<std::min((nkeys + tb - 1) / tb, 1024), tb, 0, st>>>(
+        (const unsigned int *)ix->g_ext, nkeys, (unsigned int *)ix->g_ext_max);
     TNN_CUDA_TRY(cudaGetLastError());
-    // largest extent (for the search region)
-    std::vector<float> hext(nkeys);
-    TNN_CUDA_TRY(cudaMemcpyAsync(hext.data(), ix->g_ext, sizeof(float) * nkeys,
-                                 cudaMemcpyDeviceToHost, st));
-    TNN_CUDA_TRY(cudaStreamSynchronize(st));
-    float emax = 0.f;
-    for (float v : hext)
-        emax = std::max(emax, v);
     GridDesc &G = ix->grid;
     G.x0 = g.x0;
     G.y0 = g.y0;
@@ -642,7 +686,7 @@ static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
     G.t0 = g.t0;
     G.dt = g.dt;
     G.inv_dt = g.inv_dt;
-    G.ext_max = emax;
+    G.ext_max = ix->g_ext_max;
     G.nx = nx;
     G.ny = ny;
     G.ncell = g.ncell;
@@ -708,25 +752,27 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
     for (int i = 0; i < 3; ++i)
         ix->ssq_f[i] = (float)sqrt(params->sigma[i]);
 
-    const int n2 = tnn_next_pow2_sort(n);
     const int s2 = tnn_next_pow2_sort(S);
     DevBuf toff_d, soff_d, rec_d, keys_d, flags_d;
     cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, bytes)                                                     \
     if (e == cudaSuccess)                                                     \
-        e = cudaMalloc((void **)&(ptr), (bytes));
+        e = tnn_alloc((void **)&(ptr), (bytes), st);
     ALLOC(ix->pts, sizeof(float4) * n);
     ALLOC(ix->seg, sizeof(float4) * 4 * S);
     ALLOC(ix->segTA, sizeof(float) * S);
     ALLOC(ix->segPM, sizeof(float) * S);
-    ALLOC(ix->pts_t, sizeof(float4) * n);
-    ALLOC(ix->idx_t, sizeof(int32_t) * (n + 4)); // 4 entries of padding for 16-byte copies
-    ALLOC(toff_d.p, sizeof(int32_t) * (n_traj + 1));
-    ALLOC(soff_d.p, sizeof(int32_t) * (n_traj + 1));
-    ALLOC(rec_d.p, sizeof(float4) * 4 * S);
-    ALLOC(keys_d.p, sizeof(unsigned long long) * (n2 > s2 ? n2 : s2));
-    ALLOC(flags_d.p, sizeof(unsigned int) * 4);
 #undef ALLOC
+    if (e == cudaSuccess)
+        e = toff_d.alloc(sizeof(int32_t) * (n_traj + 1), st);
+    if (e == cudaSuccess)
+        e = soff_d.alloc(sizeof(int32_t) * (n_traj + 1), st);
+    if (e == cudaSuccess)
+        e = rec_d.alloc(sizeof(float4) * 4 * S, st);
+    if (e == cudaSuccess)
+        e = keys_d.alloc(sizeof(unsigned long long) * s2, st);
+    if (e == cudaSuccess)
+        e = flags_d.alloc(sizeof(unsigned int) * 4, st);
     if (e != cudaSuccess) {
         free_index(ix);
         tnn_set_error("index allocation failed: %s", cudaGetErrorString(e));
@@ -752,7 +798,7 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
     const int ni = (int)n, Si = (int)S, Ti = (int)n_traj;
     k_validate_points<<<(ni + tb - 1) / tb, tb, 0, st>>>(
         ix->pts, ni, ix->ssq_f[0], ix->ssq_f[1], ix->ssq_f[2], flag, flag + 1);
-    k_validate_order<<<(Ti + tb - 1) / tb, tb, 0, st>>>(
+    k_validate_order<<<(int)(((int64_t)Ti * 32 + tb - 1) / tb), tb, 0, st>>>(
         ix->pts, (const int32_t *)toff_d.p, Ti, flag);
     k_segment_fit<<<(Si + tb - 1) / tb, tb, 0, st>>>(
         ix->pts, (const int32_t *)toff_d.p, (const int32_t *)soff_d.p, Ti, Si, K,
@@ -763,39 +809,21 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
     k_gather_segments<<<(Si + tb - 1) / tb, tb, 0, st>>>(keys, (const float4 *)rec_d.p,
                                                          Si, ix->seg, ix->segTA);
     k_prefix_max_tB<<<1, 1024, 0, st>>>(ix->seg, Si, ix->segPM);
+    unsigned int hflag[3] = {0, 0, 0};
     {
-        tnn_status gs = build_grid(ix, keys, s2, st);
+        tnn_status gs = build_grid(ix, keys, s2, flag, hflag, st);
         if (gs != TNN_OK) {
             free_index(ix);
             return gs;
         }
     }
-    k_time_keys<<<(n2 + tb - 1) / tb, tb, 0, st>>>(ix->pts, ni, keys, n2);
-    tnn_bitonic_sort(keys, n2, st);
-    k_gather_points<<<(ni + tb - 1) / tb, tb, 0, st>>>(keys, ix->pts, ni, ix->pts_t,
-                                                       ix->idx_t);
-    unsigned int hflag[4] = {0, 0, 0, 0};
+    // The rest of the build runs on after this call returns (stream order);
+    // a failure there surfaces at the next synchronising call.
     e = cudaGetLastError();
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(ix->idx_t + n, 0, 4 * sizeof(int32_t), st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(hflag, flag, sizeof(hflag), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess)
-        e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         free_index(ix);
         tnn_set_error("index build failed: %s", cudaGetErrorString(e));
         return TNN_ERR_CUDA;
-    }
-    if (hflag[0] & BAD_VALUE) {
-        free_index(ix);
-        tnn_set_error("non-finite or too large (|v| > 1e15) coordinate in input");
-        return TNN_ERR_INVALID_ARG;
-    }
-    if (hflag[0] & BAD_ORDER) {
-        free_index(ix);
-        tnn_set_error("times are not sorted inside a trajectory");
-        return TNN_ERR_INVALID_ARG;
     }
     memcpy(&ix->coord_max, &hflag[1], sizeof(float));
     memcpy(&ix->max_radius, &hflag[2], sizeof(float));
@@ -804,6 +832,47 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
 }
 
 extern "C" void tnn_index_destroy(tnn_index *index) { free_index(index); }
+
+static std::mutex g_time_order_mu;
+
+tnn_status tnn_index_time_order(const tnn_index *cix, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(g_time_order_mu);
+    tnn_index *ix = const_cast<tnn_index *>(cix);
+    if (ix->pts_t)
+        return TNN_OK;
+    const int n = (int)ix->n, n2 = tnn_next_pow2_sort(n), tb = 256;
+    float4 *pts_t = nullptr;
+    int32_t *idx_t = nullptr;
+    DevBuf keys_d;
+    cudaError_t e = tnn_alloc((void **)&pts_t, sizeof(float4) * n, st);
+    if (e == cudaSuccess)
+        e = tnn_alloc((void **)&idx_t, sizeof(int32_t) * (n + 4), st); // padding for 16-byte copies
+    if (e == cudaSuccess)
+        e = keys_d.alloc(sizeof(unsigned long long) * n2, st);
+    if (e != cudaSuccess) {
+        tnn_free(pts_t, st);
+        tnn_free(idx_t, st);
+        tnn_set_error("time-order allocation failed: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? TNN_ERR_OOM : TNN_ERR_CUDA;
+    }
+    unsigned long long *keys = (unsigned long long *)keys_d.p;
+    k_time_keys<<<(n2 + tb - 1) / tb, tb, 0, st>>>(ix->pts, n, keys, n2);
+    tnn_bitonic_sort(keys, n2, st);
+    k_gather_points<<<(n + tb - 1) / tb, tb, 0, st>>>(keys, ix->pts, n, pts_t, idx_t);
+    e = cudaMemsetAsync(idx_t + n, 0, 4 * sizeof(int32_t), st);
+    if (e == cudaSuccess)
+        e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        tnn_free(pts_t, st);
+        tnn_free(idx_t, st);
+        tnn_set_error("time order failed: %s", cudaGetErrorString(e));
+        return TNN_ERR_CUDA;
+    }
+    ix->pts_t = pts_t;
+    ix->idx_t = idx_t;
+    return TNN_OK;
+}
 
 extern "C" tnn_status tnn_index_get_info(const tnn_index *ix, tnn_index_info *out)
 {

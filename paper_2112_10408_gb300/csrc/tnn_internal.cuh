@@ -44,7 +44,7 @@ struct GridDesc {
     float x0, y0;       // scaled-space corner of cell (0, 0)
     float cell, inv_cell;
     float t0, dt, inv_dt; // bucket b covers t_A in [t0 + b dt, t0 + (b+1) dt)
-    float ext_max;      // largest extent over the keys
+    const float *ext_max; // [1] device: largest extent over the keys
     int32_t nx, ny, ncell, nb;
     const int32_t *off; // [nb * ncell + 1]
     const int32_t *ids; // [S] segment positions (t_A order) grouped by key
@@ -72,13 +72,15 @@ struct tnn_index {
     float4 *seg;     // [S][4] records ordered by t_A (see tnn_index_export)
     float *segTA;    // [S] t_A in that order
     float *segPM;    // [S] running max of t_B in that order
-    float4 *pts_t;   // [n] points ordered by (t, index)  (linear search)
-    int32_t *idx_t;  // [n] their input index
+    float4 *pts_t;   // [n] points ordered by (t, index) (linear search; built
+                     // by tnn_index_time_order on first use)
+    int32_t *idx_t;  // [n + 4] their input index (4 entries of padding)
     GridDesc grid;   // views of the arrays below
     int32_t *g_off, *g_ids;
     float4 *g_seg;
     float *g_ext, *g_tB, *g_bpm;
     int4 *g_krec;
+    float *g_ext_max; // [1]
     float bb_lo[4], bb_hi[4]; // bounding box of the points (x, y, z, t)
 };
 
@@ -148,6 +150,15 @@ struct KnnLaunch {
 // (tnn_index.cu); tnn_next_pow2_sort gives the n2 for n keys.
 int tnn_next_pow2_sort(int64_t n);
 void tnn_bitonic_sort(unsigned long long *keys, int n2, cudaStream_t st);
+
+// Stream-ordered device memory from the library's pool (tnn_memory.cu):
+// no device synchronisation, memory kept reserved between calls.
+cudaError_t tnn_alloc(void **p, size_t bytes, cudaStream_t st);
+void tnn_free(void *p, cudaStream_t st);
+
+// Points in (t, index) order for the linear search, built on first use
+// (stream-ordered on `st`).
+tnn_status tnn_index_time_order(const tnn_index *ix, cudaStream_t st);
 
 // Launch helpers (tnn_knn.cu).
 tnn_status tnn_fill_window(const tnn_index *ix, const float *d_q, int64_t m,

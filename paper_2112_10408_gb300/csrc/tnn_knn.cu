@@ -285,7 +285,7 @@ tnn_status tnn_launch_search(const KnnLaunch &L, bool brute, cudaStream_t st)
         unsigned long long *keys = nullptr;
         if (L.w0.m <= (1ll << 29)) {
             const int n2 = tnn_next_pow2_sort(L.w0.m);
-            TNN_CUDA_TRY(cudaMallocAsync((void **)&keys, (size_t)n2 * 8, st));
+            TNN_CUDA_TRY(tnn_alloc((void **)&keys, (size_t)n2 * 8, st));
             const float *lo = L.w0.bb_lo, *hi = L.w0.bb_hi;
             float4 l4 = make_float4(lo[0], lo[1], lo[2], lo[3]), s4;
             s4.x = hi[0] > lo[0] ? 1024.0f / (hi[0] - lo[0]) : 0.0f;
@@ -300,7 +300,7 @@ tnn_status tnn_launch_search(const KnnLaunch &L, bool brute, cudaStream_t st)
         k_linear_tc<<<(unsigned)grid, TC_THREADS, smem, st>>>(Lt);
         const cudaError_t le = cudaGetLastError();
         if (keys)
-            cudaFreeAsync(keys, st);
+            tnn_free(keys, st);
         TNN_CUDA_TRY(le);
         return finish_search(L, st, prof, pr);
     }
@@ -339,6 +339,11 @@ static tnn_status run_single(const tnn_index *ix, const float *d_q, int64_t m,
                              tnn_stats *h_stats, tnn_stream_t stream, bool brute)
 {
     tnn_clear_error();
+    if (brute && ix) {
+        tnn_status ts = tnn_index_time_order(ix, (cudaStream_t)stream);
+        if (ts != TNN_OK)
+            return ts;
+    }
     KnnLaunch L;
     memset(&L, 0, sizeof(L));
     tnn_status s = tnn_fill_window(ix, d_q, m, p, d_idx, d_d2, &L.w0);
@@ -357,14 +362,14 @@ static tnn_status run_single(const tnn_index *ix, const float *d_q, int64_t m,
     L.fb_cap = m;
     const size_t hdr = 256;
     void *buf = nullptr;
-    TNN_CUDA_TRY(cudaMallocAsync(&buf, hdr + (2 * sizeof(int2) + sizeof(float)) * (size_t)m, st));
+    TNN_CUDA_TRY(tnn_alloc(&buf, hdr + (2 * sizeof(int2) + sizeof(float)) * (size_t)m, st));
     L.scr = (KnnScratch *)buf;
     L.fb_list = (int2 *)((char *)buf + hdr);
     L.fb_list3 = L.fb_list + m;
     L.fb_tau = (float *)(L.fb_list3 + m);
     cudaError_t e = cudaMemsetAsync(buf, 0, sizeof(KnnScratch), st);
     if (e != cudaSuccess) {
-        cudaFreeAsync(buf, st);
+        tnn_free(buf, st);
         TNN_CUDA_TRY(e);
     }
     s = tnn_launch_search(L, brute, st);
@@ -393,7 +398,7 @@ static tnn_status run_single(const tnn_index *ix, const float *d_q, int64_t m,
             }
         }
     }
-    cudaFreeAsync(buf, st);
+    tnn_free(buf, st);
     return s;
 }
 
@@ -721,7 +726,7 @@ __global__ void k_knn_work(const __grid_constant__ KnnWin W, const float *__rest
         for (int b = bhi; b >= 0; --b) {
             if (!(time_lb(c, W.sig[3], G.bpm[b]) <= dk))
                 break;
-            const float R = sqrtf(dk) * (1.0f + 0x1p-18f) + G.ext_max + c.delta;
+            const float R = sqrtf(dk) * (1.0f + 0x1p-18f) + __ldg(G.ext_max) + c.delta;
             const int cx0 = max((int)floorf(fmaxf((c.sx - R - G.x0) * G.inv_cell, -1.0f)) - 1, 0);
             const int cx1 = min((int)floorf(fminf((c.sx + R - G.x0) * G.inv_cell, (float)G.nx)) + 1, G.nx - 1);
             const int cy0 = max((int)floorf(fmaxf((c.sy - R - G.y0) * G.inv_cell, -1.0f)) - 1, 0);
@@ -778,7 +783,7 @@ extern "C" tnn_status tnn_knn_work(const tnn_index *index, const float *d_q, int
     TNN_ARG_CHECK(d_d2 != nullptr, "d_d2 is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     unsigned long long *buf = nullptr;
-    TNN_CUDA_TRY(cudaMallocAsync((void **)&buf, 24, st));
+    TNN_CUDA_TRY(tnn_alloc((void **)&buf, 24, st));
     cudaError_t e = cudaMemsetAsync(buf, 0, 24, st);
     if (e == cudaSuccess) {
         k_knn_work<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(w, d_d2, k, buf);
@@ -787,7 +792,7 @@ extern "C" tnn_status tnn_knn_work(const tnn_index *index, const float *d_q, int
     unsigned long long h[3] = {0, 0, 0};
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h, buf, 24, cudaMemcpyDeviceToHost, st);
-    cudaFreeAsync(buf, st);
+    tnn_free(buf, st);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(st);
     TNN_CUDA_TRY(e);

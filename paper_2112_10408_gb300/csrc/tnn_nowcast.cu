@@ -649,10 +649,10 @@ extern "C" tnn_status tnn_nowcast(const tnn_index *ix, const float *d_wind,
     int32_t *idx = nullptr;
     float *d2 = nullptr;
     uint16_t *feat = nullptr;
-    TNN_CUDA_TRY(cudaMallocAsync((void **)&idx, sizeof(int32_t) * m * k, st));
-    cudaError_t e = cudaMallocAsync((void **)&d2, sizeof(float) * m * k, st);
+    TNN_CUDA_TRY(tnn_alloc((void **)&idx, sizeof(int32_t) * m * k, st));
+    cudaError_t e = tnn_alloc((void **)&d2, sizeof(float) * m * k, st);
     if (e == cudaSuccess && mlp)
-        e = cudaMallocAsync((void **)&feat, sizeof(uint16_t) * m * k * TNN_N_FEAT, st);
+        e = tnn_alloc((void **)&feat, sizeof(uint16_t) * m * k * TNN_N_FEAT, st);
     tnn_status s = TNN_OK;
     if (e != cudaSuccess) {
         tnn_set_error("nowcast allocation failed: %s", cudaGetErrorString(e));
@@ -665,10 +665,10 @@ extern "C" tnn_status tnn_nowcast(const tnn_index *ix, const float *d_wind,
                                  feat, mlp ? nullptr : d_uv, stream);
     if (s == TNN_OK && mlp)
         s = tnn_mlp_forward(mlp, feat, m, d_uv, stream);
-    cudaFreeAsync(idx, st);
+    tnn_free(idx, st);
     if (d2)
-        cudaFreeAsync(d2, st);
+        tnn_free(d2, st);
     if (feat)
-        cudaFreeAsync(feat, st);
+        tnn_free(feat, st);
     return s;
 }

@@ -81,6 +81,8 @@ _SIGNATURES = [
     ("tnn_knn_work", c_i32, [c_p, c_p, c_i64, c_i32, c_f64, c_p, c_p, c_p]),
     ("tnn_profile_enable", c_i32, [c_i32]),
     ("tnn_profile_read", c_i32, [ctypes.POINTER(c_f64), ctypes.POINTER(c_i64), c_i32]),
+    ("tnn_memory_trim", c_i32, [c_i64]),
+    ("tnn_memory_reserved", c_i32, [ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
     ("tnn_batch_create", c_i32, [ctypes.POINTER(c_p), ctypes.POINTER(c_p), ctypes.POINTER(c_i64),
                                  ctypes.POINTER(tnn_knn_params), c_i32, ctypes.POINTER(c_p),
                                  ctypes.POINTER(c_p), ctypes.POINTER(c_p)]),
@@ -303,6 +305,18 @@ def tnn_knn_work(index: Index, k: int, d2: torch.Tensor, lag: float = 0.0, q=Non
     _check(_L().tnn_knn_work(index.handle, _ptr(q), m, int(k), float(lag), _ptr(d2), out,
                              _stream()))
     return int(out[0]), int(out[1]), int(out[2])
+
+
+def tnn_memory_trim(keep_bytes: int = 0):
+    """Release the library pool's reserved device memory down to keep_bytes."""
+    _check(_L().tnn_memory_trim(int(keep_bytes)))
+
+
+def tnn_memory_reserved():
+    """(reserved, in use) bytes of the library's device memory pool."""
+    r, u = c_i64(0), c_i64(0)
+    _check(_L().tnn_memory_reserved(ctypes.byref(r), ctypes.byref(u)))
+    return r.value, u.value
 
 
 def tnn_profile_enable(on: bool = True):
