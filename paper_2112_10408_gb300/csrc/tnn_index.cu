@@ -91,7 +91,7 @@ __global__ void k_validate_order(const float4 *__restrict__ p,
         atomicOr(flag, (unsigned)BAD_ORDER);
 }
 
-// One thread per segment (build order).  FP64 throughout, rounded once to
+// Four lanes per segment (build order).  FP64 throughout, rounded once to
 // the stored FP32 record:
 //   A' = fl(sqrt(s) A),  AB' = fl(sqrt(s) B - A'),  U' = fl(AB' / |AB'|^2)
 // The stored segment is [A', A' + AB'] (both exactly representable);
@@ -105,9 +105,12 @@ __global__ void k_segment_fit(const float4 *__restrict__ p,
                               unsigned long long *__restrict__ keys,
                               unsigned int *rmax_bits)
 {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S)
-        return;
+    // four lanes per segment, splitting its members (FP64 is scarce: the
+    // per-segment set-up is repeated by each of the four)
+    const int s_raw = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2);
+    const int sub = threadIdx.x & 3;
+    const bool valid = s_raw < S;
+    const int s = valid ? s_raw : S - 1;
     // trajectory of segment s: largest tr with seg_off[tr] <= s
     int lo = 0, hi = n_traj; // seg_off[lo] <= s < seg_off[hi]
     while (hi - lo > 1) {
@@ -133,11 +136,9 @@ __global__ void k_segment_fit(const float4 *__restrict__ p,
         E[i] = A[i] + AB[i];
     }
     double ab2 = AB[0] * AB[0] + AB[1] * AB[1] + AB[2] * AB[2];
-    for (int i = 0; i < 3; ++i)
-        Uf[i] = ab2 > 1e-30 ? (float)(AB[i] / ab2) : 0.f;
     double r2 = 0.0, mag = fabs(A[0]) + fabs(A[1]) + fabs(A[2]) +
                           fabs(E[0]) + fabs(E[1]) + fabs(E[2]);
-    for (int j = 0; j < count; ++j) {
+    for (int j = sub; j < (valid ? count : 0); j += 4) {
         float4 v = p[first + j];
         double P[3] = {qq[0] * (double)v.x, qq[1] * (double)v.y, qq[2] * (double)v.z};
         double lam = 0.0;
@@ -154,6 +155,14 @@ __global__ void k_segment_fit(const float4 *__restrict__ p,
         r2 = fmax(r2, d2);
         mag = fmax(mag, fabs(P[0]) + fabs(P[1]) + fabs(P[2]));
     }
+    for (int o = 1; o < 4; o <<= 1) {
+        r2 = fmax(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+        mag = fmax(mag, __shfl_xor_sync(0xffffffffu, mag, o));
+    }
+    if (!valid || sub != 0)
+        return;
+    for (int i = 0; i < 3; ++i)
+        Uf[i] = ab2 > 1e-30 ? (float)(AB[i] / ab2) : 0.f;
     // FP64 rounding of the distances above is far below 1e-12 * mag.
     double r = sqrt(r2) + 1e-12 * (1.0 + mag);
     float rf = __double2float_ru(r);
@@ -286,47 +295,68 @@ __global__ void k_gather_segments(const unsigned long long *__restrict__ keys,
     tA[i] = a.w;
 }
 
-// Running maximum of t_B over the t_A order (one block of 1024 threads;
-// thread t owns a contiguous run of ceil(S / 1024) segments).
-__global__ void k_prefix_max_tB(const float4 *__restrict__ seg, int S,
-                                float *__restrict__ pm)
+// Running maximum of t_B over the t_A order, in two passes over blocks of
+// 1024 segments: the maximum of every block, then per block the maxima of
+// the blocks before it and a block-wide inclusive scan.
+__device__ __forceinline__ float block_max_1024(float v, float *sh)
 {
-    __shared__ float wmax[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int run = (S + 1023) / 1024;
-    const int b = min(S, threadIdx.x * run), e = min(S, b + run);
-    float v = -INFINITY;
-    for (int i = b; i < e; ++i)
-        v = fmaxf(v, seg[4 * i + 1].w);
-    // exclusive scan of the run maxima
-    float x = v;
+    for (int o = 16; o > 0; o >>= 1)
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0)
+        sh[w] = v;
+    __syncthreads();
+    v = sh[lane];
+    for (int o = 16; o > 0; o >>= 1)
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    return v;
+}
+
+__global__ void __launch_bounds__(1024) k_pm_block_max(const float4 *__restrict__ seg, int S,
+                                                       float *__restrict__ bmax)
+{
+    __shared__ float sh[32];
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    const float v = block_max_1024(i < S ? seg[4 * i + 1].w : -INFINITY, sh);
+    if (threadIdx.x == 0)
+        bmax[blockIdx.x] = v;
+}
+
+__global__ void __launch_bounds__(1024) k_pm_apply(const float4 *__restrict__ seg, int S,
+                                                   const float *__restrict__ bmax,
+                                                   float *__restrict__ pm)
+{
+    __shared__ float sh[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float c = -INFINITY;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += 1024)
+        c = fmaxf(c, bmax[b]);
+    const float carry = block_max_1024(c, sh);
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    float v = i < S ? seg[4 * i + 1].w : -INFINITY;
     for (int o = 1; o < 32; o <<= 1) {
-        const float u = __shfl_up_sync(0xffffffffu, x, o);
+        const float u = __shfl_up_sync(0xffffffffu, v, o);
         if (lane >= o)
-            x = fmaxf(x, u);
+            v = fmaxf(v, u);
     }
     if (lane == 31)
-        wmax[w] = x;
+        sh[w] = v;
     __syncthreads();
     if (w == 0) {
-        float y = wmax[lane];
+        float y = sh[lane];
         for (int o = 1; o < 32; o <<= 1) {
             const float u = __shfl_up_sync(0xffffffffu, y, o);
             if (lane >= o)
                 y = fmaxf(y, u);
         }
-        wmax[lane] = y;
+        sh[lane] = y;
     }
     __syncthreads();
-    float carry = __shfl_up_sync(0xffffffffu, x, 1);
-    if (lane == 0)
-        carry = -INFINITY;
     if (w > 0)
-        carry = fmaxf(carry, wmax[w - 1]);
-    for (int i = b; i < e; ++i) {
-        carry = fmaxf(carry, seg[4 * i + 1].w);
-        pm[i] = carry;
-    }
+        v = fmaxf(v, sh[w - 1]);
+    if (i < S)
+        pm[i] = fmaxf(v, carry);
 }
 
 __global__ void k_gather_points(const unsigned long long *__restrict__ keys,
@@ -387,19 +417,42 @@ __global__ void k_seg_extremes(const float4 *__restrict__ seg, int S,
         atomicAdd(dur_sum, dur);
 }
 
-// Bounding box of the raw points (x, y, z, t): ordered min/max per axis.
+// Bounding box of the raw points (x, y, z, t): ordered min/max per axis,
+// reduced over the block (grid-stride) before one atomic per value.
 __global__ void k_point_bbox(const float4 *__restrict__ p, int n, unsigned int *ord)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    const bool in = i < n;
-    if (in)
-        v = p[i];
-    const float c[4] = {v.x, v.y, v.z, v.w};
+    __shared__ unsigned int s[32][8];
+    unsigned int m[8] = {0xffffffffu, 0u, 0xffffffffu, 0u, 0xffffffffu, 0u, 0xffffffffu, 0u};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 v = p[i];
+        const float c[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int d = 0; d < 4; ++d) {
-        const unsigned int u = f2ord(c[d]);
-        warp_minmax_atomic(in ? u : 0xffffffffu, in ? u : 0u, ord + 2 * d, ord + 2 * d + 1);
+        for (int d = 0; d < 4; ++d) {
+            const unsigned int u = f2ord(c[d]);
+            m[2 * d] = min(m[2 * d], u);
+            m[2 * d + 1] = max(m[2 * d + 1], u);
+        }
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int d = 0; d < 8; ++d)
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned int x = __shfl_xor_sync(0xffffffffu, m[d], o);
+            m[d] = (d & 1) ? max(m[d], x) : min(m[d], x);
+        }
+    if (lane == 0)
+        for (int d = 0; d < 8; ++d)
+            s[w][d] = m[d];
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int d = threadIdx.x;
+        unsigned int r = s[0][d];
+        for (int j = 1; j < nw; ++j)
+            r = (d & 1) ? max(r, s[j][d]) : min(r, s[j][d]);
+        if (d & 1)
+            atomicMax(ord + d, r);
+        else
+            atomicMin(ord + d, r);
     }
 }
 
@@ -588,7 +641,8 @@ static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
     TNN_CUDA_TRY(bb.alloc(32, st));
     const unsigned int binit[8] = {0xffffffffu, 0u, 0xffffffffu, 0u, 0xffffffffu, 0u, 0xffffffffu, 0u};
     TNN_CUDA_TRY(cudaMemcpyAsync(bb.p, binit, sizeof(binit), cudaMemcpyHostToDevice, st));
-    k_point_bbox<<<(int)((ix->n + tb - 1) / tb), tb, 0, st>>>(ix->pts, (int)ix->n, (unsigned int *)bb.p);
+    k_point_bbox<<<(int)std::min<int64_t>((ix->n + tb - 1) / tb, 608), tb, 0, st>>>(
+        ix->pts, (int)ix->n, (unsigned int *)bb.p);
     unsigned int h[8], hb[8];
     double dur = 0.0;
     TNN_CUDA_TRY(cudaMemcpyAsync(h, sb.p, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -800,7 +854,7 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
         ix->pts, ni, ix->ssq_f[0], ix->ssq_f[1], ix->ssq_f[2], flag, flag + 1);
     k_validate_order<<<(int)(((int64_t)Ti * 32 + tb - 1) / tb), tb, 0, st>>>(
         ix->pts, (const int32_t *)toff_d.p, Ti, flag);
-    k_segment_fit<<<(Si + tb - 1) / tb, tb, 0, st>>>(
+    k_segment_fit<<<(int)(((int64_t)Si * 4 + tb - 1) / tb), tb, 0, st>>>(
         ix->pts, (const int32_t *)toff_d.p, (const int32_t *)soff_d.p, Ti, Si, K,
         sqrt(params->sigma[0]), sqrt(params->sigma[1]), sqrt(params->sigma[2]),
         (float4 *)rec_d.p, keys, flag + 2);
@@ -808,7 +862,12 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
     tnn_bitonic_sort(keys, s2, st);
     k_gather_segments<<<(Si + tb - 1) / tb, tb, 0, st>>>(keys, (const float4 *)rec_d.p,
                                                          Si, ix->seg, ix->segTA);
-    k_prefix_max_tB<<<1, 1024, 0, st>>>(ix->seg, Si, ix->segPM);
+    {
+        const int nblk = (Si + 1023) / 1024;
+        float *bmax = (float *)((char *)rec_d.p); // the unsorted records are no longer read
+        k_pm_block_max<<<nblk, 1024, 0, st>>>(ix->seg, Si, bmax);
+        k_pm_apply<<<nblk, 1024, 0, st>>>(ix->seg, Si, bmax, ix->segPM);
+    }
     unsigned int hflag[3] = {0, 0, 0};
     {
         tnn_status gs = build_grid(ix, keys, s2, flag, hflag, st);
