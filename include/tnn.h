@@ -260,6 +260,29 @@ tnn_status tnn_knn_work(const tnn_index *index, const float *d_q, int64_t m,
 tnn_status tnn_profile_enable(int32_t on);
 tnn_status tnn_profile_read(double *ms, int64_t *launches, int32_t reset);
 
+/* -------------------------------------------------------- host pipeline */
+
+/*
+ * The whole pipeline on host buffers: the points of Sec. 3.5's batch are
+ * copied in, indexed (as tnn_build_segments with *bp) and every point is
+ * answered as its own query (as tnn_knn with d_q = NULL and *kp); the
+ * neighbour lists land in host memory.  The queries are answered in `chunks`
+ * consecutive slices of rows (0 = the library's choice, 2; at most 64): a
+ * second stream copies a slice's lists out while the search works on the
+ * next slice.
+ *   h_xyzt [n][4] float, h_traj_off [n_traj + 1]: as tnn_build_segments,
+ *     host memory (page-locked memory is copied faster).
+ *   h_idx [n][k] int32, h_d2 [n][k] float: host outputs, layout as tnn_knn.
+ * Device memory: 16 n + 8 n k bytes of scratch and the index, from the
+ * library pool; all of it is returned before the call ends.  Synchronous:
+ * returns when the outputs are complete.  Errors as tnn_build_segments and
+ * tnn_knn; on an error the outputs are undefined.
+ */
+tnn_status tnn_knn_host(const float *h_xyzt, int64_t n, const int64_t *h_traj_off,
+                        int64_t n_traj, const tnn_build_params *bp,
+                        const tnn_knn_params *kp, int32_t chunks, int32_t *h_idx,
+                        float *h_d2, tnn_stream_t stream);
+
 /* ----------------------------------------------------------------- memory */
 
 /*

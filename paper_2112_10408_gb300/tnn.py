@@ -81,6 +81,8 @@ _SIGNATURES = [
     ("tnn_knn_work", c_i32, [c_p, c_p, c_i64, c_i32, c_f64, c_p, c_p, c_p]),
     ("tnn_profile_enable", c_i32, [c_i32]),
     ("tnn_profile_read", c_i32, [ctypes.POINTER(c_f64), ctypes.POINTER(c_i64), c_i32]),
+    ("tnn_knn_host", c_i32, [c_p, c_i64, c_p, c_i64, ctypes.POINTER(tnn_build_params),
+                             ctypes.POINTER(tnn_knn_params), c_i32, c_p, c_p, c_p]),
     ("tnn_memory_trim", c_i32, [c_i64]),
     ("tnn_memory_reserved", c_i32, [ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
     ("tnn_batch_create", c_i32, [ctypes.POINTER(c_p), ctypes.POINTER(c_p), ctypes.POINTER(c_i64),
@@ -305,6 +307,46 @@ def tnn_knn_work(index: Index, k: int, d2: torch.Tensor, lag: float = 0.0, q=Non
     _check(_L().tnn_knn_work(index.handle, _ptr(q), m, int(k), float(lag), _ptr(d2), out,
                              _stream()))
     return int(out[0]), int(out[1]), int(out[2])
+
+
+def _host(t, dtype, shape_tail, name):
+    if isinstance(t, np.ndarray):
+        t = torch.from_numpy(t)
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a host array")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape[1:]) != tuple(shape_tail) or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous [*, {', '.join(map(str, shape_tail))}] array")
+    return t
+
+
+def tnn_knn_host(xyzt, traj_off, sigma, seg_len: int, k: int, lag: float = 0.0, chunks: int = 0,
+                 out=None, **kw):
+    """The whole pipeline on host buffers (C ABI tnn_knn_host): points in,
+    index, every point's causal k-NN, neighbour lists out.  ``xyzt`` is a
+    host float32 [n, 4] array (numpy or CPU tensor; page-locked tensors copy
+    faster); returns host (idx int32 [n, k], d2 float32 [n, k]), written
+    into ``out`` when given."""
+    x = _host(xyzt, torch.float32, (4,), "xyzt")
+    n = x.shape[0]
+    off = np.ascontiguousarray(np.asarray(traj_off, dtype=np.int64))
+    bp = tnn_build_params()
+    for i in range(4):
+        bp.sigma[i] = float(sigma[i])
+    bp.seg_len = int(seg_len)
+    kp = make_knn_params(k, lag, **kw)
+    if out is None:
+        idx = torch.empty((n, k), dtype=torch.int32)
+        d2 = torch.empty((n, k), dtype=torch.float32)
+    else:
+        idx = _host(out[0], torch.int32, (k,), "idx")
+        d2 = _host(out[1], torch.float32, (k,), "d2")
+        if idx.shape[0] != n or d2.shape[0] != n:
+            raise ValueError("outputs must have n rows")
+    _check(_L().tnn_knn_host(_ptr(x), n, off.ctypes.data_as(c_p), off.shape[0] - 1, ctypes.byref(bp),
+                             ctypes.byref(kp), int(chunks), _ptr(idx), _ptr(d2), _stream()))
+    return idx, d2
 
 
 def tnn_memory_trim(keep_bytes: int = 0):

@@ -37,3 +37,20 @@ def test_pool_reuse_and_trim():
     ix.destroy()
     with pytest.raises(Exception):
         tnn.tnn_memory_trim(-1)
+
+
+@pytest.mark.parametrize("chunks", [0, 1, 3])
+def test_host_pipeline_matches_device_path(chunks):
+    """tnn_knn_host (host buffers in and out, sliced search with overlapped
+    copies) gives exactly the device path's lists."""
+    tnn.load_library()
+    wl = synth.flights(200, 50, synth.SEED_TINY)
+    x = torch.from_numpy(wl.xyzt).cuda()
+    ix = tnn.tnn_build_segments(x, wl.traj_off, synth.SIGMA_DEFAULT, 10)
+    idx_d, d2_d = tnn.tnn_knn(ix, 8, 0.0)
+    ix.destroy()
+    h_x = torch.from_numpy(wl.xyzt).pin_memory() if chunks == 3 else wl.xyzt
+    idx_h, d2_h = tnn.tnn_knn_host(h_x, wl.traj_off, synth.SIGMA_DEFAULT, 10, 8, 0.0, chunks=chunks)
+    assert not idx_h.is_cuda
+    assert torch.equal(idx_h, idx_d.cpu())
+    assert torch.equal(d2_h, d2_d.cpu())
