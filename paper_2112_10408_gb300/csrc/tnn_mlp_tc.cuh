@@ -478,3 +478,221 @@ __global__ void __launch_bounds__(MLP_ROWS, 1) k_mlp_dw1_tc(const __grid_constan
     if (!ok && t == 0)
         atomicOr(a.err, 1);
 }
+
+// k_mlp_infer_tc — inference (no targets), one persistent CTA per SM over
+// 128-row tiles, warp-specialised so that loading, the tensor cores and the
+// epilogue of different tiles overlap:
+//   warps 0-3   load the X tile of the next row block (one row per thread,
+//               written in the core-matrix order) into one of two buffers;
+//   warp 20     (one thread) issues the MMAs of a tile, all K steps at once
+//               (W1^T stays in shared memory for the whole kernel), into one
+//               of two TMEM accumulators;
+//   warps 4-19  (four per TMEM lane quadrant, a quarter of the hidden units
+//               each) read an accumulator, H = bf16(GELU(Z + b1)), the head.
+// Barriers: x_full / x_empty per X buffer, acc_full / acc_empty per
+// accumulator; every wait is bounded (TC_WAIT_NS) and a failed wait ends the
+// kernel with a.err set.
+#define MLP_INF_LOADERS 128
+#define MLP_INF_EPI 512
+#define MLP_INF_THREADS (MLP_INF_LOADERS + MLP_INF_EPI + 32)
+
+__host__ __device__ inline size_t mlp_infer_smem(int d_in, int dh)
+{
+    const size_t nk = (size_t)d_in / 16;
+    // W1^T + 2 X buffers + b1, W2 + head partials [2][4][128][2] + barriers
+    return nk * (size_t)dh * 32 + 2 * nk * 4096 + (size_t)dh * 12 + 2 * 4 * 128 * 2 * 4 + 256;
+}
+
+__device__ __forceinline__ bool epi_any(bool v)
+{
+    uint32_t r;
+    asm volatile("{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}"
+                 : "=r"(r)
+                 : "r"((uint32_t)v), "n"(MLP_INF_EPI)
+                 : "memory");
+    return r != 0;
+}
+
+__global__ void __launch_bounds__(MLP_INF_THREADS, 1) k_mlp_infer_tc(const __grid_constant__ MlpFwdArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int dh = a.dh, nk = a.d_in / 16;
+    const size_t wbytes = (size_t)nk * dh * 32, xbytes = (size_t)nk * 4096;
+    unsigned char *sW = smem;
+    unsigned char *sX = smem + wbytes; // [2][xbytes]
+    float *s_b1 = (float *)(sX + 2 * xbytes);
+    float *s_W2 = s_b1 + dh;
+    float2 *s_y = (float2 *)(s_W2 + 2 * dh); // [2 buffers][4 quarters][128 rows]
+    unsigned long long *bars = (unsigned long long *)(s_y + 2 * 4 * 128);
+    uint32_t *tmem_slot = (uint32_t *)(bars + 10);
+    volatile int *s_err = (volatile int *)(tmem_slot + 1);
+    const uint32_t b_w = su32(bars), b_xf = su32(bars + 1), b_xe = su32(bars + 3);
+    const uint32_t b_af = su32(bars + 5), b_ae = su32(bars + 7);
+    const long long ntiles = (a.B + MLP_ROWS - 1) / MLP_ROWS;
+
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_w));
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b_xf + 8u * b), "n"(MLP_INF_LOADERS));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_xe + 8u * b));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_af + 8u * b));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b_ae + 8u * b), "n"(MLP_INF_EPI));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *s_err = 0;
+        // W1^T, one bulk copy per K step, all on one barrier
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b_w), "r"((uint32_t)wbytes)
+                     : "memory");
+        for (int s = 0; s < nk; ++s)
+            tma_copy_1d(su32(sW + (size_t)s * dh * 32), a.w1t + (size_t)s * dh * 16, (uint32_t)dh * 32, b_w);
+    }
+    for (int i = t; i < dh; i += MLP_INF_THREADS) {
+        s_b1[i] = a.b1[i];
+        s_W2[2 * i] = a.W2[2 * i];
+        s_W2[2 * i + 1] = a.W2[2 * i + 1];
+    }
+    const uint32_t cols = a.tmem_cols; // >= 2 dh
+    if (warp == 20) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(su32(tmem_slot)), "r"(cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    bool w_seen = false;
+
+    if (t < MLP_INF_LOADERS) {
+        // ---- loaders: row t of each tile
+        for (long long j = 0;; ++j) {
+            const long long T = blockIdx.x + j * gridDim.x;
+            if (T >= ntiles)
+                break;
+            const int b = (int)(j & 1);
+            if (j >= 2 && !mbar_wait(b_xe + 8u * b, (uint32_t)(((j >> 1) + 1) & 1), s_err))
+                break;
+            const long long r = T * MLP_ROWS + t;
+            const bool valid = r < a.B;
+            const uint4 *src = (const uint4 *)(a.X + r * a.d_in);
+            unsigned char *dst = sX + (size_t)b * xbytes;
+            for (int s0 = 0; s0 < nk; s0 += 8) {
+                uint4 q[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    q[i] = (valid && s0 + (i >> 1) < nk) ? __ldg(src + 2 * s0 + i) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    if (s0 + (i >> 1) < nk)
+                        *(uint4 *)(dst + (size_t)(s0 + (i >> 1)) * 4096 + kmaj_off_bf16(t, (i & 1) * 8)) = q[i];
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(b_xf + 8u * b);
+        }
+    } else if (t < MLP_INF_LOADERS + MLP_INF_EPI) {
+        // ---- epilogue: warp e of 16; TMEM lane quadrant warp % 4, quarter
+        // (e / 4) of the hidden units
+        const int quad = warp & 3, quarter = (warp - 4) >> 2;
+        const int rr = quad * 32 + lane;
+        const int qc = dh / 4, c0 = quarter * qc, c1 = c0 + qc;
+        for (long long j = 0;; ++j) {
+            const long long T = blockIdx.x + j * gridDim.x;
+            if (T >= ntiles)
+                break;
+            const int b = (int)(j & 1);
+            const bool ok = mbar_wait(b_af + 8u * b, (uint32_t)((j >> 1) & 1), s_err);
+            if (epi_any(!ok))
+                break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t trow = tmem + (uint32_t)(b * dh) + ((uint32_t)(quad * 32) << 16);
+            float y0 = 0.f, y1 = 0.f;
+            uint32_t v[32];
+            for (int c = c0; c < c1; c += 32) {
+                tmem_ld32_nowait(trow + (uint32_t)c, v);
+                tmem_wait_ld();
+                const float4 *b1v = (const float4 *)(s_b1 + c);
+                const float4 *w2v = (const float4 *)(s_W2 + 2 * c);
+#pragma unroll
+                for (int jj = 0; jj < 32; jj += 4) {
+                    const float4 bb = b1v[jj >> 2], wa = w2v[jj >> 1], wb = w2v[(jj >> 1) + 1];
+                    const uint32_t p01 = bf2_pack(gelu_f(__uint_as_float(v[jj]) + bb.x),
+                                                  gelu_f(__uint_as_float(v[jj + 1]) + bb.y));
+                    const uint32_t p23 = bf2_pack(gelu_f(__uint_as_float(v[jj + 2]) + bb.z),
+                                                  gelu_f(__uint_as_float(v[jj + 3]) + bb.w));
+                    const float h0 = __uint_as_float(p01 << 16), h1 = __uint_as_float(p01 & 0xffff0000u);
+                    const float h2 = __uint_as_float(p23 << 16), h3 = __uint_as_float(p23 & 0xffff0000u);
+                    y0 = fmaf(h0, wa.x, y0);
+                    y1 = fmaf(h0, wa.y, y1);
+                    y0 = fmaf(h1, wa.z, y0);
+                    y1 = fmaf(h1, wa.w, y1);
+                    y0 = fmaf(h2, wb.x, y0);
+                    y1 = fmaf(h2, wb.y, y1);
+                    y0 = fmaf(h3, wb.z, y0);
+                    y1 = fmaf(h3, wb.w, y1);
+                }
+            }
+            // the accumulator is free once this thread's loads have completed
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(b_ae + 8u * b);
+            s_y[(b * 4 + quarter) * 128 + rr] = make_float2(y0, y1);
+            asm volatile("bar.sync 1, %0;" ::"n"(MLP_INF_EPI) : "memory");
+            const long long r = T * MLP_ROWS + rr;
+            if (quarter == 0 && r < a.B) {
+                const float2 p0 = s_y[(b * 4) * 128 + rr], p1 = s_y[(b * 4 + 1) * 128 + rr];
+                const float2 p2 = s_y[(b * 4 + 2) * 128 + rr], p3 = s_y[(b * 4 + 3) * 128 + rr];
+                a.Y[2 * r] = ((p0.x + p1.x) + (p2.x + p3.x)) + a.b2[0];
+                a.Y[2 * r + 1] = ((p0.y + p1.y) + (p2.y + p3.y)) + a.b2[1];
+            }
+        }
+    } else if (lane == 0) {
+        // ---- MMA issuer
+        long long last = -1;
+        if (mbar_wait(b_w, 0, s_err)) {
+            w_seen = true;
+            const uint32_t idesc = mlp_idesc(128, dh);
+            for (long long j = 0;; ++j) {
+                const long long T = blockIdx.x + j * gridDim.x;
+                if (T >= ntiles)
+                    break;
+                const int b = (int)(j & 1);
+                if (!mbar_wait(b_xf + 8u * b, (uint32_t)((j >> 1) & 1), s_err))
+                    break;
+                if (j >= 2 && !mbar_wait(b_ae + 8u * b, (uint32_t)(((j >> 1) + 1) & 1), s_err))
+                    break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t xa = su32(sX + (size_t)b * xbytes), wa = su32(sW);
+                for (int s = 0; s < nk; ++s) {
+                    const uint64_t da = umma_desc(xa + (uint32_t)s * 4096u);
+                    const uint64_t db = umma_desc(wa + (uint32_t)(s * dh * 32));
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                                 ::"r"(tmem + (uint32_t)(b * dh)), "l"(da), "l"(db), "r"(idesc), "r"(s));
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(b_xe + 8u * b)
+                             : "memory");
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(b_af + 8u * b)
+                             : "memory");
+                last = j;
+            }
+        }
+        // no MMA of this CTA may still run, and no commit still arrive, when
+        // its TMEM and shared memory are released
+        if (last >= 0) {
+            mbar_wait(b_af + 8u * (int)(last & 1), (uint32_t)((last >> 1) & 1), nullptr);
+            mbar_wait(b_xe + 8u * (int)(last & 1), (uint32_t)((last >> 1) & 1), nullptr);
+        }
+        // nor a copy into its shared memory
+        if (!w_seen)
+            mbar_wait(b_w, 0, nullptr);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 20)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
+    if (t == 0 && *s_err)
+        atomicOr(a.err, 1);
+}

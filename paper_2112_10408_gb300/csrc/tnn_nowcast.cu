@@ -488,6 +488,7 @@ static tnn_status mlp_setup()
     if (!done) {
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_mlp_dw1_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        TNN_CUDA_TRY(cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         done = true;
     }
     return TNN_OK;
@@ -524,6 +525,19 @@ static tnn_status mlp_forward_impl(const tnn_mlp *n, const uint16_t *d_x, long l
     a.err = n->err;
     if (d_t)
         TNN_CUDA_TRY(cudaMemsetAsync(n->acc, 0, sizeof(float) * 4, st));
+    if (!d_t && n->dh % 128 == 0 && n->dh <= 256 &&
+        mlp_infer_smem(n->d_in, n->dh) <= (size_t)227 * 1024) {
+        // inference: persistent warp-specialised kernel, one CTA per SM
+        int dev = 0, nsm = 0;
+        TNN_CUDA_TRY(cudaGetDevice(&dev));
+        TNN_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        a.tmem_cols = tmem_cols_for(2 * n->dh);
+        const long long tiles = (B + MLP_ROWS - 1) / MLP_ROWS;
+        k_mlp_infer_tc<<<(unsigned)std::min<long long>(tiles, nsm), MLP_INF_THREADS,
+                         mlp_infer_smem(n->d_in, n->dh), st>>>(a);
+        TNN_CUDA_TRY(cudaGetLastError());
+        return TNN_OK;
+    }
     const size_t smem = tc_smem_request(mlp_fwd_smem(n->dh), a.tmem_cols);
     k_mlp_fwd_tc<<<(unsigned)((B + MLP_ROWS - 1) / MLP_ROWS), MLP_FWD_THREADS, smem, st>>>(a);
     TNN_CUDA_TRY(cudaGetLastError());
