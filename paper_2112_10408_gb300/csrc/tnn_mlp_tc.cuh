@@ -482,17 +482,20 @@ __global__ void __launch_bounds__(MLP_ROWS, 1) k_mlp_dw1_tc(const __grid_constan
 // k_mlp_infer_tc — inference (no targets), one persistent CTA per SM over
 // 128-row tiles, warp-specialised so that loading, the tensor cores and the
 // epilogue of different tiles overlap:
-//   warps 0-3   load the X tile of the next row block (one row per thread,
+//   warps 0-1   load the X tile of the next row block (two rows per thread,
 //               written in the core-matrix order) into one of two buffers;
-//   warp 20     (one thread) issues the MMAs of a tile, all K steps at once
+//   warp 18     (one thread) issues the MMAs of a tile, all K steps at once
 //               (W1^T stays in shared memory for the whole kernel), into one
 //               of two TMEM accumulators;
-//   warps 4-19  (four per TMEM lane quadrant, a quarter of the hidden units
+//   warps 2-17  (four per TMEM lane quadrant, a quarter of the hidden units
 //               each) read an accumulator, H = bf16(GELU(Z + b1)), the head.
+// 19 warps: at most 5 per SM sub-partition, so 96 registers per thread.
+// (X moved by TMA tensor copies of 16-byte-wide boxes measured slower.)
 // Barriers: x_full / x_empty per X buffer, acc_full / acc_empty per
 // accumulator; every wait is bounded (TC_WAIT_NS) and a failed wait ends the
 // kernel with a.err set.
-#define MLP_INF_LOADERS 128
+#define MLP_INF_LOADERS 64
+#define MLP_INF_MMA_WARP ((MLP_INF_LOADERS + MLP_INF_EPI) / 32)
 #define MLP_INF_EPI 512
 #define MLP_INF_THREADS (MLP_INF_LOADERS + MLP_INF_EPI + 32)
 
@@ -553,7 +556,7 @@ __global__ void __launch_bounds__(MLP_INF_THREADS, 1) k_mlp_infer_tc(const __gri
         s_W2[2 * i + 1] = a.W2[2 * i + 1];
     }
     const uint32_t cols = a.tmem_cols; // >= 2 dh
-    if (warp == 20) {
+    if (warp == MLP_INF_MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      ::"r"(su32(tmem_slot)), "r"(cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -565,7 +568,7 @@ __global__ void __launch_bounds__(MLP_INF_THREADS, 1) k_mlp_infer_tc(const __gri
     bool w_seen = false;
 
     if (t < MLP_INF_LOADERS) {
-        // ---- loaders: row t of each tile
+        // ---- loaders: rows t and t + 64 of each tile
         for (long long j = 0;; ++j) {
             const long long T = blockIdx.x + j * gridDim.x;
             if (T >= ntiles)
@@ -573,19 +576,22 @@ __global__ void __launch_bounds__(MLP_INF_THREADS, 1) k_mlp_infer_tc(const __gri
             const int b = (int)(j & 1);
             if (j >= 2 && !mbar_wait(b_xe + 8u * b, (uint32_t)(((j >> 1) + 1) & 1), s_err))
                 break;
-            const long long r = T * MLP_ROWS + t;
-            const bool valid = r < a.B;
-            const uint4 *src = (const uint4 *)(a.X + r * a.d_in);
             unsigned char *dst = sX + (size_t)b * xbytes;
-            for (int s0 = 0; s0 < nk; s0 += 8) {
-                uint4 q[16];
+            for (int h = 0; h < 2; ++h) {
+                const int row = t + h * MLP_INF_LOADERS;
+                const long long r = T * MLP_ROWS + row;
+                const bool valid = r < a.B;
+                const uint4 *src = (const uint4 *)(a.X + r * a.d_in);
+                for (int s0 = 0; s0 < nk; s0 += 8) {
+                    uint4 q[16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    q[i] = (valid && s0 + (i >> 1) < nk) ? __ldg(src + 2 * s0 + i) : make_uint4(0, 0, 0, 0);
+                    for (int i = 0; i < 16; ++i)
+                        q[i] = (valid && s0 + (i >> 1) < nk) ? __ldg(src + 2 * s0 + i) : make_uint4(0, 0, 0, 0);
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    if (s0 + (i >> 1) < nk)
-                        *(uint4 *)(dst + (size_t)(s0 + (i >> 1)) * 4096 + kmaj_off_bf16(t, (i & 1) * 8)) = q[i];
+                    for (int i = 0; i < 16; ++i)
+                        if (s0 + (i >> 1) < nk)
+                            *(uint4 *)(dst + (size_t)(s0 + (i >> 1)) * 4096 + kmaj_off_bf16(row, (i & 1) * 8)) = q[i];
+                }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(b_xf + 8u * b);
@@ -593,7 +599,7 @@ __global__ void __launch_bounds__(MLP_INF_THREADS, 1) k_mlp_infer_tc(const __gri
     } else if (t < MLP_INF_LOADERS + MLP_INF_EPI) {
         // ---- epilogue: warp e of 16; TMEM lane quadrant warp % 4, quarter
         // (e / 4) of the hidden units
-        const int quad = warp & 3, quarter = (warp - 4) >> 2;
+        const int quad = warp & 3, quarter = (warp - MLP_INF_LOADERS / 32) >> 2;
         const int rr = quad * 32 + lane;
         const int qc = dh / 4, c0 = quarter * qc, c1 = c0 + qc;
         for (long long j = 0;; ++j) {
@@ -607,10 +613,10 @@ __global__ void __launch_bounds__(MLP_INF_THREADS, 1) k_mlp_infer_tc(const __gri
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t trow = tmem + (uint32_t)(b * dh) + ((uint32_t)(quad * 32) << 16);
             float y0 = 0.f, y1 = 0.f;
-            uint32_t v[32];
-            for (int c = c0; c < c1; c += 32) {
-                tmem_ld32_nowait(trow + (uint32_t)c, v);
-                tmem_wait_ld();
+            // 32 columns at a time; the load of the next 32 is in flight
+            // while these are evaluated
+            uint32_t va[32], vb[32];
+            auto head32 = [&](const uint32_t (&v)[32], int c) {
                 const float4 *b1v = (const float4 *)(s_b1 + c);
                 const float4 *w2v = (const float4 *)(s_W2 + 2 * c);
 #pragma unroll
@@ -631,7 +637,21 @@ __global__ void __launch_bounds__(MLP_INF_THREADS, 1) k_mlp_infer_tc(const __gri
                     y0 = fmaf(h3, wb.z, y0);
                     y1 = fmaf(h3, wb.w, y1);
                 }
+            };
+            tmem_ld32_nowait(trow + (uint32_t)c0, va);
+            for (int c = c0; c < c1; c += 64) {
+                tmem_wait_ld();
+                if (c + 32 < c1)
+                    tmem_ld32_nowait(trow + (uint32_t)(c + 32), vb);
+                head32(va, c);
+                if (c + 32 >= c1)
+                    break;
+                tmem_wait_ld();
+                if (c + 64 < c1)
+                    tmem_ld32_nowait(trow + (uint32_t)(c + 64), va);
+                head32(vb, c + 32);
             }
+            tmem_wait_ld();
             // the accumulator is free once this thread's loads have completed
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(b_ae + 8u * b);
@@ -691,7 +711,7 @@ __global__ void __launch_bounds__(MLP_INF_THREADS, 1) k_mlp_infer_tc(const __gri
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 20)
+    if (warp == MLP_INF_MMA_WARP)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
     if (t == 0 && *s_err)
         atomicOr(a.err, 1);

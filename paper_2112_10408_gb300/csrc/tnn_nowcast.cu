@@ -156,9 +156,21 @@ __device__ __forceinline__ float2 normal_cdf_and_gauss(float z)
     const float erf_x = copysignf(erf_ax, x);
     return make_float2(fmaf(0.5f, erf_x, 0.5f), g);
 }
+// z Phi(z) by the same approximation, with the scalings by 1/sqrt(2) and 1/2
+// folded into its constants: for z >= 0, z Phi(z) = z - q and for z < 0 it is
+// q, where q = z t P(t) exp(-z^2 / 2) / 2 and t = 1 / (1 + p |z| / sqrt(2)).
 __device__ __forceinline__ float gelu_f(float z)
 {
-    return z * normal_cdf_and_gauss(z).x;
+    const float t = __fdividef(1.0f, fmaf(0.3275911f * 0.70710678118654752f, fabsf(z), 1.0f));
+    float poly = fmaf(t, 0.5f * 1.061405429f, 0.5f * -1.453152027f);
+    poly = fmaf(t, poly, 0.5f * 1.421413741f);
+    poly = fmaf(t, poly, 0.5f * -0.284496736f);
+    poly = fmaf(t, poly, 0.5f * 0.254829592f);
+    poly *= t;
+    float g; // 2^(-z^2 log2(e) / 2)
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(g) : "f"(z * (z * -0.72134752044448170f)));
+    const float q = (poly * g) * z;
+    return z >= 0.0f ? z - q : q;
 }
 __device__ __forceinline__ float gelu_grad_f(float z)
 {
