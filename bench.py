@@ -424,6 +424,25 @@ def _extras(tnn, synth, flush, peaks, steps):
     c0 = time.perf_counter()
     ncr.gka_forward(wl.xyzt, wl.wind, wl.xyzt[smp], idx_s, np.log(gsig.astype(np.float64)))
     c_gka = time.perf_counter() - c0
+    # one training step of each learned form in the oracle (batch B)
+    xb_, yb_ = batches[1]
+    Xo = xb_.float().cpu().numpy().astype(np.float64)
+    To = yb_.cpu().numpy().astype(np.float64)
+    wflat = mlp.get_params().astype(np.float64)
+    c0 = time.perf_counter()
+    _, go = ncr.mlp_grads(Xo, To, W1, b1m, W2, b2m)
+    gflat = np.concatenate([np.ravel(go[nm]) for nm in ("W1", "b1", "W2", "b2")])
+    ncr.adamw_step(wflat, gflat, np.zeros_like(wflat), np.zeros_like(wflat), 1)
+    c_train = time.perf_counter() - c0
+    rows_o = gbatches[1].cpu().numpy()
+    idx_all = idx.cpu().numpy()
+    c0 = time.perf_counter()
+    ncr.gka_loss_grad(wl.xyzt, wl.wind, rows_o, idx_all, np.log(gsig.astype(np.float64)))
+    c_gka_train = time.perf_counter() - c0
+    lo_b, hi_b = wl.xyzt.min(axis=0), wl.xyzt.max(axis=0)
+    c0 = time.perf_counter()
+    ncr.gkamlp_forward(wl.xyzt, wl.wind, wl.xyzt[smp], idx_s, gm.get_params()[0].astype(np.float64), 32, lo_b, hi_b)
+    c_gm = time.perf_counter() - c0
 
     def _cpu(sec, unit):
         return {"value": ns / sec, "unit": unit, "cores": os.cpu_count(), "kind": "oracle",
@@ -441,6 +460,9 @@ def _extras(tnn, synth, flush, peaks, steps):
                       "how": "CUDA graph of 16 tnn_mlp_train_step calls, replayed",
                       "host_loop_ms_per_step": ms_train, "batch": B, "steps": len(batches) - 1,
                       "epochs": epochs,
+                      "cpu_baseline": {"value": B / c_train, "unit": "samples/s", "cores": os.cpu_count(),
+                                       "kind": "oracle",
+                                       "sample": f"one training step (batch {B}): float64 numpy gradients + AdamW"},
                       "roofline": {"bound": "tensor", "achieved": flops_step / (ms_graph / 1e3) / 1e12,
                                    "peak": bf16, "unit": "TFLOP/s",
                                    "frac": flops_step / (ms_graph / 1e3) / 1e12 / bf16,
@@ -462,9 +484,13 @@ def _extras(tnn, synth, flush, peaks, steps):
                                          "frac": gka_bytes / (ms_gka / 1e3) / 1e9 / hbm,
                                          "bytes_per_context": 28 * k + 24, "peak_note": "of measured hbm_gbs"}},
                 "train_step": {"value": B / (ms_gka_train / 1e3), "unit": "samples/s", "ms": ms_gka_train,
-                               "batch": B, "steps": gstep},
+                               "batch": B, "steps": gstep,
+                               "cpu_baseline": {"value": B / c_gka_train, "unit": "samples/s",
+                                                "cores": os.cpu_count(), "kind": "oracle",
+                                                "sample": f"one loss + gradient evaluation (batch {B}), float64 numpy"}},
                 "sigma": [float(x) for x in gsig]},
         "gka_mlp": {"forward": {"value": qte.shape[0] / (ms_gm / 1e3), "unit": "nowcasts/s", "ms": ms_gm,
+                                "cpu_baseline": _cpu(c_gm, "nowcasts/s"),
                                 "roofline": {"bound": "hbm", "achieved": gka_bytes / (ms_gm / 1e3) / 1e9,
                                              "peak": hbm, "unit": "GB/s",
                                              "frac": gka_bytes / (ms_gm / 1e3) / 1e9 / hbm,

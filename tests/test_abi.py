@@ -58,3 +58,34 @@ def test_argument_errors_without_device(lib):
     st = L.tnn_mlp_create(100, 256, 0, ctypes.byref(h))
     assert st == 1 and b"d_in" in L.tnn_last_error()
     assert L.tnn_status_string(0) == b"ok"
+
+
+def test_host_pipeline_and_memory_argument_errors(lib):
+    from paper_2112_10408_gb300 import tnn
+    L = tnn.load_library()
+    bp = tnn.tnn_build_params()
+    bp.seg_len = 10
+    for i in range(4):
+        bp.sigma[i] = 1.0
+    kp = tnn.make_knn_params(8)
+    off = (ctypes.c_int64 * 2)(0, 10)
+    buf = (ctypes.c_float * 40)()
+    oi = (ctypes.c_int32 * 80)()
+    od = (ctypes.c_float * 80)()
+    # NULL outputs
+    st = L.tnn_knn_host(buf, 10, off, 1, ctypes.byref(bp), ctypes.byref(kp), 0, None, None, None)
+    assert st == 1 and b"NULL" in L.tnn_last_error()
+    # no points
+    st = L.tnn_knn_host(buf, 0, off, 1, ctypes.byref(bp), ctypes.byref(kp), 0, oi, od, None)
+    assert st == 1 and b"n must" in L.tnn_last_error()
+    # k out of range
+    kp0 = tnn.make_knn_params(65)
+    st = L.tnn_knn_host(buf, 10, off, 1, ctypes.byref(bp), ctypes.byref(kp0), 0, oi, od, None)
+    assert st == 1 and b"k must" in L.tnn_last_error()
+    # too many slices
+    st = L.tnn_knn_host(buf, 10, off, 1, ctypes.byref(bp), ctypes.byref(kp), 65, oi, od, None)
+    assert st == 1 and b"chunks" in L.tnn_last_error()
+    st = L.tnn_memory_trim(-1)
+    assert st == 1 and b"keep_bytes" in L.tnn_last_error()
+    st = L.tnn_memory_reserved(None, None)
+    assert st == 1 and b"NULL" in L.tnn_last_error()
