@@ -10,7 +10,11 @@
 #include <mutex>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "tnn_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 // ------------------------------------------------------------------ errors
 
@@ -218,7 +222,7 @@ __global__ void k_bitonic_block(unsigned long long *keys)
     for (int k = 2; k <= BS_BLOCK; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
             int t = threadIdx.x;
-            int i = (t / j) * 2 * j + (t % j);
+            int i = ((t & ~(j - 1)) << 1) | (t & (j - 1)); // j is a power of two
             bool asc = ((base + i) & k) == 0;
             cmpx(s[i], s[i + j], asc);
             __syncthreads();
@@ -237,7 +241,7 @@ __global__ void k_bitonic_merge_local(unsigned long long *keys, int k)
     __syncthreads();
     for (int j = BS_BLOCK >> 1; j > 0; j >>= 1) {
         int t = threadIdx.x;
-        int i = (t / j) * 2 * j + (t % j);
+        int i = ((t & ~(j - 1)) << 1) | (t & (j - 1)); // j is a power of two
         bool asc = ((base + i) & k) == 0;
         cmpx(s[i], s[i + j], asc);
         __syncthreads();
@@ -249,7 +253,7 @@ __global__ void k_bitonic_merge_local(unsigned long long *keys, int k)
 __global__ void k_bitonic_global(unsigned long long *keys, int j, int k)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x; // one per pair
-    int i = (t / j) * 2 * j + (t % j);
+    int i = ((t & ~(j - 1)) << 1) | (t & (j - 1)); // j is a power of two
     bool asc = (i & k) == 0;
     unsigned long long a = keys[i], b = keys[i + j];
     if ((a > b) == asc) {
@@ -266,8 +270,61 @@ int tnn_next_pow2_sort(int64_t n)
     return (int)p;
 }
 
+// The whole network for n2 <= 32768 keys in one launch: a cluster of 8 CTAs,
+// each holding n2 / 8 consecutive keys in shared memory.  Steps whose
+// partner lies in the same CTA exchange in shared memory; steps whose
+// partner lies in another CTA (j >= n2 / 8) read it through distributed
+// shared memory between two cluster barriers (all old values read before
+// any is replaced).
+#define BS_CLUSTER 8
+#define BS_CLUSTER_MAX (BS_CLUSTER * 4096)
+
+__global__ void __cluster_dims__(BS_CLUSTER, 1, 1) __launch_bounds__(1024)
+    k_bitonic_cluster(unsigned long long *keys, int n2)
+{
+    __shared__ unsigned long long s[4096];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int c = (int)cluster.block_rank(), nl = n2 / BS_CLUSTER, base = c * nl;
+    for (int e = threadIdx.x; e < nl; e += 1024)
+        s[e] = keys[base + e];
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j < nl) {
+                for (int q = threadIdx.x; q < nl / 2; q += 1024) {
+                    const int i = ((q & ~(j - 1)) << 1) | (q & (j - 1)); // j is a power of two
+                    cmpx(s[i], s[i + j], ((base + i) & k) == 0);
+                }
+                __syncthreads();
+            } else {
+                const unsigned long long *peer = cluster.map_shared_rank(s, c ^ (j / nl));
+                unsigned long long nv[4];
+                cluster.sync();
+                for (int e = threadIdx.x, u = 0; e < nl; e += 1024, ++u) {
+                    const int g = base + e;
+                    const unsigned long long v = s[e], w = peer[e];
+                    const bool take_min = ((g & j) == 0) == ((g & k) == 0);
+                    nv[u] = take_min ? (w < v ? w : v) : (w < v ? v : w);
+                }
+                cluster.sync();
+                for (int e = threadIdx.x, u = 0; e < nl; e += 1024, ++u)
+                    s[e] = nv[u];
+                __syncthreads();
+            }
+        }
+    }
+    for (int e = threadIdx.x; e < nl; e += 1024)
+        keys[base + e] = s[e];
+    // no CTA may leave while another still reads its shared memory
+    cluster.sync();
+}
+
 void tnn_bitonic_sort(unsigned long long *keys, int n2, cudaStream_t st)
 {
+    if (n2 <= BS_CLUSTER_MAX) {
+        k_bitonic_cluster<<<BS_CLUSTER, 1024, 0, st>>>(keys, n2);
+        return;
+    }
     k_bitonic_block<<<n2 / BS_BLOCK, 1024, 0, st>>>(keys);
     for (int k = 2 * BS_BLOCK; k <= n2; k <<= 1) {
         for (int j = k >> 1; j >= BS_BLOCK; j >>= 1)
