@@ -139,6 +139,67 @@ __global__ void __launch_bounds__(GKA_WARPS * 32) k_gka(const __grid_constant__ 
     }
 }
 
+// Forward for k <= 32: two queries per warp, lane = neighbour, so that the
+// index loads and the neighbour gathers of both queries are in flight
+// together.  The arithmetic is k_gka's, operation for operation.
+__global__ void __launch_bounds__(GKA_WARPS * 32) k_gka_fwd_pair(const __grid_constant__ GkaArgs a)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long r0 = ((long long)blockIdx.x * GKA_WARPS + warp) * 2;
+    const float sxy = __expf(a.theta[0]), sz = __expf(a.theta[1]), st = __expf(a.theta[2]);
+    int id[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const long long r = r0 + h;
+        id[h] = (r < a.m && lane < a.k) ? a.idx[r * a.k + lane] : -1;
+    }
+    float4 q[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const long long r = r0 + h < a.m ? r0 + h : 0;
+        q[h] = a.q ? a.q[r] : a.pts[r];
+    }
+    float e[2], su[2], sv[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        e[h] = INFINITY;
+        su[h] = sv[h] = 0.f;
+        if (id[h] >= 0) {
+            const float4 p = a.pts[id[h]];
+            const float2 s = a.wind[id[h]];
+            const float dx = p.x - q[h].x, dy = p.y - q[h].y, dz = p.z - q[h].z, dt = p.w - q[h].w;
+            e[h] = fmaf(sxy, fmaf(dx, dx, dy * dy), fmaf(sz, dz * dz, st * (dt * dt)));
+            su[h] = s.x;
+            sv[h] = s.y;
+        }
+    }
+    float emin[2] = {e[0], e[1]};
+    for (int o = 16; o > 0; o >>= 1) {
+        emin[0] = fminf(emin[0], __shfl_xor_sync(FULLMASK, emin[0], o));
+        emin[1] = fminf(emin[1], __shfl_xor_sync(FULLMASK, emin[1], o));
+    }
+    float W[2], U[2], V[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float w = id[h] >= 0 ? expf(emin[h] - e[h]) : 0.f;
+        W[h] = w;
+        U[h] = fmaf(w, su[h], 0.f);
+        V[h] = fmaf(w, sv[h], 0.f);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            W[h] += __shfl_xor_sync(FULLMASK, W[h], o);
+            U[h] += __shfl_xor_sync(FULLMASK, U[h], o);
+            V[h] += __shfl_xor_sync(FULLMASK, V[h], o);
+        }
+    }
+    if (lane < 2 && r0 + lane < a.m) {
+        const int h = lane;
+        a.out[r0 + h] = make_float2(U[h] / W[h], V[h] / W[h]); // NaN for an empty context
+    }
+}
+
 struct GkaAdamArgs {
     const float *part;
     long long nblocks;
@@ -310,7 +371,11 @@ extern "C" tnn_status tnn_gka_forward(const tnn_gka *g, const tnn_index *ix, con
     a.k = k;
     a.theta = g->theta;
     a.out = (float2 *)d_uv;
-    k_gka<<<(unsigned)((m + GKA_WARPS - 1) / GKA_WARPS), GKA_WARPS * 32, 0, (cudaStream_t)stream>>>(a);
+    if (k <= 32)
+        k_gka_fwd_pair<<<(unsigned)((m + 2 * GKA_WARPS - 1) / (2 * GKA_WARPS)), GKA_WARPS * 32, 0,
+                         (cudaStream_t)stream>>>(a);
+    else
+        k_gka<<<(unsigned)((m + GKA_WARPS - 1) / GKA_WARPS), GKA_WARPS * 32, 0, (cudaStream_t)stream>>>(a);
     TNN_CUDA_TRY(cudaGetLastError());
     return TNN_OK;
 }
