@@ -483,6 +483,80 @@ struct GkaMlpArgs {
     float inv_B;
 };
 
+// Forward for k <= 32: two queries per warp (lane = neighbour, lane =
+// hidden unit), the arithmetic of k_gkamlp operation for operation.
+__global__ void __launch_bounds__(GKA_WARPS * 32) k_gkamlp_fwd_pair(const __grid_constant__ GkaMlpArgs a)
+{
+    extern __shared__ float s_w[]; // [P] parameters
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int H = a.H, P = a.P;
+    for (int i = threadIdx.x; i < P; i += blockDim.x)
+        s_w[i] = a.w[i];
+    __syncthreads();
+    const float *W1 = s_w, *b1 = s_w + 3 * H, *W2 = s_w + 4 * H, *b2 = s_w + 7 * H;
+    const long long r0 = ((long long)blockIdx.x * GKA_WARPS + warp) * 2;
+    int id[2];
+    float4 q[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const long long r = r0 + h;
+        id[h] = (r < a.m && lane < a.k) ? a.idx[r * a.k + lane] : -1;
+        const long long rq = r < a.m ? r : 0;
+        q[h] = a.q ? a.q[rq] : a.pts[rq];
+    }
+    float sc[2][3];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float u[3] = {(q[h].x - a.lo[0]) * a.inv_ext[0], (q[h].y - a.lo[1]) * a.inv_ext[1],
+                            (q[h].z - a.lo[2]) * a.inv_ext[2]};
+        float hj = 0.f;
+        if (lane < H)
+            hj = tanhf(fmaf(W1[lane], u[0], fmaf(W1[H + lane], u[1], fmaf(W1[2 * H + lane], u[2], b1[lane]))));
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+            sc[h][f] = __expf(b2[f] + warp_sum(lane < H ? hj * W2[3 * lane + f] : 0.f));
+    }
+    float e[2], su[2], sv[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        e[h] = INFINITY;
+        su[h] = sv[h] = 0.f;
+        if (id[h] >= 0) {
+            const float4 p = a.pts[id[h]];
+            const float2 s = a.wind[id[h]];
+            const float dx = p.x - q[h].x, dy = p.y - q[h].y, dz = p.z - q[h].z, dt = p.w - q[h].w;
+            e[h] = fmaf(sc[h][0], fmaf(dx, dx, dy * dy), fmaf(sc[h][1], dz * dz, sc[h][2] * (dt * dt)));
+            su[h] = s.x;
+            sv[h] = s.y;
+        }
+    }
+    float emin[2] = {e[0], e[1]};
+    for (int o = 16; o > 0; o >>= 1) {
+        emin[0] = fminf(emin[0], __shfl_xor_sync(FULLMASK, emin[0], o));
+        emin[1] = fminf(emin[1], __shfl_xor_sync(FULLMASK, emin[1], o));
+    }
+    float W[2], U[2], V[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float w = id[h] >= 0 ? expf(emin[h] - e[h]) : 0.f;
+        W[h] = w;
+        U[h] = fmaf(w, su[h], 0.f);
+        V[h] = fmaf(w, sv[h], 0.f);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            W[h] += __shfl_xor_sync(FULLMASK, W[h], o);
+            U[h] += __shfl_xor_sync(FULLMASK, U[h], o);
+            V[h] += __shfl_xor_sync(FULLMASK, V[h], o);
+        }
+    }
+    if (lane < 2 && r0 + lane < a.m) {
+        const int h = lane;
+        a.out[r0 + h] = make_float2(U[h] / W[h], V[h] / W[h]); // NaN for an empty context
+    }
+}
+
 __global__ void __launch_bounds__(GKA_WARPS * 32) k_gkamlp(const __grid_constant__ GkaMlpArgs a)
 {
     extern __shared__ float s_w[]; // [P] parameters, then [GKA_WARPS][P + 1] partials
@@ -785,8 +859,12 @@ extern "C" tnn_status tnn_gkamlp_forward(const tnn_gkamlp *g, const tnn_index *i
     a.q = (const float4 *)d_q;
     a.m = m;
     a.out = (float2 *)d_uv;
-    k_gkamlp<<<(unsigned)((m + GKA_WARPS - 1) / GKA_WARPS), GKA_WARPS * 32, g->P * sizeof(float),
-               (cudaStream_t)stream>>>(a);
+    if (k <= 32 && g->H <= 32)
+        k_gkamlp_fwd_pair<<<(unsigned)((m + 2 * GKA_WARPS - 1) / (2 * GKA_WARPS)), GKA_WARPS * 32,
+                            g->P * sizeof(float), (cudaStream_t)stream>>>(a);
+    else
+        k_gkamlp<<<(unsigned)((m + GKA_WARPS - 1) / GKA_WARPS), GKA_WARPS * 32, g->P * sizeof(float),
+                   (cudaStream_t)stream>>>(a);
     TNN_CUDA_TRY(cudaGetLastError());
     return TNN_OK;
 }
