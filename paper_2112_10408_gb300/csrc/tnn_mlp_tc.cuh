@@ -70,9 +70,18 @@ struct MlpFwdArgs {
     float inv_B;
     uint32_t tmem_cols;
     int *err;            // set when a device wait timed out
+    int resident;        // 1: all K steps of X and W1^T staged at once (mlp_fwd_smem_res)
 };
 
 #define MLP_FWD_THREADS 256 // two warps per TMEM lane quadrant, one per half of the hidden units
+
+// Shared memory with every K step staged at once (resident = 1): the same
+// layout with nk stages instead of 4.
+__host__ __device__ inline size_t mlp_fwd_smem_res(int d_in, int dh)
+{
+    const size_t nk = (size_t)d_in / 16;
+    return nk * (4096 + (size_t)dh * 32) + (size_t)dh * 12 + 4 * ((size_t)dh * 3 + 2) * 4 + 2048 + 128;
+}
 
 __host__ __device__ inline size_t mlp_fwd_smem(int dh)
 {
@@ -107,9 +116,10 @@ __global__ void __launch_bounds__(MLP_FWD_THREADS, 2) k_mlp_fwd_tc(const __grid_
     const int rr = t & (MLP_ROWS - 1);           // row of the tile (= TMEM lane)
     const int dh = a.dh, nk = a.d_in / 16, hh = dh / 2;
     const size_t bstage = (size_t)dh * 32;
-    unsigned char *sA = smem;                 // [4][4096]
-    unsigned char *sB = smem + 4 * 4096;      // [4][bstage]
-    float *s_b1 = (float *)(sB + 4 * bstage); // [dh]
+    const int nst = a.resident ? nk : 4;        // K-step stages in shared memory
+    unsigned char *sA = smem;                   // [nst][4096]
+    unsigned char *sB = smem + (size_t)nst * 4096; // [nst][bstage]
+    float *s_b1 = (float *)(sB + nst * bstage); // [dh]
     float *s_W2 = s_b1 + dh;                  // [dh][2]
     const int ncol = 3 * dh + 2;
     float *s_col = s_W2 + 2 * dh;             // [4 quadrants][3 dh + 2]
@@ -129,12 +139,22 @@ __global__ void __launch_bounds__(MLP_FWD_THREADS, 2) k_mlp_fwd_tc(const __grid_
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bars + i)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *s_err = 0;
-        // W1^T slices of the first two K steps
-        for (int s = 0; s < 2 && s < nk; ++s) {
+        if (a.resident) {
+            // every W1^T slice, on one barrier
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                         ::"r"(bar_full0 + 8u * s), "r"((uint32_t)bstage)
+                         ::"r"(bar_full0), "r"((uint32_t)(bstage * nk))
                          : "memory");
-            tma_copy_1d(su32(sB + s * bstage), a.w1t + (size_t)s * dh * 16, (uint32_t)bstage, bar_full0 + 8u * s);
+            for (int s = 0; s < nk; ++s)
+                tma_copy_1d(su32(sB + s * bstage), a.w1t + (size_t)s * dh * 16, (uint32_t)bstage, bar_full0);
+        } else {
+            // W1^T slices of the first two K steps
+            for (int s = 0; s < 2 && s < nk; ++s) {
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                             ::"r"(bar_full0 + 8u * s), "r"((uint32_t)bstage)
+                             : "memory");
+                tma_copy_1d(su32(sB + s * bstage), a.w1t + (size_t)s * dh * 16, (uint32_t)bstage,
+                            bar_full0 + 8u * s);
+            }
         }
     }
     for (int i = t; i < dh; i += MLP_FWD_THREADS) {
@@ -154,76 +174,118 @@ __global__ void __launch_bounds__(MLP_FWD_THREADS, 2) k_mlp_fwd_tc(const __grid_
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    // ---- Z = X W1: K steps of 16 inputs, four stages; the W1^T slice of
-    // step s + 2 is copied while step s is prepared; thread (row rr, half)
-    // moves 8 of the 16 values of its row
     bool ok = true;
-    uint4 xq[8]; // this thread's X values of the next 8 K steps, loaded together
-    for (int s = 0; s < nk; ++s) {
-        const int st = s & 3;
-        if ((s & 7) == 0) {
+    if (a.resident) {
+        // ---- Z = X W1 with every K step staged at once: the threads write
+        // all of X (and X^T when training), then one thread issues every MMA
+#pragma unroll 4
+        for (int s = 0; s < nk; ++s) {
+            const uint4 x = valid ? __ldg((const uint4 *)(a.X + r * a.d_in + s * 16 + half * 8))
+                                  : make_uint4(0, 0, 0, 0);
+            *(uint4 *)(sA + (size_t)s * 4096 + kmaj_off_bf16(rr, half * 8)) = x;
+            if (train && r < Bp) {
+                const uint16_t *xs = (const uint16_t *)&x;
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-                xq[i] = (valid && s + i < nk) ? __ldg((const uint4 *)(a.X + r * a.d_in + (s + i) * 16 + half * 8))
-                                              : make_uint4(0, 0, 0, 0);
-        }
-        if (s >= 2) {
-            // the MMA of step s - 2 (and every one before it) has completed:
-            // stage (s + 2) & 3 and stage s & 3 are free
-            const bool w = mbar_wait(bar_mma0 + 8u * ((s - 2) & 3), (uint32_t)(((s - 2) >> 2) & 1), s_err);
-            if (__syncthreads_or(!w)) {
-                ok = false;
-                break;
+                for (int j = 0; j < 8; ++j)
+                    a.Xt[(long long)(s * 16 + half * 8 + j) * a.ldt + r] = xs[j];
             }
-        }
-        if (t == 0 && s + 2 < nk) {
-            const int s2 = s + 2, st2 = s2 & 3;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                         ::"r"(bar_full0 + 8u * st2), "r"((uint32_t)bstage)
-                         : "memory");
-            tma_copy_1d(su32(sB + st2 * bstage), a.w1t + (size_t)s2 * dh * 16, (uint32_t)bstage,
-                        bar_full0 + 8u * st2);
-        }
-        uint4 x = xq[0];
-#pragma unroll
-        for (int i = 1; i < 8; ++i)
-            if ((s & 7) == i)
-                x = xq[i];
-        *(uint4 *)(sA + st * 4096 + kmaj_off_bf16(rr, half * 8)) = x;
-        if (train && r < Bp) {
-            // X^T for the dW1 product (zeros pad the batch to 16)
-            const uint16_t *xs = (const uint16_t *)&x;
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                a.Xt[(long long)(s * 16 + half * 8 + j) * a.ldt + r] = xs[j];
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (t == 0) {
-            if (!mbar_wait(bar_full0 + 8u * st, (uint32_t)((s >> 2) & 1), s_err)) {
+            if (!mbar_wait(bar_full0, 0u, s_err)) {
                 ok = false;
             } else {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint64_t da = umma_desc(su32(sA + st * 4096));
-                for (int n0 = 0; n0 < dh; n0 += 256) {
-                    const int nn = min(256, dh - n0);
-                    const uint64_t db = umma_desc(su32(sB + st * bstage + (size_t)n0 * 32));
-                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
-                                 ::"r"(tmem + (uint32_t)n0), "l"(da), "l"(db), "r"(mlp_idesc(128, nn)),
-                                 "r"(s));
+                for (int s = 0; s < nk; ++s) {
+                    const uint64_t da = umma_desc(su32(sA + (size_t)s * 4096));
+                    for (int n0 = 0; n0 < dh; n0 += 256) {
+                        const int nn = min(256, dh - n0);
+                        const uint64_t db = umma_desc(su32(sB + s * bstage + (size_t)n0 * 32));
+                        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                                     ::"r"(tmem + (uint32_t)n0), "l"(da), "l"(db), "r"(mlp_idesc(128, nn)),
+                                     "r"(s));
+                    }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             ::"r"(bar_mma0 + 8u * st)
+                             ::"r"(bar_mma0)
                              : "memory");
             }
         }
-    }
-    // the last MMA's barrier covers every MMA before it
-    {
-        const int sl = nk - 1;
-        const bool w = ok && mbar_wait(bar_mma0 + 8u * (sl & 3), (uint32_t)((sl >> 2) & 1), s_err);
+        const bool w = __syncthreads_and(ok) && mbar_wait(bar_mma0, 0u, s_err);
         ok = !__syncthreads_or(!w);
+    } else {
+        // ---- Z = X W1: K steps of 16 inputs, four stages; the W1^T slice of
+        // step s + 2 is copied while step s is prepared; thread (row rr, half)
+        // moves 8 of the 16 values of its row
+        uint4 xq[8]; // this thread's X values of the next 8 K steps, loaded together
+        for (int s = 0; s < nk; ++s) {
+            const int st = s & 3;
+            if ((s & 7) == 0) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    xq[i] = (valid && s + i < nk) ? __ldg((const uint4 *)(a.X + r * a.d_in + (s + i) * 16 + half * 8))
+                                                  : make_uint4(0, 0, 0, 0);
+            }
+            if (s >= 2) {
+                // the MMA of step s - 2 (and every one before it) has completed:
+                // stage (s + 2) & 3 and stage s & 3 are free
+                const bool w = mbar_wait(bar_mma0 + 8u * ((s - 2) & 3), (uint32_t)(((s - 2) >> 2) & 1), s_err);
+                if (__syncthreads_or(!w)) {
+                    ok = false;
+                    break;
+                }
+            }
+            if (t == 0 && s + 2 < nk) {
+                const int s2 = s + 2, st2 = s2 & 3;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                             ::"r"(bar_full0 + 8u * st2), "r"((uint32_t)bstage)
+                             : "memory");
+                tma_copy_1d(su32(sB + st2 * bstage), a.w1t + (size_t)s2 * dh * 16, (uint32_t)bstage,
+                            bar_full0 + 8u * st2);
+            }
+            uint4 x = xq[0];
+#pragma unroll
+            for (int i = 1; i < 8; ++i)
+                if ((s & 7) == i)
+                    x = xq[i];
+            *(uint4 *)(sA + st * 4096 + kmaj_off_bf16(rr, half * 8)) = x;
+            if (train && r < Bp) {
+                // X^T for the dW1 product (zeros pad the batch to 16)
+                const uint16_t *xs = (const uint16_t *)&x;
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    a.Xt[(long long)(s * 16 + half * 8 + j) * a.ldt + r] = xs[j];
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (t == 0) {
+                if (!mbar_wait(bar_full0 + 8u * st, (uint32_t)((s >> 2) & 1), s_err)) {
+                    ok = false;
+                } else {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint64_t da = umma_desc(su32(sA + st * 4096));
+                    for (int n0 = 0; n0 < dh; n0 += 256) {
+                        const int nn = min(256, dh - n0);
+                        const uint64_t db = umma_desc(su32(sB + st * bstage + (size_t)n0 * 32));
+                        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                                     ::"r"(tmem + (uint32_t)n0), "l"(da), "l"(db), "r"(mlp_idesc(128, nn)),
+                                     "r"(s));
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 ::"r"(bar_mma0 + 8u * st)
+                                 : "memory");
+                }
+            }
+        }
+        // the last MMA's barrier covers every MMA before it
+        {
+            const int sl = nk - 1;
+            const bool w = ok && mbar_wait(bar_mma0 + 8u * (sl & 3), (uint32_t)((sl >> 2) & 1), s_err);
+            ok = !__syncthreads_or(!w);
+        }
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {

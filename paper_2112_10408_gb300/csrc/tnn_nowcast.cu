@@ -550,7 +550,10 @@ static tnn_status mlp_forward_impl(const tnn_mlp *n, const uint16_t *d_x, long l
         TNN_CUDA_TRY(cudaGetLastError());
         return TNN_OK;
     }
-    const size_t smem = tc_smem_request(mlp_fwd_smem(n->dh), a.tmem_cols);
+    // every K step staged at once when it fits (no per-step synchronisation)
+    a.resident = mlp_fwd_smem_res(n->d_in, n->dh) <= (size_t)227 * 1024;
+    const size_t smem = tc_smem_request(a.resident ? mlp_fwd_smem_res(n->d_in, n->dh) : mlp_fwd_smem(n->dh),
+                                        a.tmem_cols);
     k_mlp_fwd_tc<<<(unsigned)((B + MLP_ROWS - 1) / MLP_ROWS), MLP_FWD_THREADS, smem, st>>>(a);
     TNN_CUDA_TRY(cudaGetLastError());
     return TNN_OK;

@@ -81,12 +81,15 @@ def test_mlp_inference_many_tiles(d_in, dh, B):
     np.testing.assert_array_equal(y2, y[B // 3:])
 
 
-def test_mlp_gradients_match_oracle():
-    m, w = _mlp_with_params(192, 256, seed=2)
+@pytest.mark.parametrize("d_in,dh", [(192, 256), (512, 512)])
+def test_mlp_gradients_match_oracle(d_in, dh):
+    """(192, 256) stages every K step at once; (512, 512) does not fit and
+    streams the K steps through four stages."""
+    m, w = _mlp_with_params(d_in, dh, seed=2)
     W1, b1, W2, b2 = m.unflatten(w.astype(np.float64))
     rng = np.random.default_rng(3)
     B = 1000
-    X = rng.normal(0, 1, size=(B, 192)).astype(np.float32)
+    X = rng.normal(0, 1, size=(B, d_in)).astype(np.float32)
     T = rng.normal(0, 1, size=(B, 2)).astype(np.float32)
     loss, g = m.gradients(torch.from_numpy(X).to(torch.bfloat16).cuda(), torch.from_numpy(T).cuda())
     g = g.cpu().numpy().astype(np.float64)
