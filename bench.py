@@ -39,11 +39,11 @@ OPS_PER_KEY = 20
 # summarised in profiles/k_tnn_grid_search_medium.md, with a hash of the
 # kernel sources it was taken on (stale, and reported as null, once they
 # change) and the tuning of that capture.
-SEARCH_TRAFFIC = {"bytes": (10480384 + 32906752) + (7974144 + 93184) + 113920, "workload": "medium",
+SEARCH_TRAFFIC = {"bytes": (10512384 + 31606016) + (8107264 + 119552) + 115200, "workload": "medium",
                   "sources": ["tnn_device.cuh", "tnn_grid.cuh", "tnn_fallback.cuh", "tnn_internal.cuh",
                               "tnn_knn.cu", "tnn_index.cu"],
-                  "tuning": {"seed_segments": 3, "extra": 4, "defer_cells": 0.75},
-                  "sha256_16": "6f47a0781f7201eb"}
+                  "tuning": {"seed_segments": 3, "extra": 4, "defer_cells": 0.6},
+                  "sha256_16": "011cf2dd8bbfc911"}
 
 
 def _search_traffic(workload):
