@@ -267,9 +267,9 @@ tnn_status tnn_profile_read(double *ms, int64_t *launches, int32_t reset);
  * copied in, indexed (as tnn_build_segments with *bp) and every point is
  * answered as its own query (as tnn_knn with d_q = NULL and *kp); the
  * neighbour lists land in host memory.  The queries are answered in `chunks`
- * consecutive slices of rows (0 = the library's choice, 2; at most 64): a
- * second stream copies a slice's lists out while the search works on the
- * next slice.
+ * consecutive slices of rows (0 = the library's choice, 2; at most 64),
+ * shrinking by 2/3 from one to the next: a second stream copies a slice's
+ * lists out while the search works on the next slice.
  *   h_xyzt [n][4] float, h_traj_off [n_traj + 1]: as tnn_build_segments,
  *     host memory (page-locked memory is copied faster).
  *   h_idx [n][k] int32, h_d2 [n][k] float: host outputs, layout as tnn_knn.

@@ -72,10 +72,27 @@ extern "C" tnn_status tnn_knn_host(const float *h_xyzt, int64_t n, const int64_t
     }
     if (s == TNN_OK)
         s = tnn_build_segments(d_x, n, h_traj_off, n_traj, bp, stream, &ix);
-    // slice c: rows [n c / nc, n (c + 1) / nc); its lists go out on the copy
-    // stream once the search stream has answered it
+    // Slices shrink geometrically (ratio 2/3, about the time a row's lists
+    // take to copy over the time its search takes), so that the copy of one
+    // slice ends under the search of the next; each slice's lists go out on
+    // the copy stream once the search stream has answered it.
+    int64_t bound[65];
+    {
+        double wsum = 0.0, w = 1.0;
+        for (int c = 0; c < nc; ++c, w *= 2.0 / 3.0)
+            wsum += w;
+        double acc = 0.0;
+        w = 1.0;
+        bound[0] = 0;
+        for (int c = 0; c < nc; ++c, w *= 2.0 / 3.0) {
+            acc += w;
+            bound[c + 1] = c + 1 == nc ? n : std::min<int64_t>(n, (int64_t)(n * (acc / wsum)));
+        }
+    }
     for (int c = 0; c < nc && s == TNN_OK; ++c) {
-        const int64_t r0 = n * c / nc, r1 = n * (c + 1) / nc;
+        const int64_t r0 = bound[c], r1 = bound[c + 1];
+        if (r1 <= r0)
+            continue;
         s = tnn_knn(ix, (const float *)(ix->pts + r0), r1 - r0, kp, d_idx + r0 * k,
                     d_d2 + r0 * k, nullptr, stream);
         if (s != TNN_OK)
