@@ -35,8 +35,8 @@ OPS_PER_PAIR = 14
 OPS_PER_KEY = 20
 
 # DRAM bytes (read + write) of one search on the medium workload, summed over
-# k_tnn_grid_search + k_tnn_warp + k_fallback_exact, from the ncu capture
-# summarised in profiles/k_tnn_grid_search_medium.md, with a hash of the
+# k_tnn_grid_search + k_tnn_warp + k_fallback_exact, from an ncu capture of
+# the three kernels on this workload (dram__bytes_read/write.sum), with a hash of the
 # kernel sources it was taken on (stale, and reported as null, once they
 # change) and the tuning of that capture.
 SEARCH_TRAFFIC = {"bytes": (10512384 + 31606016) + (8107264 + 119552) + 115200, "workload": "medium",
