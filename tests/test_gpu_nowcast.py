@@ -249,6 +249,27 @@ def test_gka_forward_matches_oracle():
     np.testing.assert_allclose(uq[ok], rq[ok], rtol=1e-4, atol=1e-4)
 
 
+@pytest.mark.parametrize("k", [5, 48])
+def test_gka_forward_other_context_sizes(k):
+    """Contexts narrower than a warp (two queries per warp) and wider than
+    one (one query per warp, two neighbours per lane) against the oracle."""
+    wl, ix, _, wind = _gka_setup()
+    sig = np.array([0.05, 4.0, 1e-4], np.float32)
+    g = tnn.GKA(sig)
+    gm = tnn.GKAMLP(sig, hidden=16, seed=3)
+    idx, _ = tnn.tnn_knn(ix, k, 600.0)
+    uv = g.forward(ix, wind, idx).cpu().numpy()
+    ref, _ = nc.gka_forward(wl.xyzt, wl.wind, wl.xyzt, idx.cpu().numpy(), np.log(sig.astype(np.float64)))
+    ok = ~np.isnan(ref).any(axis=1)
+    assert np.isnan(uv[~ok]).all()
+    np.testing.assert_allclose(uv[ok], ref[ok], rtol=1e-4, atol=1e-4)
+    w, _ = gm.get_params()
+    lo, hi = wl.xyzt.min(axis=0), wl.xyzt.max(axis=0)
+    um = gm.forward(ix, wind, idx).cpu().numpy()
+    rm = nc.gkamlp_forward(wl.xyzt, wl.wind, wl.xyzt, idx.cpu().numpy(), w, 16, lo, hi)
+    np.testing.assert_allclose(um[ok], rm[ok], rtol=1e-4, atol=1e-4)
+
+
 def test_gka_gradient_and_adam_step_match_oracle():
     wl, ix, idx, wind = _gka_setup()
     idx_h = idx.cpu().numpy()
