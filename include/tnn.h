@@ -273,6 +273,8 @@ tnn_status tnn_profile_read(double *ms, int64_t *launches, int32_t reset);
  *   h_xyzt [n][4] float, h_traj_off [n_traj + 1]: as tnn_build_segments,
  *     host memory (page-locked memory is copied faster).
  *   h_idx [n][k] int32, h_d2 [n][k] float: host outputs, layout as tnn_knn.
+ *   stream: where the copies in, the build and the searches run; the copies
+ *     out run on a second stream the library keeps per device.
  * Device memory: 16 n + 8 n k bytes of scratch and the index, from the
  * library pool; all of it is returned before the call ends.  Synchronous:
  * returns when the outputs are complete.  Errors as tnn_build_segments and
