@@ -96,10 +96,12 @@ def test_mlp_gradients_match_oracle(d_in, dh):
     lr, gr = nc.mlp_grads(_bf16_round(X), T, _bf16_round(W1), b1, W2, b2)
     assert float(loss.item()) == pytest.approx(lr, rel=2e-2)
     gW1, gb1, gW2, gb2 = m.unflatten(g)
+    # element by element: BF16 operands (relative 2^-8 each) and FP32
+    # accumulation over <= 1000 rows; the absolute part is 2e-2 of the
+    # block's largest entry, so one wrong entry cannot hide in a norm
     for name, got in (("W1", gW1), ("b1", gb1), ("W2", gW2), ("b2", gb2)):
         ref = gr[name]
-        rel = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-12)
-        assert rel < 2e-2, (name, rel)
+        np.testing.assert_allclose(got, ref, rtol=2e-2, atol=2e-2 * np.abs(ref).max(), err_msg=name)
 
 
 def test_adamw_step_matches_oracle_update():

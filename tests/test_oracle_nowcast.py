@@ -1,7 +1,8 @@
 """Pins of the nowcast oracle: GELU against the standard normal CDF, the
-MLP gradient against central finite differences, AdamW against its closed
-form under a constant gradient, IDW special cases and a hand-worked
-feature row."""
+MLP forward on a hand-worked 2-2-2 network, the MLP gradient against central
+finite differences, AdamW against its closed form under a constant
+gradient, IDW special cases, a hand-worked feature row, GKA closed forms and
+the GKA-MLP scales on a hand-worked one-unit network."""
 import math
 
 import numpy as np
@@ -179,3 +180,60 @@ def test_gkamlp_gradient_matches_central_differences():
         fd = (nc.gkamlp_loss_grad(pts, wind, rows, idx, pp, H, lo, hi)[0]
               - nc.gkamlp_loss_grad(pts, wind, rows, idx, pm, H, lo, hi)[0]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_mlp_forward_hand_worked_network():
+    # A 2-input, 2-hidden, 2-output network worked by hand (W1 is d_in x
+    # d_hidden, W2 is d_hidden x 2):
+    #   W1 = [[1, -1], [0.5, 2]], b1 = [-1, -4], W2 = [[2, 1], [3, -1]],
+    #   b2 = [0.1, -0.2].
+    # Row x = (1, 2): Z = (1 + 1 - 1, -1 + 4 - 4) = (1, -1), so
+    #   H = (Phi(1), -Phi(-1)) with the normal-table values Phi(1) =
+    #   0.841344746068543, Phi(-1) = 0.158655253931457;
+    #   Y = (2 Phi(1) - 3 Phi(-1) + 0.1, Phi(1) + Phi(-1) - 0.2) = (1.306723730342715, 0.8).
+    # Row x = (0, -1): Z = (-0.5 - 1, -2 - 4) = (-1.5, -6), so
+    #   H = (-1.5 Phi(-1.5), -6 Phi(-6)) with Phi(-1.5) = 0.0668072012688581 and
+    #   Phi(-6) = 9.865876450377e-10: H = (-0.10021080190328715, -5.9195258702262e-9);
+    #   Y = (-0.10042162156515191, -0.30021079598376128).
+    X = np.array([[1.0, 2.0], [0.0, -1.0]])
+    W1 = np.array([[1.0, -1.0], [0.5, 2.0]])
+    b1 = np.array([-1.0, -4.0])
+    W2 = np.array([[2.0, 1.0], [3.0, -1.0]])
+    b2 = np.array([0.1, -0.2])
+    Z, H, Y = nc.mlp_forward(X, W1, b1, W2, b2)
+    np.testing.assert_allclose(Z, [[1.0, -1.0], [-1.5, -6.0]], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(H, [[0.841344746068543, -0.158655253931457],
+                                   [-0.10021080190328715, -5.9195258702262e-9]], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(Y, [[1.306723730342715, 0.8],
+                                   [-0.10042162156515191, -0.30021079598376128]], rtol=1e-12, atol=1e-14)
+
+
+def test_gkamlp_theta_hand_worked_single_hidden_unit():
+    # H = 1 hidden unit.  Bounding box lo = (0, 100, 8), hi = (10, 300, 12);
+    # query (5, 150, 11) -> u = (5/10, 50/200, 3/4) = (0.5, 0.25, 0.75).
+    # W1 = (2, -4, 1)^T, b1 = 0.25: pre-activation 1 - 1 + 0.75 + 0.25 = 1,
+    # h = tanh(1) = 0.7615941559557649.  W2 = (1, -2, 0.5), b2 = (0.1, 0.2, -3):
+    # theta = (0.1 + h, 0.2 - 2h, -3 + h/2)
+    #       = (0.8615941559557649, -1.3231883119115298, -2.6192029220221176).
+    params = np.array([2.0, -4.0, 1.0,   # W1 [3][1]
+                       0.25,             # b1 [1]
+                       1.0, -2.0, 0.5,   # W2 [1][3]
+                       0.1, 0.2, -3.0])  # b2 [3]
+    lo = np.array([0.0, 100.0, 8.0, 0.0], np.float32)
+    hi = np.array([10.0, 300.0, 12.0, 50.0], np.float32)
+    q = np.array([[5.0, 150.0, 11.0, 20.0]], np.float32)
+    theta, h, u = nc.gkamlp_theta(q, params, 1, lo, hi)
+    np.testing.assert_allclose(u, [[0.5, 0.25, 0.75]], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(h, [[0.7615941559557649]], rtol=1e-14)
+    np.testing.assert_allclose(theta, [[0.8615941559557649, -1.3231883119115298, -2.6192029220221176]],
+                               rtol=1e-14)
+    # the nowcast then uses s = exp(theta) in Eq. GKA: one neighbour at
+    # offset (1, 0, 0, 0) and one at (0, 0, 1, 0) weigh exp(-s_xy) and
+    # exp(-s_z) relative to each other
+    pts = np.array([[5.0, 150.0, 11.0, 20.0], [6.0, 150.0, 11.0, 20.0], [5.0, 150.0, 12.0, 20.0]],
+                   np.float32)
+    wind = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]], np.float32)
+    out = nc.gkamlp_forward(pts, wind, q, np.array([[1, 2]], np.int32), params, 1, lo, hi)
+    w1 = math.exp(-math.exp(0.8615941559557649))
+    w2 = math.exp(-math.exp(-1.3231883119115298))
+    np.testing.assert_allclose(out, [[w1 / (w1 + w2), w2 / (w1 + w2)]], rtol=1e-12)
