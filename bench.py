@@ -172,18 +172,87 @@ def _peaks():
         return {}
 
 
-def _cpu_baseline(wl, k, n_sample, seed=0x5A00):
-    """The FP64 oracle as it stands on a bounded sample of the queries."""
+def _parity(gi, gd, oi, od):
+    """Sampled GPU rows against the oracle's: identical neighbour indices
+    (ties by index), and the largest relative error of the reported FP32
+    distance against the FP64 one."""
+    import numpy as np
+    same = bool(np.array_equal(gi, oi))
+    fin = np.isfinite(od)
+    pad_ok = bool(np.array_equal(np.isfinite(gd), fin))
+    err = 0.0
+    if fin.any():
+        err = float(np.max(np.abs(gd[fin].astype(np.float64) - od[fin]) / np.maximum(od[fin], 1e-300)))
+    return {"queries_checked": int(gi.shape[0]), "identical_indices": same and pad_ok,
+            "rows_differing": int((gi != oi).any(axis=1).sum()), "max_rel_d2_err_vs_fp64": err,
+            "tolerance": 1e-5}
+
+
+def _cpu_baseline(wl, k, n_sample, idx=None, d2=None, lag=0.0, seed=0x5A00):
+    """The FP64 oracle as it stands on a bounded sample of the queries, and
+    (given the GPU outputs) the parity of those rows."""
     import oracle
     from paper_2112_10408_gb300 import synth
     q = synth.query_sample(wl.n, n_sample, seed=seed)
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    oracle.knn(wl.xyzt, k, (1.0, 1.0, 10.0, 0.01), lag=0.0, qsel=q, nthreads=cores)
+    oi, od, o64 = oracle.knn(wl.xyzt, k, (1.0, 1.0, 10.0, 0.01), lag=lag, qsel=q, nthreads=cores,
+                             want_d64=True)
     dt = time.perf_counter() - t0
-    return {"value": q.size / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{q.size} uniformly sampled self-queries of the same workload "
-                      f"(FP64 brute force, {cores} threads, {dt:.2f} s)"}
+    out = {"value": q.size / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{q.size} uniformly sampled self-queries of the same workload "
+                     f"(FP64 brute force, {cores} threads, {dt:.2f} s)"}
+    if idx is not None:
+        import torch
+        qt = torch.from_numpy(q).to(idx.device)
+        out["parity"] = _parity(idx[qt].cpu().numpy(), d2[qt].cpu().numpy(), oi, o64)
+    return out
+
+
+def _fp32_peak(tnn, peaks, nsm):
+    """FFMA lane-operations/s measured by the library's probe (best of 3),
+    with the unit-count figure beside it."""
+    best = 0.0
+    for _ in range(3):
+        ops, _ms = tnn.tnn_probe_fp32(1 << 16)
+        best = max(best, ops)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    return best / 1e12, nsm * 128 * sm_max * 1e6 / 1e12
+
+
+def _search_roofline(tnn, ix, k, lag, tune, kern_ms, launches, alu_peak, derived_peak, traffic, out):
+    """Roofline of the search, split by kernel: the necessary work of the
+    queries each kernel finished (tnn_knn_trace + tnn_knn_work_split) over
+    that kernel's own CUDA-event time; the top level is the kernel that
+    takes the larger share."""
+    idx, d2 = out
+    _, _, path = tnn.tnn_knn_trace(ix, k, lag, out=(idx, d2), **tune)
+    split = tnn.tnn_knn_work_split(ix, k, d2, path, lag)
+    names = ["k_tnn_grid_search", "k_tnn_warp", "k_fallback_exact"]
+    per = {}
+    for c, name in enumerate(names):
+        nlb, npairs, nkeys = split[c]
+        ops = OPS_PER_LB * nlb + OPS_PER_PAIR * npairs + OPS_PER_KEY * nkeys
+        ms = kern_ms[c] / max(launches, 1)
+        ach = ops / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+        per[name] = {"ms": ms, "queries": int((path == c).sum().item()),
+                     "lb_needed": nlb, "pairs_needed": npairs, "keys_needed": nkeys,
+                     "achieved": ach, "frac": ach / alu_peak}
+    tot_ops = sum(OPS_PER_LB * split[c][0] + OPS_PER_PAIR * split[c][1] + OPS_PER_KEY * split[c][2]
+                  for c in range(3))
+    tot_ms = sum(kern_ms) / max(launches, 1)
+    dom = max(names[:2], key=lambda n: per[n]["ms"])
+    d = per[dom]
+    return {"bound": "alu", "achieved": d["achieved"], "peak": alu_peak, "unit": "T FP32 lane-ops/s",
+            "frac": d["frac"], "traffic": traffic, "kernel": dom, "kernel_ms": d["ms"],
+            "peak_note": "of measured: FFMA issue rate from tnn_probe_fp32 (best of 3); "
+                         f"unit-count figure {derived_peak:.2f}",
+            "work_note": "necessary work of the queries this kernel finished; ops per unit "
+                         f"{OPS_PER_LB}/{OPS_PER_PAIR}/{OPS_PER_KEY} (bound/pair/key)",
+            "kernels": per,
+            "search": {"ms": tot_ms, "achieved": tot_ops / (tot_ms / 1e3) / 1e12,
+                       "frac": tot_ops / (tot_ms / 1e3) / 1e12 / alu_peak,
+                       "kernels": "k_tnn_grid_search + k_tnn_warp + k_fallback_exact"}}
 
 
 def run_reference(a):
@@ -271,11 +340,48 @@ def _extras(tnn, synth, flush, peaks, steps):
     with _Range("batched"):
         ms = _timed(b.run, steps, flush)
     nq = sum(wl.n for wl, _ in wins)
+    # each window on its own (tnn_knn, same knobs), for the per-window rates
+    per_window = []
+    for w, (wl, kw_) in enumerate(wins):
+        iw, dw = b.idx[w], b.d2[w]
+        tnn.tnn_knn(idxs[w], kw_, 0.0, out=(iw, dw))
+        torch.cuda.synchronize()
+        wms = _timed(lambda: tnn.tnn_knn(idxs[w], kw_, 0.0, out=(iw, dw)), 3, flush)
+        per_window.append({"window": w, "points": wl.n, "k": kw_, "ms": wms,
+                           "contexts_per_s": wl.n / (wms / 1e3)})
+    b.run()  # the batched outputs again, for the parity sample below
+    torch.cuda.synchronize()
+    # the oracle on 64 sampled queries per window (host cores), and the
+    # parity of those rows of the batched outputs
+    import numpy as np
+    import oracle
+    cores = os.cpu_count() or 1
+    gi_all, gd_all, oi_all, od_all = [], [], [], []
+    t0 = time.perf_counter()
+    for w, (wl, kw_) in enumerate(wins):
+        q = synth.query_sample(wl.n, 64, seed=0x5A00 + w)
+        oi, od, o64 = oracle.knn(wl.xyzt, kw_, sigma, qsel=q, nthreads=cores, want_d64=True)
+        qt = torch.from_numpy(q).cuda()
+        gi = b.idx[w][qt].cpu().numpy()
+        gd = b.d2[w][qt].cpu().numpy()
+        pad = 64 - kw_
+        gi_all.append(np.pad(gi, ((0, 0), (0, pad)), constant_values=-2))
+        oi_all.append(np.pad(oi, ((0, 0), (0, pad)), constant_values=-2))
+        gd_all.append(np.pad(gd, ((0, 0), (0, pad)), constant_values=np.inf))
+        od_all.append(np.pad(o64, ((0, 0), (0, pad)), constant_values=np.inf))
+    dt = time.perf_counter() - t0
+    nsq = 64 * len(wins)
     out["batched"] = {"metric": "causal k-NN contexts/s over 64 windows in one persistent launch",
                       "value": nq / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "windows": len(wins),
                       "queries": nq, "k_mix": {str(k): sum(1 for _, kk in wins if kk == k) for k in (16, 32, 64)},
                       "launch": "tnn_batch_run: one CUDA graph (tile kernel + warp kernel + exact kernel)",
-                      "tuning": "library defaults"}
+                      "tuning": "library defaults",
+                      "per_window": per_window,
+                      "per_window_note": "each window alone through tnn_knn (L2 flushed), same knobs",
+                      "cpu_baseline": {"value": nsq / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                       "sample": f"64 sampled self-queries per window ({nsq}), FP64 brute force",
+                                       "parity": _parity(np.concatenate(gi_all), np.concatenate(gd_all),
+                                                         np.concatenate(oi_all), np.concatenate(od_all))}}
     b.destroy()
     for ix in idxs:
         ix.destroy()
@@ -362,6 +468,25 @@ def _extras(tnn, synth, flush, peaks, steps):
     torch.cuda.synchronize()
     ms_now = _timed(lambda: tnn.tnn_nowcast(ix, wind, k, lag, q=qte, mlp=mlp, mean=mean, std=std, **tune),
                     steps, flush)
+    # the same held-out queries with the IDW fallback (no MLP): latency and
+    # RMSE side by side with the MLP (matched query count, same search)
+    tnn.tnn_nowcast(ix, wind, k, lag, q=qte, **tune)
+    torch.cuda.synchronize()
+    ms_now_idw = _timed(lambda: tnn.tnn_nowcast(ix, wind, k, lag, q=qte, **tune), steps, flush)
+    now_idw = tnn.tnn_nowcast(ix, wind, k, lag, q=qte, **tune)
+    now_mlp = tnn.tnn_nowcast(ix, wind, k, lag, q=qte, mlp=mlp, mean=mean, std=std, **tune)
+    okq = torch.isfinite(now_idw).all(dim=1)
+    rmse_now_idw = float(torch.sqrt(((now_idw[okq] - wind[ted][okq]) ** 2).mean()))
+    rmse_now_mlp = float(torch.sqrt(((now_mlp[okq] - wind[ted][okq]) ** 2).mean()))
+    # the averaging baselines of Table 2: hour average [t - 1 h 30, t - 30 min]
+    # (causal) and day average (non-causal, every point)
+    hour = tnn.tnn_window_average(ix, wind, 5400.0, 1800.0, q=qte)
+    torch.cuda.synchronize()
+    ms_hour = _timed(lambda: tnn.tnn_window_average(ix, wind, 5400.0, 1800.0, q=qte), steps, flush)
+    hok = torch.isfinite(hour).all(dim=1)
+    rmse_hour = float(torch.sqrt(((hour[hok] - wind[ted][hok]) ** 2).mean()))
+    day = tnn.tnn_window_average(ix, wind, float("inf"), float("-inf"), q=qte)
+    rmse_day = float(torch.sqrt(((day - wind[ted]) ** 2).mean()))
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     bf16 = float(peaks.get("bf16_tflops", 1900.0))
     # GKA-TNN (Eq. GKA): scales trained by Adam on the training rows
@@ -479,6 +604,14 @@ def _extras(tnn, synth, flush, peaks, steps):
                                      "peak_note": "of measured bf16 burst; hbm_frac: X read + Y written over measured hbm_gbs"}},
         "nowcast_e2e": {"value": qte.shape[0] / (ms_now / 1e3), "unit": "nowcasts/s", "ms": ms_now,
                         "queries": int(qte.shape[0]), "includes": "tnn_nowcast: search + features + MLP"},
+        "matched_latency": {
+            "queries": int(qte.shape[0]), "includes": "tnn_nowcast on the held-out queries, same search",
+            "mlp": {"ms": ms_now, "nowcasts_per_s": qte.shape[0] / (ms_now / 1e3), "rmse_ms": rmse_now_mlp},
+            "idw": {"ms": ms_now_idw, "nowcasts_per_s": qte.shape[0] / (ms_now_idw / 1e3),
+                    "rmse_ms": rmse_now_idw},
+            "mlp_extra_ms": ms_now - ms_now_idw},
+        "hour_average": {"value": qte.shape[0] / (ms_hour / 1e3), "unit": "nowcasts/s", "ms": ms_hour,
+                         "window": "[t - 5400 s, t - 1800 s]", "queries_with_data": int(hok.sum())},
         "gka": {"forward": {"value": qte.shape[0] / (ms_gka / 1e3), "unit": "nowcasts/s", "ms": ms_gka,
                             "cpu_baseline": _cpu(c_gka, "nowcasts/s"),
                             "roofline": {"bound": "hbm", "achieved": gka_bytes / (ms_gka / 1e3) / 1e9,
@@ -501,10 +634,123 @@ def _extras(tnn, synth, flush, peaks, steps):
                     "train_step": {"value": B / (ms_gm_train / 1e3), "unit": "samples/s", "ms": ms_gm_train,
                                    "batch": B, "steps": len(mbatches), "hidden": 32}},
         "rmse_ms": {"mlp": rmse_mlp, "idw": rmse_idw, "gka": rmse_gka, "gka_mlp": rmse_gm,
+                    "hour_average": rmse_hour, "day_average": rmse_day,
+                    "hour_average_rows": int(hok.sum()),
                     "held_out_rows": int(te.size),
                     "note": "synthetic wind field; noise floor 1 m/s per component (parity unpinned)"}}
     ix.destroy()
     return out
+
+
+def _precision(tnn, synth, flush, steps, alu_peak, derived_peak, cpu=True):
+    """The precision workload: 20,000 flights x 200 samples = 4,000,000
+    points, k = 32, every point a query; FP32 screening with certified
+    margins and an FP64 recheck of the candidates inside the margin of the
+    k-th distance.  Reports its rate, the per-kernel roofline, the margin
+    fraction and the error against the FP64 oracle on 4,096 sampled queries,
+    and the tensor-core linear search on a query sample."""
+    import torch
+    sigma = (1.0, 1.0, 10.0, 0.01)
+    wl = synth.precision()
+    k, K = 32, 20
+    ix = tnn.tnn_build_segments(torch.from_numpy(wl.xyzt).cuda(), wl.traj_off, sigma, K)
+    tune = tnn.tnn_autotune(ix, k, 0.0)
+    idx = torch.empty((wl.n, k), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((wl.n, k), dtype=torch.float32, device="cuda")
+
+    def step():
+        tnn.tnn_knn(ix, k, 0.0, out=(idx, d2), **tune)
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    tnn.tnn_profile_read(reset=True)
+    tnn.tnn_profile_enable(True)
+    with _Range("precision_search"):
+        ms = _timed(step, steps, flush)
+    tnn.tnn_profile_enable(False)
+    kern, launches = tnn.tnn_profile_read_kernels(reset=True)
+    _, _, st = tnn.tnn_knn(ix, k, 0.0, stats=True, out=(idx, d2), **tune)
+    roof = _search_roofline(tnn, ix, k, 0.0, tune, kern, launches, alu_peak, derived_peak, None, (idx, d2))
+    # tensor-core linear search on 131,072 queries spread over the workload
+    import numpy as np
+    qs = np.linspace(0, wl.n - 1, 131072).astype(np.int64)
+    qd = torch.from_numpy(wl.xyzt[qs].copy()).cuda()
+    bi = torch.empty((qd.shape[0], k), dtype=torch.int32, device="cuda")
+    bd = torch.empty_like(bi, dtype=torch.float32)
+    tnn.tnn_knn_bruteforce(ix, k, 0.0, q=qd, out=(bi, bd))
+    torch.cuda.synchronize()
+    cms = _timed(lambda: tnn.tnn_knn_bruteforce(ix, k, 0.0, q=qd, out=(bi, bd)), 2, flush)
+    same = bool(torch.equal(bi, idx[torch.from_numpy(qs).cuda()]))
+    out = {"workload": "precision-4M: 20,000 synthetic flights x 200 samples = 4,000,000 points, "
+                       "self-query of every point, k = 32, 20-point segments",
+           "metric": "causal k-NN contexts/s (exact, k=32)", "value": wl.n / (ms / 1e3), "unit": UNIT,
+           "ms_per_step": ms, "steps": steps, "tuning": tune,
+           "distance_form": "FP32 direct differences with certified bounds, FP64 settlement of "
+                            "candidates within the margin of the k-th distance",
+           "margin": {"fp64_rechecks": st["fp64_rechecks"], "queries": st["queries"],
+                      "rechecks_per_query": st["fp64_rechecks"] / max(st["queries"], 1),
+                      "fraction_of_candidates": st["fp64_rechecks"] / max(st["pairs"], 1),
+                      "pairs": st["pairs"], "exact_queries": st["exact_queries"]},
+           "roofline": roof,
+           "comparator_tensor_core": {"queries": int(qd.shape[0]), "ms": cms,
+                                      "contexts_per_s": qd.shape[0] / (cms / 1e3),
+                                      "tnn_speedup": (wl.n / (ms / 1e3)) / (qd.shape[0] / (cms / 1e3)),
+                                      "identical_neighbours": same},
+           "stats_per_step": st}
+    if cpu:
+        out["cpu_baseline"] = _cpu_baseline(wl, k, 4096, idx, d2)
+        out["max_rel_d2_err_vs_fp64"] = out["cpu_baseline"]["parity"]["max_rel_d2_err_vs_fp64"]
+    ix.destroy()
+    del idx, d2, bi, bd
+    torch.cuda.empty_cache()
+    return out
+
+
+def _e2e_breakdown(tnn, wl, k, K, sigma, tune, h_x, h_i, h_d, reps=5):
+    """Where the end-to-end time goes: the stages tnn_knn_host runs, timed
+    one after another (no overlap), then tnn_knn_host with 1-4 slices."""
+    import torch
+    m = wl.n
+    d_x = torch.empty((m, 4), dtype=torch.float32, device="cuda")
+    idx = torch.empty((m, k), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((m, k), dtype=torch.float32, device="cuda")
+    stages = {"h2d": [], "build": [], "search": [], "d2h": []}
+    for rep in range(reps + 1):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        d_x.copy_(h_x, non_blocking=True)
+        ev[1].record()
+        ix = tnn.tnn_build_segments(d_x, wl.traj_off, sigma, K)
+        ev[2].record()
+        tnn.tnn_knn(ix, k, 0.0, out=(idx, d2), **tune)
+        ev[3].record()
+        h_i.copy_(idx, non_blocking=True)
+        h_d.copy_(d2, non_blocking=True)
+        ev[4].record()
+        torch.cuda.synchronize()
+        ix.destroy()
+        if rep:
+            for i, name in enumerate(stages):
+                stages[name].append(ev[i].elapsed_time(ev[i + 1]))
+    slices = {}
+    for nc in (1, 2, 3, 4):
+        ts = []
+        for rep in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            tnn.tnn_knn_host(h_x, wl.traj_off, sigma, K, k, 0.0, chunks=nc, out=(h_i, h_d), **tune)
+            e1.record()
+            torch.cuda.synchronize()
+            if rep:
+                ts.append(e0.elapsed_time(e1))
+        slices[str(nc)] = sum(ts) / len(ts)
+    st = {name: sum(v) / len(v) for name, v in stages.items()}
+    return {"stages_ms": st, "stages_sum_ms": sum(st.values()), "d2h_GB_per_s": m * k * 8 / st["d2h"] / 1e6,
+            "tnn_knn_host_ms_by_slices": slices,
+            "note": "stages one after another, no overlap; tnn_knn_host overlaps a slice's copy-out "
+                    "with the next slice's search"}
 
 
 def run_ours(a):
@@ -568,7 +814,7 @@ def run_ours(a):
             ev[s][1].record()
         torch.cuda.synchronize()
     tnn.tnn_profile_enable(False)
-    kern_ms, launches = tnn.tnn_profile_read(reset=True)
+    kern3, launches = tnn.tnn_profile_read_kernels(reset=True)
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
@@ -576,26 +822,17 @@ def run_ours(a):
     ms_step = total_ms / max(a.steps, 1)
     value = _throughput(world, m, a.steps, total_ms)
 
-    # executed and necessary work of one pass (outside the timed region)
+    # executed and necessary work of one pass (outside the timed region),
+    # attributed to the kernel that finished each query
     _, _, st = tnn.tnn_knn(ix, k, 0.0, stats=True, out=(idx, d2), **tune)
-    nlb, npairs, nkeys = tnn.tnn_knn_work(ix, k, d2, 0.0)
-    kern_avg_ms = kern_ms / max(launches, 1)
-    alg_ops = OPS_PER_LB * nlb + OPS_PER_PAIR * npairs + OPS_PER_KEY * nkeys
     peaks = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
-    alu_peak = nsm * 128 * sm_max * 1e6 / 1e12  # T FP32 lane-ops/s
-    achieved = alg_ops / (kern_avg_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "T FP32 lane-ops/s",
-                "frac": achieved / alu_peak, "traffic": _search_traffic(a.workload),
-                "traffic_note": "ncu capture at tuning %s" % SEARCH_TRAFFIC["tuning"],
-                "kernel": "search = k_tnn_grid_search + k_tnn_warp + k_fallback_exact",
-                "kernel_ms": kern_avg_ms,
-                "peak_note": f"{nsm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived, not measured)",
-                "work_per_launch": {"lb_needed": nlb, "pairs_needed": npairs, "keys_needed": nkeys,
-                                    "lb_executed": st["lb_evals"], "pairs_executed": st["pairs"],
-                                    "ops_per_lb": OPS_PER_LB, "ops_per_pair": OPS_PER_PAIR,
-                                    "ops_per_key": OPS_PER_KEY}}
+    alu_peak, derived_peak = _fp32_peak(tnn, peaks, nsm)
+    roofline = _search_roofline(tnn, ix, k, 0.0, tune, kern3, launches, alu_peak, derived_peak,
+                                _search_traffic(a.workload), (idx, d2))
+    roofline["traffic_note"] = ("ncu dram bytes of the dominant kernel at tuning %s (null: kernel "
+                                "changed since the capture)" % SEARCH_TRAFFIC["tuning"])
+    roofline["executed"] = {"lb": st["lb_evals"], "pairs": st["pairs"]}
 
     # comparator: linear search on the same queries, distance tiles on the
     # tensor cores (default) and on the CUDA cores (ffma)
@@ -633,6 +870,13 @@ def run_ours(a):
                 ent["tensor"] = {"tiles": tiles, "achieved_tflops": tf, "tf32_peak_tflops": tf32_peak,
                                  "frac": tf / tf32_peak,
                                  "peak_note": "of measured: bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"}
+            if ffma:
+                # direct FP32 differences: every causal pair costs a distance,
+                # a mask and a compare
+                ach = OPS_PER_PAIR * cst["pairs"] / (cmean / 1e3) / 1e12
+                ent["alu"] = {"achieved": ach, "peak": alu_peak, "unit": "T FP32 lane-ops/s",
+                              "frac": ach / alu_peak, "ops_per_pair": OPS_PER_PAIR,
+                              "peak_note": "of measured FFMA issue rate"}
             comparator[name] = ent
 
     # end to end through the C ABI on host buffers (tnn_knn_host): pinned
@@ -656,14 +900,22 @@ def run_ours(a):
            "ms_per_step": e2e_avg,
            "includes": "tnn_knn_host: H2D points, index build, search, D2H results (pinned host buffers)"}
 
-    extras = None
-    if rank == 0 and world == 1 and not a.no_extras:
-        from paper_2112_10408_gb300 import synth
-        extras = _extras(tnn, synth, flush, _peaks(), max(3, min(a.steps, 20)))
+    e2e_break = None
+    if rank == 0 and world == 1 and a.e2e_steps > 0:
+        e2e_break = _e2e_breakdown(tnn, wl, k, K, sigma, tune, h_x, h_i, h_d)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        cpu = _cpu_baseline(wl, k, 8192 if a.workload != "tiny" else wl.n)
+        cpu = _cpu_baseline(wl, k, 8192 if a.workload != "tiny" else wl.n, idx, d2)
+
+    extras = None
+    if rank == 0 and world == 1 and not a.no_extras:
+        from paper_2112_10408_gb300 import synth
+        nsteps = max(3, min(a.steps, 20))
+        extras = _extras(tnn, synth, flush, _peaks(), nsteps)
+        if a.workload != "precision":
+            extras["precision"] = _precision(tnn, synth, flush, nsteps, alu_peak, derived_peak,
+                                             cpu=not a.no_cpu_baseline)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -673,7 +925,7 @@ def run_ours(a):
                               parallelism=f"replicas x{world}: each rank its own window"),
                "clocks": clocks, "e2e": e2e, "gpu_launches": 3 * a.steps,
                "roofline": roofline, "cpu_baseline": cpu, "comparator": comparator,
-               "stats_per_step": st}
+               "stats_per_step": st, "e2e_breakdown": e2e_break}
         if extras:
             out.update(extras)
         print(json.dumps(out))

@@ -171,9 +171,10 @@ typedef struct {
  *           indexed point is a query (m must equal n_points).
  *   d_idx   [m][k] int32 out, d_d2 [m][k] float out (device).
  *   h_stats optional; when non-NULL the call SYNCHRONISES `stream`, fills
- *           the counters and reports what the kernels flagged: a device
- *           wait that timed out (TNN_ERR_TIMEOUT; the outputs are then
- *           incomplete) or an internal list overflow (TNN_ERR_CUDA).
+ *           the counters and reports what the kernels flagged (see
+ *           tnn_sync_status).  Without it the call does not wait, and a flag
+ *           raised by its kernels is reported by the next call that
+ *           synchronises and checks the device's fault word.
  * Device scratch (a few bytes per query) is taken from the stream-ordered
  * allocator and released on the stream.
  */
@@ -207,16 +208,20 @@ tnn_status tnn_knn_bruteforce(const tnn_index *index, const float *d_q,
  * paper has no counterpart: this is a deployment variant of tnn_knn.)
  * Arguments and results as tnn_knn, without statistics.  It allocates
  * nothing: its scratch -- work-queue counter, counters and the lists of
- * queries handed to the fallback scans, 1 MiB + 256 B -- is a static array
- * of this library in device memory, held by every GPU that loads the
- * library until the process exits.
+ * queries handed to the fallback scans, 256 B + 20 B x 65,536 = 1,310,976 B
+ * (1.25 MiB + 256 B) -- is a static array of this library in device memory,
+ * held by every GPU that loads the library until the process exits.
  *  - At most 65,536 queries per call (TNN_ERR_INVALID_ARG beyond, before any
  *    device work); answer more by calling it on slices of the queries.
  *  - The first call on a device looks up the array's device address, with
- *    that device current; make that first call before any stream capture.
+ *    that device current, and keeps it; make that first call before any
+ *    stream capture.  After cudaDeviceReset the kept address is stale: do not
+ *    call it again in that process.
  *  - Every call uses the same array and clears its counters first: calls
  *    whose work overlaps on the GPU (other streams, other threads) race and
  *    corrupt each other's results.  Order them, e.g. on one stream.
+ *  - It does not wait for its kernels; what they flag is reported by
+ *    tnn_sync_status (or any other call that checks the fault word).
  */
 tnn_status tnn_knn_noalloc(const tnn_index *index, const float *d_q, int64_t m,
                            const tnn_knn_params *params, int32_t *d_idx,
@@ -251,14 +256,82 @@ tnn_status tnn_knn_work(const tnn_index *index, const float *d_q, int64_t m,
                         uint64_t *h_work, tnn_stream_t stream);
 
 /*
+ * tnn_knn_work per kernel: the same sums, split by the kernel that finished
+ * each query.  d_path [m] (uint8, device) as tnn_knn_trace writes it, or
+ * NULL (every query in class 0).  h_work [3][3]: row c = the three sums of
+ * tnn_knn_work over the queries of class c.  Synchronises `stream`.
+ */
+tnn_status tnn_knn_work_split(const tnn_index *index, const float *d_q, int64_t m,
+                              int32_t k, double lag, const float *d_d2,
+                              const uint8_t *d_path, uint64_t *h_work,
+                              tnn_stream_t stream);
+
+/*
+ * tnn_knn (without statistics) that also records, per query, which kernel
+ * finished it: d_path [m] (uint8, device) = 0 for the 32-query tile kernel,
+ * 1 for the warp-per-query kernel (queries deferred from their tile, or whose
+ * tie chain needed a longer list), 2 for the FP64 definition.  For
+ * measurement tools (it attributes the necessary work to the kernels) and
+ * tests.  d_seen (optional, grid order only): [m][(n_points + 31) / 32]
+ * uint32 (device), zeroed by the call; bit j of row q is set when the
+ * search scanned the segment holding point j for query q (the FP64
+ * definition, path 2, records nothing) -- the segments it skipped are those
+ * its stop rule and exclusion criterion certified.
+ */
+tnn_status tnn_knn_trace(const tnn_index *index, const float *d_q, int64_t m,
+                         const tnn_knn_params *params, int32_t *d_idx, float *d_d2,
+                         uint8_t *d_path, uint32_t *d_seen, tnn_stream_t stream);
+
+/*
  * Kernel timing for measurement tools.  While enabled, every launch of the
  * search kernels (TNN or linear search) is bracketed by CUDA events recorded
- * on the stream it is launched on.  tnn_profile_read synchronises on those
- * events and returns the summed device time in ms and the number of
- * launches since the last reset (reset != 0 clears them).
+ * on the stream it is launched on: before the main kernel, before the
+ * warp-per-query kernel, before the FP64 kernel and after it.
+ * tnn_profile_read synchronises on those events and returns the summed
+ * device time in ms and the number of launches since the last reset
+ * (reset != 0 clears them); tnn_profile_read_kernels returns the three
+ * kernels' times separately, h_ms [3] = (main kernel -- the tile kernel, or
+ * the query order and the linear-search kernel --, warp-per-query kernel,
+ * FP64 kernel).
  */
 tnn_status tnn_profile_enable(int32_t on);
 tnn_status tnn_profile_read(double *ms, int64_t *launches, int32_t reset);
+tnn_status tnn_profile_read_kernels(double *h_ms, int64_t *launches, int32_t reset);
+
+/*
+ * FP32 issue throughput of this GPU, measured: every SM runs warps of
+ * independent FFMA chains (`iters` fused multiply-adds per chain, 8 chains
+ * per thread) and the launch is timed with CUDA events on `stream`.
+ * *h_lane_ops = FFMA lane-operations per second (one per thread and
+ * instruction); *h_ms = the launch's duration.  The roofline peak of the
+ * ALU-bound search kernels.  Synchronises `stream`.
+ */
+tnn_status tnn_probe_fp32(int32_t iters, double *h_lane_ops, double *h_ms,
+                          tnn_stream_t stream);
+
+/* ------------------------------------------------------ device faults */
+
+/*
+ * Device-side faults.  The search kernels flag what they cannot recover
+ * from -- a bounded device wait that expired (1 s), an internal list that
+ * overflowed -- in a fault word of the device, kept until reported.
+ * tnn_sync_status synchronises `stream`, then reports and clears that word:
+ * TNN_ERR_TIMEOUT for an expired wait, TNN_ERR_CUDA for an overflow (the
+ * outputs of the flagged search are incomplete), TNN_OK otherwise.  The
+ * calls that synchronise anyway check it too: tnn_knn and
+ * tnn_knn_bruteforce with statistics, tnn_batch_stats, tnn_autotune,
+ * tnn_knn_host.
+ */
+tnn_status tnn_sync_status(tnn_stream_t stream);
+
+/*
+ * Self-test of that path (the paper has no counterpart): one warp waits, at
+ * most limit_us microseconds (1..10^6), on an mbarrier that nothing arrives
+ * on -- with no copy or tensor-core operation in flight -- then raises the
+ * timeout flag as an expired wait of the search kernels does.  The next
+ * tnn_sync_status on `stream` returns TNN_ERR_TIMEOUT.  Asynchronous.
+ */
+tnn_status tnn_selftest_bounded_wait(int32_t limit_us, tnn_stream_t stream);
 
 /* -------------------------------------------------------- host pipeline */
 
@@ -315,6 +388,8 @@ typedef struct tnn_batch tnn_batch;
  *   d_d2[w]: as tnn_knn, per window.  The arrays are read at creation; the
  *   device buffers must stay valid while the batch is run.
  * The launch is captured once into a CUDA graph; tnn_batch_run replays it.
+ * This is the batched k-NN call of the library (create once, run many
+ * times).
  */
 tnn_status tnn_batch_create(const tnn_index *const *indexes,
                             const float *const *d_q, const int64_t *m,
@@ -365,6 +440,20 @@ tnn_status tnn_context_features(const tnn_index *index, const float *d_wind,
                                 uint16_t *d_feat, float *d_idw,
                                 tnn_stream_t stream);
 
+/*
+ * The averaging baselines of the nowcasting comparison (Sec. 4.1, Table 2):
+ * d_uv [m][2] = the mean wind (u, v) of every indexed point measured in
+ *     t_q - before_lo <= t_j <= t_q - before_hi      (FP64 comparisons)
+ * NaN where no point falls in that window.  before_lo = 5400, before_hi =
+ * 1800 is the paper's hour average over [t - 1 h 30, t - 30 min];
+ * before_lo = +inf, before_hi = -inf the (non-causal) day average.  d_wind
+ * [n_points][2] float (device), d_q [m][4] queries or NULL (self-query).
+ * Scratch (16 B per indexed point) from the stream-ordered allocator.
+ */
+tnn_status tnn_window_average(const tnn_index *index, const float *d_wind,
+                              const float *d_q, int64_t m, double before_lo,
+                              double before_hi, float *d_uv, tnn_stream_t stream);
+
 typedef struct tnn_mlp tnn_mlp;
 
 typedef struct {
@@ -395,6 +484,17 @@ tnn_status tnn_mlp_get_params(const tnn_mlp *mlp, float *h_params,
 tnn_status tnn_mlp_set_params(tnn_mlp *mlp, const float *h_params,
                               const float *h_m, const float *h_v,
                               int64_t step);
+/*
+ * Checkpoint: tnn_mlp_save writes the parameters, both AdamW moments and the
+ * step to `path`; tnn_mlp_load reads such a file into an MLP of the same
+ * d_in and d_hidden (TNN_ERR_INVALID_ARG for another shape, a foreign or a
+ * truncated file).  Format, little-endian on every host: int64 magic
+ * 0x544E4E4D ("TNNM"), int64 version 1, int64 d_in, int64 d_hidden, int64
+ * step, then P float32 parameters (flat layout above), P float32 first
+ * moments, P float32 second moments.  Both synchronise the device.
+ */
+tnn_status tnn_mlp_save(const tnn_mlp *mlp, const char *path);
+tnn_status tnn_mlp_load(tnn_mlp *mlp, const char *path);
 /* y [B][2] = MLP(x), x [B][d_in] bf16 (device, 16-byte aligned).  Needs no
    workspace. */
 tnn_status tnn_mlp_forward(const tnn_mlp *mlp, const uint16_t *d_x, int64_t B,

@@ -23,6 +23,10 @@ aggregators written here are the readings used by this project:
   neighbours with w_k = exp(-(s_xy ((x - x_k)^2 + (y - y_k)^2)
   + s_z (z - z_k)^2 + s_t (t - t_k)^2)); the parameters are theta = log(s)
   (s_xy, s_z, s_t > 0), trained with Adam on the same mean squared error.
+* window average (Sec. 4.1, Table 2 "Hour Average"): the mean wind of every
+  point measured in [t_q - before_lo, t_q - before_hi], closed at both ends
+  as the paper writes [t - 1h30; t - 30min]; NaN for an empty window; the
+  day average is the same mean over every point.
 * GKA-MLP (Sec. 3.2: the scales as a function of the location): per query
   theta(q) = tanh(u W1 + b1) W2 + b2 with u = (q_xyz - lo) / (hi - lo) the
   location normalised by the points' bounding box, then GKA with
@@ -72,6 +76,25 @@ def idw(d2, idx, wind, eps: float = 1e-6):
     den = w.sum(axis=1)
     with np.errstate(invalid="ignore", divide="ignore"):
         return num / den[:, None]
+
+
+def window_average(pts, wind, queries, before_lo: float = 5400.0, before_hi: float = 1800.0,
+                   chunk: int = 256):
+    """Mean wind [m, 2] (float64) of the points j with
+    t_q - before_lo <= t_j <= t_q - before_hi, compared in float64 on the
+    float32 times; a plain masked mean over all points for every query."""
+    t = np.asarray(pts, dtype=np.float32)[:, 3].astype(np.float64)
+    w = np.asarray(wind, dtype=np.float32).astype(np.float64)
+    tq = np.asarray(queries, dtype=np.float32)[:, 3].astype(np.float64)
+    out = np.full((tq.shape[0], 2), np.nan)
+    for a in range(0, tq.shape[0], chunk):
+        q = tq[a:a + chunk, None]
+        mask = (t[None, :] >= q - before_lo) & (t[None, :] <= q - before_hi)
+        cnt = mask.sum(axis=1)
+        s = mask.astype(np.float64) @ w
+        ok = cnt > 0
+        out[a:a + chunk][ok] = s[ok] / cnt[ok, None]
+    return out
 
 
 def gelu(z):

@@ -295,6 +295,15 @@ __device__ __forceinline__ void seg_points_store(const SegPoints &sp, float4 *pb
         pbuf[lane + 32] = sp.b;
 }
 
+// Tests only: record that the distances of points [first, first + cnt) to
+// query `row` were taken (the segment was scanned for it).
+__device__ __forceinline__ void dbg_mark_seen(const KnnLaunch &L, int64_t row, int first, int cnt)
+{
+    uint32_t *r = L.dbg_seen + row * L.dbg_words;
+    for (int j = first; j < first + cnt; ++j)
+        atomicOr(r + (j >> 5), 1u << (j & 31));
+}
+
 struct LaneStats {
     unsigned long long q, lb, pairs, segs, fp64;
 };

@@ -189,6 +189,8 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_WARP_MINB)
         auto scan_seg = [&](int first, int cnt) {
             if (lane == 0)
                 st.segs++;
+            if (L.dbg_seen && lane == 0)
+                dbg_mark_seen(L, ent.y, first, cnt);
             for (int o = 0; o < cnt; o += 32) {
                 const int j = o + lane;
                 unsigned long long ck = SENT;
@@ -218,6 +220,8 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_WARP_MINB)
                 const int rank = __popc(m & ((1u << lane) - 1u));
                 Sstart[rank] = incl - cnt;
                 Sfirst[rank] = __float_as_int(meta.x);
+                if (L.dbg_seen)
+                    dbg_mark_seen(L, ent.y, __float_as_int(meta.x), cnt);
             }
             if (lane == 0)
                 st.segs += nseg;
@@ -440,9 +444,23 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_WARP_MINB)
         L.scr->stats[5] = nfb;
 }
 
+// Fault flags of the search launches on this device (the bits of
+// KnnScratch::status: 1 and 2 a fallback list overflowed, 4 a bounded wait
+// timed out), ORed in by the last kernel of every search and kept until a
+// synchronising call reports and clears them (tnn_sync_status).  Searches
+// without statistics and tnn_knn_noalloc report through it.
+static __device__ unsigned int g_search_fault;
+
 __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
     k_fallback_exact(const __grid_constant__ KnnLaunch L)
 {
+    // The kernels before this one on the stream have completed: their flags
+    // are final.  Nothing below sets a flag.
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned f = *(volatile unsigned *)&L.scr->status;
+        if (f)
+            atomicOr(&g_search_fault, f);
+    }
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int kmax = L.L_max;

@@ -114,6 +114,8 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_GRID_MINB)
                 return;
             st.segs++;
             st.pairs += cnt;
+            if (L.dbg_seen)
+                dbg_mark_seen(L, qrow, first, cnt);
             // newest member first: along a trajectory the members nearest a
             // later query come last, and keys arriving in ascending order
             // make the sorted insertion an append

@@ -126,6 +126,8 @@ extern "C" tnn_status tnn_knn_host(const float *h_xyzt, int64_t n, const int64_t
                       cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
         s = TNN_ERR_CUDA;
     }
+    if (s == TNN_OK)
+        s = tnn_take_search_faults(st);
     for (int c = 0; c <= nc; ++c)
         if (ev[c])
             cudaEventDestroy(ev[c]);

@@ -144,6 +144,9 @@ struct KnnLaunch {
                           // tile kernel handed it over (parallel to fb_list)
     const unsigned long long *qorder; // tensor-core linear search: sorted
                                       // (space-time key << 32 | query row)
+    uint32_t *dbg_seen;   // tests only (tnn_knn_trace), else NULL: bit j of
+                          // row q = point j's distance to query q was taken
+    int64_t dbg_words;    // 32-bit words per row of dbg_seen
 };
 
 // Ascending sort of n2 (a power of two, >= 2048) 64-bit keys in place
@@ -168,5 +171,10 @@ tnn_status tnn_launch_search(const KnnLaunch &L, bool brute,
                              cudaStream_t stream);
 size_t tnn_search_smem_per_warp(int L_max, int kseg_max, int mode);
 
+// Search faults flagged on the device since the last report: synchronise
+// `st`, then read and clear the device's fault word (tnn_knn.cu).
+tnn_status tnn_take_search_faults(cudaStream_t st);
+
 #define TNN_WARPS_PER_CTA 4
 #define TNN_TILE 32
+#define TNN_MAX_DEVICES 64

@@ -51,6 +51,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "tnn_internal.cuh"
@@ -82,25 +83,30 @@ __global__ void k_segment_lb(const __grid_constant__ KnnWin W, float *out)
 static int g_num_sms = 0;
 static int g_smem_per_sm = 0; // shared memory of one SM (bytes)
 
-// ---- kernel timing for measurement tools (tnn_profile_*)
+// ---- kernel timing for measurement tools (tnn_profile_*): four events per
+// search launch, on its stream -- before the main kernel (tile kernel, or
+// query order + tensor-core kernel), before the warp-per-query kernel,
+// before the exact kernel, after it.
+struct ProfEv {
+    cudaEvent_t e[4];
+};
 static bool g_prof_on = false;
-static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_ev; // recorded pairs
-static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_pool; // free pairs
+static std::vector<ProfEv> g_prof_ev;   // recorded
+static std::vector<ProfEv> g_prof_pool; // free
 
-static cudaError_t prof_begin(cudaStream_t st, std::pair<cudaEvent_t, cudaEvent_t> *pr)
+static cudaError_t prof_begin(cudaStream_t st, ProfEv *pr)
 {
     if (!g_prof_pool.empty()) {
         *pr = g_prof_pool.back();
         g_prof_pool.pop_back();
     } else {
-        cudaError_t e = cudaEventCreate(&pr->first);
-        if (e != cudaSuccess)
-            return e;
-        e = cudaEventCreate(&pr->second);
-        if (e != cudaSuccess)
-            return e;
+        for (int i = 0; i < 4; ++i) {
+            cudaError_t e = cudaEventCreate(&pr->e[i]);
+            if (e != cudaSuccess)
+                return e;
+        }
     }
-    return cudaEventRecord(pr->first, st);
+    return cudaEventRecord(pr->e[0], st);
 }
 
 static tnn_status device_setup()
@@ -116,8 +122,16 @@ static tnn_status device_setup()
     }
     g_num_sms = prop.multiProcessorCount;
     g_smem_per_sm = (int)prop.sharedMemPerMultiprocessor;
-    static bool attrs = false;
-    if (!attrs) {
+    // The shared-memory limit of a kernel is a per-device attribute: raised
+    // once on every device that runs a search.
+    static std::mutex mu;
+    static bool attrs[TNN_MAX_DEVICES];
+    if (dev < 0 || dev >= TNN_MAX_DEVICES) {
+        tnn_set_error("device ids must be below %d, got %d", TNN_MAX_DEVICES, dev);
+        return TNN_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!attrs[dev]) {
         const int maxs = 227 * 1024;
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_tnn_search, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_tnn_grid_search, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
@@ -125,7 +139,7 @@ static tnn_status device_setup()
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_linear_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_tnn_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_fallback_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
-        attrs = true;
+        attrs[dev] = true;
     }
     return TNN_OK;
 }
@@ -229,9 +243,10 @@ __global__ void k_query_order_keys(const float4 *__restrict__ q, int64_t m, int6
 
 // The per-query kernels that finish the tile kernel's deferred and
 // unsettled queries; the measured interval covers the whole search.
-static tnn_status finish_search(const KnnLaunch &L, cudaStream_t st, bool prof,
-                                std::pair<cudaEvent_t, cudaEvent_t> &pr)
+static tnn_status finish_search(const KnnLaunch &L, cudaStream_t st, bool prof, ProfEv &pr)
 {
+    if (prof)
+        TNN_CUDA_TRY(cudaEventRecord(pr.e[1], st));
     {
         const size_t wsm = wq_smem_per_warp() * TNN_WARPS_PER_CTA;
         int nbw = 0;
@@ -239,11 +254,13 @@ static tnn_status finish_search(const KnnLaunch &L, cudaStream_t st, bool prof,
         k_tnn_warp<<<(unsigned)(std::max(nbw, 1) * g_num_sms), TNN_WARPS_PER_CTA * 32, wsm, st>>>(L);
     }
     TNN_CUDA_TRY(cudaGetLastError());
+    if (prof)
+        TNN_CUDA_TRY(cudaEventRecord(pr.e[2], st));
     k_fallback_exact<<<(unsigned)g_num_sms, TNN_WARPS_PER_CTA * 32,
                        fb_exact_smem_per_warp(L.L_max) * TNN_WARPS_PER_CTA, st>>>(L);
     TNN_CUDA_TRY(cudaGetLastError());
     if (prof) {
-        TNN_CUDA_TRY(cudaEventRecord(pr.second, st));
+        TNN_CUDA_TRY(cudaEventRecord(pr.e[3], st));
         g_prof_ev.push_back(pr);
     }
     return TNN_OK;
@@ -278,7 +295,7 @@ tnn_status tnn_launch_search(const KnnLaunch &L, bool brute, cudaStream_t st)
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         cudaStreamIsCapturing(st, &cap);
         const bool prof = g_prof_on && cap == cudaStreamCaptureStatusNone;
-        std::pair<cudaEvent_t, cudaEvent_t> pr;
+        ProfEv pr;
         if (prof)
             TNN_CUDA_TRY(prof_begin(st, &pr));
         // queries in space-time order (skipped beyond 2^29 queries)
@@ -321,7 +338,7 @@ tnn_status tnn_launch_search(const KnnLaunch &L, bool brute, cudaStream_t st)
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cap);
     const bool prof = g_prof_on && cap == cudaStreamCaptureStatusNone;
-    std::pair<cudaEvent_t, cudaEvent_t> pr;
+    ProfEv pr;
     if (prof)
         TNN_CUDA_TRY(prof_begin(st, &pr));
     if (brute)
@@ -334,9 +351,79 @@ tnn_status tnn_launch_search(const KnnLaunch &L, bool brute, cudaStream_t st)
     return finish_search(L, st, prof, pr);
 }
 
+// ------------------------------------------------------------- faults
+
+tnn_status tnn_take_search_faults(cudaStream_t st)
+{
+    unsigned int f = 0;
+    TNN_CUDA_TRY(cudaStreamSynchronize(st));
+    TNN_CUDA_TRY(cudaMemcpyFromSymbol(&f, g_search_fault, sizeof(f)));
+    if (!f)
+        return TNN_OK;
+    const unsigned int zero = 0;
+    TNN_CUDA_TRY(cudaMemcpyToSymbol(g_search_fault, &zero, sizeof(zero)));
+    if (f & 4u) {
+        tnn_set_error("a bounded device wait of a search timed out (1 s); its outputs are incomplete");
+        return TNN_ERR_TIMEOUT;
+    }
+    tnn_set_error("a search overflowed an internal list (flags %u); its outputs are incomplete", f);
+    return TNN_ERR_CUDA;
+}
+
+extern "C" tnn_status tnn_sync_status(tnn_stream_t stream)
+{
+    tnn_clear_error();
+    return tnn_take_search_faults((cudaStream_t)stream);
+}
+
+// Self-test of the bounded-wait path: one warp waits on an mbarrier that no
+// thread and no copy ever arrives on (nothing else is in flight), gives up
+// after limit_ns and raises the timeout flag exactly as the tensor-core
+// kernels do.
+__global__ void k_selftest_wait(uint64_t limit_ns)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ int s_err;
+    if (threadIdx.x == 0) {
+        s_err = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&bar)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_try(su32(&bar), 0u) ||
+                    mbar_wait_slow(su32(&bar), 0u, (volatile int *)&s_err, limit_ns);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!ok)
+            atomicOr(&g_search_fault, 4u);
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(su32(&bar)) : "memory");
+    }
+}
+
+extern "C" tnn_status tnn_selftest_bounded_wait(int32_t limit_us, tnn_stream_t stream)
+{
+    tnn_clear_error();
+    TNN_ARG_CHECK(limit_us >= 1 && limit_us <= 1000000, "limit_us must be in [1, 10^6]");
+    k_selftest_wait<<<1, 32, 0, (cudaStream_t)stream>>>((uint64_t)limit_us * 1000ull);
+    TNN_CUDA_TRY(cudaGetLastError());
+    return TNN_OK;
+}
+
+// Which kernel finished each query: 1 for the entries of the list of the
+// warp-per-query kernel, then 2 for those of the exact kernel.
+__global__ void k_mark_paths(const int2 *__restrict__ list, const unsigned *__restrict__ count,
+                             int64_t cap, uint8_t v, uint8_t *__restrict__ path)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = min((int64_t)*count, cap);
+    if (i < n)
+        path[list[i].y] = v;
+}
+
 static tnn_status run_single(const tnn_index *ix, const float *d_q, int64_t m,
                              const tnn_knn_params *p, int32_t *d_idx, float *d_d2,
-                             tnn_stats *h_stats, tnn_stream_t stream, bool brute)
+                             tnn_stats *h_stats, tnn_stream_t stream, bool brute,
+                             uint8_t *d_path = nullptr, uint32_t *d_seen = nullptr)
 {
     tnn_clear_error();
     if (brute && ix) {
@@ -368,11 +455,29 @@ static tnn_status run_single(const tnn_index *ix, const float *d_q, int64_t m,
     L.fb_list3 = L.fb_list + m;
     L.fb_tau = (float *)(L.fb_list3 + m);
     cudaError_t e = cudaMemsetAsync(buf, 0, sizeof(KnnScratch), st);
+    if (e == cudaSuccess && d_seen) {
+        L.dbg_seen = d_seen;
+        L.dbg_words = (ix->n + 31) / 32;
+        e = cudaMemsetAsync(d_seen, 0, sizeof(uint32_t) * (size_t)(m * L.dbg_words), st);
+    }
     if (e != cudaSuccess) {
         tnn_free(buf, st);
         TNN_CUDA_TRY(e);
     }
     s = tnn_launch_search(L, brute, st);
+    if (s == TNN_OK && d_path) {
+        e = cudaMemsetAsync(d_path, 0, (size_t)m, st);
+        if (e == cudaSuccess) {
+            const unsigned nb = (unsigned)((m + 255) / 256);
+            k_mark_paths<<<nb, 256, 0, st>>>(L.fb_list, &L.scr->n_fallback, m, 1, d_path);
+            k_mark_paths<<<nb, 256, 0, st>>>(L.fb_list3, &L.scr->n_fallback3, m, 2, d_path);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            tnn_set_error("marking the query paths failed: %s", cudaGetErrorString(e));
+            s = TNN_ERR_CUDA;
+        }
+    }
     KnnScratch hs;
     if (s == TNN_OK && h_stats) {
         e = cudaMemcpyAsync(&hs, buf, sizeof(hs), cudaMemcpyDeviceToHost, st);
@@ -389,13 +494,9 @@ static tnn_status run_single(const tnn_index *ix, const float *d_q, int64_t m,
             h_stats->fp64_rechecks = hs.stats[4];
             h_stats->warp_queries = hs.stats[5];
             h_stats->exact_queries = hs.stats[6];
-            if (hs.status & 4u) {
-                tnn_set_error("a device wait of the tensor-core search timed out");
-                s = TNN_ERR_TIMEOUT;
-            } else if (hs.status) {
-                tnn_set_error("a device list overflowed (status %u)", hs.status);
-                s = TNN_ERR_CUDA;
-            }
+            // this call's flags (folded into the device's fault word by
+            // its last kernel) and any earlier unreported ones
+            s = tnn_take_search_faults(st);
         }
     }
     tnn_free(buf, st);
@@ -407,6 +508,17 @@ extern "C" tnn_status tnn_knn(const tnn_index *index, const float *d_q, int64_t 
                               float *d_d2, tnn_stats *h_stats, tnn_stream_t stream)
 {
     return run_single(index, d_q, m, params, d_idx, d_d2, h_stats, stream, false);
+}
+
+extern "C" tnn_status tnn_knn_trace(const tnn_index *index, const float *d_q, int64_t m,
+                                    const tnn_knn_params *params, int32_t *d_idx, float *d_d2,
+                                    uint8_t *d_path, uint32_t *d_seen, tnn_stream_t stream)
+{
+    tnn_clear_error();
+    TNN_ARG_CHECK(d_path != nullptr || m == 0, "d_path is NULL");
+    TNN_ARG_CHECK(d_seen == nullptr || (params && (params->flags & TNN_FLAG_SWEEP) == 0),
+                  "d_seen records the grid order only");
+    return run_single(index, d_q, m, params, d_idx, d_d2, nullptr, stream, false, d_path, d_seen);
 }
 
 extern "C" tnn_status tnn_knn_bruteforce(const tnn_index *index, const float *d_q,
@@ -573,7 +685,7 @@ extern "C" tnn_status tnn_batch_stats(tnn_batch *b, tnn_stats *h, tnn_stream_t s
     h->fp64_rechecks = hs.stats[4];
     h->warp_queries = hs.stats[5];
     h->exact_queries = hs.stats[6];
-    return TNN_OK;
+    return tnn_take_search_faults((cudaStream_t)stream);
 }
 
 // --------------------------------------------------------------- autotune
@@ -665,6 +777,8 @@ extern "C" tnn_status tnn_autotune(const tnn_index *ix, tnn_knn_params *params,
     cudaFree(dq);
     cudaFree(di);
     cudaFree(dd);
+    if (s == TNN_OK)
+        s = tnn_take_search_faults(st);
     if (s == TNN_OK) {
         params->seed_segments = bestp.seed_segments;
         params->seed_window = bestp.seed_window;
@@ -682,18 +796,21 @@ extern "C" tnn_status tnn_profile_enable(int32_t on)
     return TNN_OK;
 }
 
-extern "C" tnn_status tnn_profile_read(double *ms, int64_t *launches, int32_t reset)
+extern "C" tnn_status tnn_profile_read_kernels(double *h_ms, int64_t *launches, int32_t reset)
 {
     tnn_clear_error();
-    double tot = 0.0;
+    double tot[3] = {0.0, 0.0, 0.0};
     for (auto &pr : g_prof_ev) {
-        TNN_CUDA_TRY(cudaEventSynchronize(pr.second));
-        float x = 0.f;
-        TNN_CUDA_TRY(cudaEventElapsedTime(&x, pr.first, pr.second));
-        tot += x;
+        TNN_CUDA_TRY(cudaEventSynchronize(pr.e[3]));
+        for (int i = 0; i < 3; ++i) {
+            float x = 0.f;
+            TNN_CUDA_TRY(cudaEventElapsedTime(&x, pr.e[i], pr.e[i + 1]));
+            tot[i] += x;
+        }
     }
-    if (ms)
-        *ms = tot;
+    if (h_ms)
+        for (int i = 0; i < 3; ++i)
+            h_ms[i] = tot[i];
     if (launches)
         *launches = (int64_t)g_prof_ev.size();
     if (reset) {
@@ -702,6 +819,15 @@ extern "C" tnn_status tnn_profile_read(double *ms, int64_t *launches, int32_t re
         g_prof_ev.clear();
     }
     return TNN_OK;
+}
+
+extern "C" tnn_status tnn_profile_read(double *ms, int64_t *launches, int32_t reset)
+{
+    double k3[3];
+    tnn_status s = tnn_profile_read_kernels(k3, launches, reset);
+    if (s == TNN_OK && ms)
+        *ms = k3[0] + k3[1] + k3[2];
+    return s;
 }
 
 // ------------------------------------------------------- necessary work
@@ -713,10 +839,11 @@ extern "C" tnn_status tnn_profile_read(double *ms, int64_t *launches, int32_t re
 // segment of the keys whose bound does not exceed d_k, and the distance of
 // every member of the segments whose bound does not exceed d_k.
 __global__ void k_knn_work(const __grid_constant__ KnnWin W, const float *__restrict__ d2,
-                           int k, unsigned long long *out)
+                           int k, const uint8_t *__restrict__ path, unsigned long long *out)
 {
     const long long qi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long nlb = 0, npairs = 0, nkeys = 0;
+    const int cls = (qi < W.m && path) ? min((int)path[qi], 2) : 0;
     if (qi < W.m) {
         const QCtx c = make_qctx(&W, W.q[qi], true);
         const float dk = d2[qi * k + (k - 1)];
@@ -751,21 +878,26 @@ __global__ void k_knn_work(const __grid_constant__ KnnWin W, const float *__rest
                 }
         }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        nlb += __shfl_xor_sync(FULLMASK, nlb, o);
-        npairs += __shfl_xor_sync(FULLMASK, npairs, o);
-        nkeys += __shfl_xor_sync(FULLMASK, nkeys, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(out, nlb);
-        atomicAdd(out + 1, npairs);
-        atomicAdd(out + 2, nkeys);
+    // per class of query (the kernel that finished it), summed over the warp
+    for (int c = 0; c < 3; ++c) {
+        unsigned long long v0 = cls == c ? nlb : 0, v1 = cls == c ? npairs : 0, v2 = cls == c ? nkeys : 0;
+        for (int o = 16; o > 0; o >>= 1) {
+            v0 += __shfl_xor_sync(FULLMASK, v0, o);
+            v1 += __shfl_xor_sync(FULLMASK, v1, o);
+            v2 += __shfl_xor_sync(FULLMASK, v2, o);
+        }
+        if ((threadIdx.x & 31) == 0 && (v0 | v1 | v2)) {
+            atomicAdd(out + 3 * c, v0);
+            atomicAdd(out + 3 * c + 1, v1);
+            atomicAdd(out + 3 * c + 2, v2);
+        }
     }
 }
 
-extern "C" tnn_status tnn_knn_work(const tnn_index *index, const float *d_q, int64_t m,
-                                   int32_t k, double lag, const float *d_d2,
-                                   uint64_t *h_work, tnn_stream_t stream)
+extern "C" tnn_status tnn_knn_work_split(const tnn_index *index, const float *d_q, int64_t m,
+                                         int32_t k, double lag, const float *d_d2,
+                                         const uint8_t *d_path, uint64_t *h_work,
+                                         tnn_stream_t stream)
 {
     tnn_clear_error();
     TNN_ARG_CHECK(h_work != nullptr, "h_work is NULL");
@@ -777,27 +909,40 @@ extern "C" tnn_status tnn_knn_work(const tnn_index *index, const float *d_q, int
     tnn_status s = tnn_fill_window(index, d_q, m, &p, nullptr, nullptr, &w);
     if (s != TNN_OK)
         return s;
-    h_work[0] = h_work[1] = h_work[2] = 0;
+    for (int i = 0; i < 9; ++i)
+        h_work[i] = 0;
     if (m == 0)
         return TNN_OK;
     TNN_ARG_CHECK(d_d2 != nullptr, "d_d2 is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     unsigned long long *buf = nullptr;
-    TNN_CUDA_TRY(tnn_alloc((void **)&buf, 24, st));
-    cudaError_t e = cudaMemsetAsync(buf, 0, 24, st);
+    TNN_CUDA_TRY(tnn_alloc((void **)&buf, 72, st));
+    cudaError_t e = cudaMemsetAsync(buf, 0, 72, st);
     if (e == cudaSuccess) {
-        k_knn_work<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(w, d_d2, k, buf);
+        k_knn_work<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(w, d_d2, k, d_path, buf);
         e = cudaGetLastError();
     }
-    unsigned long long h[3] = {0, 0, 0};
+    unsigned long long h[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h, buf, 24, cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(h, buf, 72, cudaMemcpyDeviceToHost, st);
     tnn_free(buf, st);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(st);
     TNN_CUDA_TRY(e);
-    h_work[0] = h[0];
-    h_work[1] = h[1];
-    h_work[2] = h[2];
+    for (int i = 0; i < 9; ++i)
+        h_work[i] = h[i];
     return TNN_OK;
+}
+
+extern "C" tnn_status tnn_knn_work(const tnn_index *index, const float *d_q, int64_t m,
+                                   int32_t k, double lag, const float *d_d2,
+                                   uint64_t *h_work, tnn_stream_t stream)
+{
+    TNN_ARG_CHECK(h_work != nullptr, "h_work is NULL");
+    uint64_t h9[9];
+    tnn_status s = tnn_knn_work_split(index, d_q, m, k, lag, d_d2, nullptr, h9, stream);
+    if (s == TNN_OK)
+        for (int i = 0; i < 3; ++i)
+            h_work[i] = h9[i];
+    return s;
 }

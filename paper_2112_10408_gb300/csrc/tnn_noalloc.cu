@@ -17,7 +17,8 @@
 #define TNN_NOALLOC_HEADER 256
 #define TNN_NOALLOC_BYTES (TNN_NOALLOC_HEADER + (2 * 8 + 4) * TNN_NOALLOC_MAX_QUERIES)
 
-// Resident on every device that loads the library, until the process exits.
+// Resident on every device that loads the library, until the process exits:
+// 256 B + 20 B x 65,536 = 1,310,976 B (1.25 MiB + 256 B).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[TNN_NOALLOC_BYTES];
 
 #define TNN_NOALLOC_MAX_DEVICES 64
@@ -26,7 +27,10 @@ static std::mutex g_noalloc_mutex;
 
 // Device address of the array on the current device.  The name of the array
 // in host code only stands for it; the address is looked up once per device,
-// with that device current, and kept.
+// with that device current, and kept (so a call inside a stream capture does
+// no lookup, provided an earlier call on the device did it).  cudaDeviceReset
+// reloads the module, after which the kept address is stale: the header
+// tells callers not to call again after a reset.
 static tnn_status noalloc_scratch(void **out)
 {
     int dev = 0;
@@ -79,5 +83,9 @@ extern "C" tnn_status tnn_knn_noalloc(const tnn_index *index, const float *d_q, 
     // The array keeps the previous call's contents: the queue counter, the
     // counters and the list lengths must start at zero.
     TNN_CUDA_TRY(cudaMemsetAsync(scr, 0, sizeof(KnnScratch), st));
+    // Each of the two fallback lists holds m entries and a query is appended
+    // to each at most once, so neither can overflow here; the kernels'
+    // flags (an overflow, should that ever change, or an expired wait) go to
+    // the device's fault word, which tnn_sync_status reports.
     return tnn_launch_search(L, false, st);
 }

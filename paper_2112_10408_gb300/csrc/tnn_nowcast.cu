@@ -11,6 +11,7 @@
 //          dY = (Y - T) / B, dW2 = H^T dY, db2 = sum dY,
 //          dZ = (dY W2^T) * GELU'(Z) (BF16), dW1 = X^T dZ, db1 = sum dZ.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -480,6 +481,93 @@ extern "C" tnn_status tnn_mlp_set_params(tnn_mlp *n, const float *h_params, cons
     k_to_w1t<<<(unsigned)((nW1 + 255) / 256), 256>>>(n->w, n->w1t, n->d_in, n->dh);
     TNN_CUDA_TRY(cudaDeviceSynchronize());
     return TNN_OK;
+}
+
+// ------------------------------------------------------------- checkpoint
+
+// File layout (little-endian whatever the host): five int64 -- magic
+// "TNNM" (0x544E4E4D), version 1, d_in, d_hidden, AdamW step -- then the
+// flat parameters, the first and the second AdamW moments, P float32 each.
+#define TNN_MLP_MAGIC 0x544E4E4Dll
+#define TNN_MLP_VERSION 1
+
+static void put_le64(unsigned char *b, long long v)
+{
+    const unsigned long long u = (unsigned long long)v;
+    for (int i = 0; i < 8; ++i)
+        b[i] = (unsigned char)(u >> (8 * i));
+}
+static long long get_le64(const unsigned char *b)
+{
+    unsigned long long u = 0;
+    for (int i = 0; i < 8; ++i)
+        u |= (unsigned long long)b[i] << (8 * i);
+    return (long long)u;
+}
+static void f32_to_le(const float *x, long long n, unsigned char *b)
+{
+    for (long long i = 0; i < n; ++i) {
+        uint32_t u;
+        memcpy(&u, x + i, 4);
+        for (int j = 0; j < 4; ++j)
+            b[4 * i + j] = (unsigned char)(u >> (8 * j));
+    }
+}
+static void le_to_f32(const unsigned char *b, long long n, float *x)
+{
+    for (long long i = 0; i < n; ++i) {
+        uint32_t u = 0;
+        for (int j = 0; j < 4; ++j)
+            u |= (uint32_t)b[4 * i + j] << (8 * j);
+        memcpy(x + i, &u, 4);
+    }
+}
+
+extern "C" tnn_status tnn_mlp_save(const tnn_mlp *n, const char *path)
+{
+    tnn_clear_error();
+    TNN_ARG_CHECK(n != nullptr && path != nullptr, "NULL argument");
+    std::vector<float> h(3 * (size_t)n->P);
+    int64_t step = 0;
+    tnn_status s = tnn_mlp_get_params(n, h.data(), h.data() + n->P, h.data() + 2 * n->P, &step);
+    if (s != TNN_OK)
+        return s;
+    std::vector<unsigned char> buf(40 + 4 * h.size());
+    put_le64(&buf[0], TNN_MLP_MAGIC);
+    put_le64(&buf[8], TNN_MLP_VERSION);
+    put_le64(&buf[16], n->d_in);
+    put_le64(&buf[24], n->dh);
+    put_le64(&buf[32], step);
+    f32_to_le(h.data(), (long long)h.size(), &buf[40]);
+    FILE *f = fopen(path, "wb");
+    TNN_ARG_CHECK(f != nullptr, "cannot open %s for writing", path);
+    const size_t wr = fwrite(buf.data(), 1, buf.size(), f);
+    const int cl = fclose(f);
+    TNN_ARG_CHECK(wr == buf.size() && cl == 0, "writing %s failed", path);
+    return TNN_OK;
+}
+
+extern "C" tnn_status tnn_mlp_load(tnn_mlp *n, const char *path)
+{
+    tnn_clear_error();
+    TNN_ARG_CHECK(n != nullptr && path != nullptr, "NULL argument");
+    FILE *f = fopen(path, "rb");
+    TNN_ARG_CHECK(f != nullptr, "cannot open %s", path);
+    unsigned char hdr[40];
+    const size_t got = fread(hdr, 1, sizeof(hdr), f);
+    if (got != sizeof(hdr) || get_le64(hdr) != TNN_MLP_MAGIC || get_le64(hdr + 8) != TNN_MLP_VERSION ||
+        get_le64(hdr + 16) != n->d_in || get_le64(hdr + 24) != n->dh || get_le64(hdr + 32) < 0) {
+        fclose(f);
+        tnn_set_error("%s is not a checkpoint of a %d -> %d MLP", path, n->d_in, n->dh);
+        return TNN_ERR_INVALID_ARG;
+    }
+    std::vector<unsigned char> buf(12 * (size_t)n->P);
+    const size_t body = fread(buf.data(), 1, buf.size(), f);
+    fclose(f);
+    TNN_ARG_CHECK(body == buf.size(), "%s is truncated", path);
+    std::vector<float> h(3 * (size_t)n->P);
+    le_to_f32(buf.data(), (long long)h.size(), h.data());
+    return tnn_mlp_set_params(n, h.data(), h.data() + n->P, h.data() + 2 * n->P, get_le64(hdr + 32));
 }
 
 // Dynamic shared memory of a tensor-core kernel, raised so that no more CTAs

@@ -48,10 +48,11 @@ __device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity)
     return ok != 0;
 }
 
-// Wait for an mbarrier phase.  Gives up (false) after TC_WAIT_NS, or as soon
+// Wait for an mbarrier phase.  Gives up (false) after limit_ns, or as soon
 // as another thread of the CTA has flagged an error in *err (when err is
 // non-NULL); a thread that times out sets the flag.
-static __device__ __noinline__ bool mbar_wait_slow(uint32_t addr, uint32_t parity, volatile int *err)
+static __device__ __noinline__ bool mbar_wait_slow(uint32_t addr, uint32_t parity, volatile int *err,
+                                                   uint64_t limit_ns)
 {
     const uint64_t t0 = globaltimer_ns();
     for (;;) {
@@ -59,7 +60,7 @@ static __device__ __noinline__ bool mbar_wait_slow(uint32_t addr, uint32_t parit
             return true;
         if (err && *err)
             return false;
-        if (globaltimer_ns() - t0 > TC_WAIT_NS) {
+        if (globaltimer_ns() - t0 > limit_ns) {
             if (err)
                 *err = 1;
             return false;
@@ -67,9 +68,10 @@ static __device__ __noinline__ bool mbar_wait_slow(uint32_t addr, uint32_t parit
     }
 }
 
+// The wait of every tensor-core kernel: at most TC_WAIT_NS.
 __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, volatile int *err)
 {
-    return mbar_try(addr, parity) || mbar_wait_slow(addr, parity, err);
+    return mbar_try(addr, parity) || mbar_wait_slow(addr, parity, err, TC_WAIT_NS);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t addr)

@@ -79,8 +79,15 @@ _SIGNATURES = [
     ("tnn_knn_noalloc", c_i32, [c_p, c_p, c_i64, ctypes.POINTER(tnn_knn_params), c_p, c_p, c_p]),
     ("tnn_segment_lower_bounds", c_i32, [c_p, c_p, c_i64, c_f64, c_p, c_p]),
     ("tnn_knn_work", c_i32, [c_p, c_p, c_i64, c_i32, c_f64, c_p, c_p, c_p]),
+    ("tnn_knn_work_split", c_i32, [c_p, c_p, c_i64, c_i32, c_f64, c_p, c_p, c_p, c_p]),
+    ("tnn_knn_trace", c_i32, [c_p, c_p, c_i64, ctypes.POINTER(tnn_knn_params), c_p, c_p, c_p, c_p,
+                              c_p]),
     ("tnn_profile_enable", c_i32, [c_i32]),
     ("tnn_profile_read", c_i32, [ctypes.POINTER(c_f64), ctypes.POINTER(c_i64), c_i32]),
+    ("tnn_profile_read_kernels", c_i32, [c_p, ctypes.POINTER(c_i64), c_i32]),
+    ("tnn_probe_fp32", c_i32, [c_i32, ctypes.POINTER(c_f64), ctypes.POINTER(c_f64), c_p]),
+    ("tnn_sync_status", c_i32, [c_p]),
+    ("tnn_selftest_bounded_wait", c_i32, [c_i32, c_p]),
     ("tnn_knn_host", c_i32, [c_p, c_i64, c_p, c_i64, ctypes.POINTER(tnn_build_params),
                              ctypes.POINTER(tnn_knn_params), c_i32, c_p, c_p, c_p]),
     ("tnn_memory_trim", c_i32, [c_i64]),
@@ -94,7 +101,10 @@ _SIGNATURES = [
     ("tnn_autotune", c_i32, [c_p, ctypes.POINTER(tnn_knn_params), c_i64, c_p]),
     ("tnn_context_features", c_i32, [c_p, c_p, c_p, c_i64, c_p, c_p, c_i32, c_p, c_p, c_f32,
                                      c_p, c_p, c_p]),
+    ("tnn_window_average", c_i32, [c_p, c_p, c_p, c_i64, c_f64, c_f64, c_p, c_p]),
     ("tnn_mlp_create", c_i32, [c_i32, c_i32, ctypes.c_uint64, ctypes.POINTER(c_p)]),
+    ("tnn_mlp_save", c_i32, [c_p, ctypes.c_char_p]),
+    ("tnn_mlp_load", c_i32, [c_p, ctypes.c_char_p]),
     ("tnn_mlp_destroy", None, [c_p]),
     ("tnn_mlp_num_params", c_i64, [c_p]),
     ("tnn_mlp_get_params", c_i32, [c_p, c_p, c_p, c_p, ctypes.POINTER(c_i64)]),
@@ -309,6 +319,69 @@ def tnn_knn_work(index: Index, k: int, d2: torch.Tensor, lag: float = 0.0, q=Non
     return int(out[0]), int(out[1]), int(out[2])
 
 
+def tnn_knn_trace(index: Index, k: int, lag: float = 0.0, q=None, out=None, seen: bool = False,
+                  **kw):
+    """tnn_knn that also returns, per query, the kernel that finished it
+    (uint8 [m]: 0 tile kernel, 1 warp-per-query kernel, 2 FP64 definition)
+    and, with ``seen``, the bitmap [m, ceil(n/32)] int32 of the points whose
+    segment was scanned for each query (returned as a fourth value)."""
+    p = make_knn_params(k, lag, **kw)
+    if q is not None:
+        q = _dev(q, torch.float32, (4,), "q")
+        m = q.shape[0]
+    else:
+        m = index.n_points
+    if out is None:
+        idx = torch.empty((m, k), dtype=torch.int32, device="cuda")
+        d2 = torch.empty((m, k), dtype=torch.float32, device="cuda")
+    else:
+        idx, d2 = out
+        _dev(idx, torch.int32, (k,), "idx")
+        _dev(d2, torch.float32, (k,), "d2")
+    path = torch.empty((m,), dtype=torch.uint8, device="cuda")
+    sn = (torch.empty((m, (index.n_points + 31) // 32), dtype=torch.int32, device="cuda")
+          if seen else None)
+    _check(_L().tnn_knn_trace(index.handle, _ptr(q), m, ctypes.byref(p), _ptr(idx), _ptr(d2),
+                              _ptr(path), _ptr(sn), _stream()))
+    return (idx, d2, path, sn) if seen else (idx, d2, path)
+
+
+def tnn_knn_work_split(index: Index, k: int, d2: torch.Tensor, path=None, lag: float = 0.0, q=None):
+    """[3][3] nested lists: per finishing kernel (row), the (segment bounds,
+    member points, key bounds) any exact search must evaluate."""
+    if q is not None:
+        q = _dev(q, torch.float32, (4,), "q")
+        m = q.shape[0]
+    else:
+        m = index.n_points
+    _dev(d2, torch.float32, (k,), "d2")
+    if path is not None:
+        _dev(path, torch.uint8, (), "path")
+    out = (ctypes.c_uint64 * 9)()
+    _check(_L().tnn_knn_work_split(index.handle, _ptr(q), m, int(k), float(lag), _ptr(d2),
+                                   _ptr(path), out, _stream()))
+    return [[int(out[3 * c + i]) for i in range(3)] for c in range(3)]
+
+
+def tnn_sync_status():
+    """Synchronise the current stream and raise TNNError for a fault the
+    search kernels flagged since the last report."""
+    _check(_L().tnn_sync_status(_stream()))
+
+
+def tnn_selftest_bounded_wait(limit_us: int):
+    """Enqueue the bounded-wait self-test (tnn_sync_status then reports a
+    timeout)."""
+    _check(_L().tnn_selftest_bounded_wait(int(limit_us), _stream()))
+
+
+def tnn_probe_fp32(iters: int = 1 << 16):
+    """(measured FFMA lane-operations per second, launch ms)."""
+    ops, ms = c_f64(), c_f64()
+    _check(_L().tnn_probe_fp32(int(iters), ctypes.byref(ops), ctypes.byref(ms), _stream()))
+    return float(ops.value), float(ms.value)
+
+
 def _host(t, dtype, shape_tail, name):
     if isinstance(t, np.ndarray):
         t = torch.from_numpy(t)
@@ -371,6 +444,14 @@ def tnn_profile_read(reset: bool = True):
     n = c_i64()
     _check(_L().tnn_profile_read(ctypes.byref(ms), ctypes.byref(n), 1 if reset else 0))
     return float(ms.value), int(n.value)
+
+
+def tnn_profile_read_kernels(reset: bool = True):
+    """([main kernel ms, warp-per-query kernel ms, FP64 kernel ms], launches)."""
+    ms = (c_f64 * 3)()
+    n = c_i64()
+    _check(_L().tnn_profile_read_kernels(ms, ctypes.byref(n), 1 if reset else 0))
+    return [float(ms[i]) for i in range(3)], int(n.value)
 
 
 def tnn_autotune(index: Index, k: int, lag: float = 0.0, m_sample: int = 4096, exact_d2=False):
@@ -453,6 +534,23 @@ def tnn_context_features(index: Index, wind: torch.Tensor, idx: torch.Tensor, d2
         hs.ctypes.data_as(c_p) if hs is not None else None, float(idw_eps),
         _ptr(feat), _ptr(idw), _stream()))
     return feat, idw
+
+
+def tnn_window_average(index: Index, wind: torch.Tensor, before_lo: float = 5400.0,
+                       before_hi: float = 1800.0, q=None) -> torch.Tensor:
+    """Mean wind [m, 2] of the indexed points measured in
+    [t_q - before_lo, t_q - before_hi] (the hour average of Sec. 4.1 with the
+    defaults; the day average with before_lo = inf, before_hi = -inf)."""
+    wind = _dev(wind, torch.float32, (2,), "wind")
+    if q is not None:
+        q = _dev(q, torch.float32, (4,), "q")
+        m = q.shape[0]
+    else:
+        m = index.n_points
+    out = torch.empty((m, 2), dtype=torch.float32, device="cuda")
+    _check(_L().tnn_window_average(index.handle, _ptr(wind), _ptr(q), m, float(before_lo),
+                                   float(before_hi), _ptr(out), _stream()))
+    return out
 
 
 @dataclass
@@ -547,25 +645,17 @@ class MLP:
         b2 = w[o:o + 2]
         return W1, b1, W2, b2
 
-    def save(self, path: str):
-        """Checkpoint: parameters, AdamW moments and step (little-endian)."""
-        w, m, v, step = self.get_params(with_moments=True)
-        hdr = np.array([0x544E4E4D, 1, self.d_in, self.d_hidden, step], dtype=np.int64)
-        with open(path, "wb") as f:
-            f.write(hdr.astype("<i8").tobytes())
-            for a in (w, m, v):
-                f.write(a.astype("<f4").tobytes())
+    def tnn_mlp_save(self, path: str):
+        """Checkpoint (C ABI tnn_mlp_save): parameters, AdamW moments, step."""
+        _check(_L().tnn_mlp_save(self._h, os.fsencode(path)))
 
-    def load(self, path: str):
-        with open(path, "rb") as f:
-            hdr = np.frombuffer(f.read(40), dtype="<i8")
-            if hdr[0] != 0x544E4E4D or hdr[1] != 1 or hdr[2] != self.d_in or hdr[3] != self.d_hidden:
-                raise ValueError("checkpoint does not match this MLP")
-            P = self.n_params
-            w = np.frombuffer(f.read(4 * P), dtype="<f4")
-            m = np.frombuffer(f.read(4 * P), dtype="<f4")
-            v = np.frombuffer(f.read(4 * P), dtype="<f4")
-        self.set_params(w, m, v, int(hdr[4]))
+    save = tnn_mlp_save
+
+    def tnn_mlp_load(self, path: str):
+        """Restore a checkpoint of an MLP of the same shape (tnn_mlp_load)."""
+        _check(_L().tnn_mlp_load(self._h, os.fsencode(path)))
+
+    load = tnn_mlp_load
 
     def destroy(self):
         if getattr(self, "_h", None) is not None and _lib is not None:

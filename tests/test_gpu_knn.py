@@ -274,7 +274,7 @@ def test_precision_config_sampled_queries():
     wl = synth.precision()
     ix = _index(wl, 20)
     ti, td, st = tnn.tnn_knn(ix, 32, 0.0, stats=True)
-    q = synth.query_sample(wl.n, 1024)
+    q = synth.query_sample(wl.n, 4096)
     oi, od = oracle.knn(wl.xyzt, 32, SIG, qsel=q)
     assert_knn_equal(ti.cpu().numpy()[q], td.cpu().numpy()[q], oi, od, what="tnn precision")
     assert st["exact_queries"] <= wl.n * 1e-4
@@ -346,3 +346,135 @@ def test_linear_tensor_core_far_and_large_coordinates():
     for ffma in (False, True):
         bi, bd = tnn.tnn_knn_bruteforce(ix, 10, 3.0, q=qd, ffma=ffma)
         assert_knn_equal(bi.cpu().numpy(), bd.cpu().numpy(), oi, od, what=f"far ffma={ffma}")
+
+
+def test_stop_certificate_every_skipped_segment_is_bounded_out():
+    """Algorithm 2's stop rule and exclusion criterion, checked directly: the
+    search records which segments it scanned for each query; every causal
+    segment it skipped must have a cylinder bound above the query's final
+    k-th distance (the bound it skipped against is the (k + extra)-th
+    candidate, never below the k-th)."""
+    for wl, k, lag in ((synth.flights(60, 70, seed=41, n_routes=5), 16, 0.0),
+                       (synth.flights(50, 80, seed=42, n_routes=4), 5, 90.0),
+                       (synth.smoothed_random_walks(25, 90, seed=3), 32, 0.0)):
+        ix = _index(wl, 12)
+        idx, d2, path, seen = tnn.tnn_knn_trace(ix, k, lag, seen=True)
+        lb = tnn.tnn_segment_lower_bounds(ix, lag=lag)
+        seg, _ = tnn.tnn_index_export(ix)
+        torch.cuda.synchronize()
+        oi, od = oracle.knn(wl.xyzt, k, SIG, lag=lag)
+        assert_knn_equal(idx.cpu().numpy(), d2.cpu().numpy(), oi, od, what=f"traced {wl.name}")
+        seg = seg.cpu().numpy()
+        first = seg[:, 12].view(np.int32)
+        cnt = seg[:, 13].view(np.int32)
+        bits = seen.cpu().numpy().view(np.uint32)
+        pt_seen = ((bits[:, :, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(wl.n, -1)[:, :wl.n]
+        # a segment counts as scanned for a query when its first member was
+        # (members are recorded together)
+        scanned = pt_seen[:, first].astype(bool)
+        lbv = lb.cpu().numpy()
+        dk = d2.cpu().numpy()[:, k - 1].astype(np.float64)
+        p = path.cpu().numpy()
+        rows = np.nonzero(p < 2)[0]
+        assert rows.size > 0.9 * wl.n
+        causal = np.isfinite(lbv)
+        skipped = causal & ~scanned
+        for q in rows:
+            s = np.nonzero(skipped[q])[0]
+            if s.size == 0:
+                continue
+            assert np.isfinite(dk[q]), (wl.name, q, "skipped a causal segment before k were found")
+            worst = lbv[q, s].min()
+            assert worst > dk[q] * (1.0 - 2.0 ** -18), (wl.name, q, worst, dk[q])
+        # and the pruning did skip work
+        assert skipped[rows].sum() > 0
+        # every point of a segment scanned for a query was recorded with it
+        scnt = pt_seen[rows].sum(axis=1)
+        assert (scnt == (scanned[rows] * cnt[None, :]).sum(axis=1)).all()
+
+
+def test_trace_paths_and_work_split_add_up():
+    wl = synth.flights(300, 120, seed=61, n_routes=8)
+    ix = _index(wl, 20)
+    ti, td, st = tnn.tnn_knn(ix, 32, 0.0, stats=True)
+    pi, pd, path = tnn.tnn_knn_trace(ix, 32, 0.0)
+    torch.cuda.synchronize()
+    assert torch.equal(pi, ti) and torch.equal(pd, td)
+    p = path.cpu().numpy()
+    assert set(np.unique(p).tolist()) <= {0, 1, 2}
+    assert (p >= 1).sum() <= st["warp_queries"] and (p == 2).sum() == st["exact_queries"]
+    total = tnn.tnn_knn_work(ix, 32, td)
+    split = tnn.tnn_knn_work_split(ix, 32, td, path)
+    for i in range(3):
+        assert sum(split[c][i] for c in range(3)) == total[i]
+    assert tnn.tnn_knn_work_split(ix, 32, td)[0] == list(total)
+
+
+def test_expired_bounded_wait_is_reported_and_cleared():
+    """A wait that nothing satisfies (the self-test kernel: an mbarrier no
+    thread or copy arrives on, nothing in flight) gives up after its limit;
+    the flag reaches the host as TNN_ERR_TIMEOUT at the next synchronising
+    status call, once, and the context stays usable."""
+    wl = synth.flights(30, 40, seed=5, n_routes=3)
+    ix = _index(wl, 10)
+    ref = tnn.tnn_knn(ix, 8, 0.0)
+    tnn.tnn_sync_status()  # nothing pending
+    tnn.tnn_selftest_bounded_wait(2000)
+    with pytest.raises(tnn.TNNError) as ei:
+        tnn.tnn_sync_status()
+    assert ei.value.status == 4
+    tnn.tnn_sync_status()  # reported once, then cleared
+    again = tnn.tnn_knn(ix, 8, 0.0)
+    torch.cuda.synchronize()
+    assert torch.equal(again[0], ref[0]) and torch.equal(again[1], ref[1])
+    # a search with statistics reports a pending flag too
+    tnn.tnn_selftest_bounded_wait(1000)
+    with pytest.raises(tnn.TNNError) as ei:
+        tnn.tnn_knn(ix, 8, 0.0, stats=True)
+    assert ei.value.status == 4
+    tnn.tnn_sync_status()
+
+
+def test_fp32_probe_measures_a_plausible_issue_rate():
+    ops, ms = tnn.tnn_probe_fp32(1 << 14)
+    props = torch.cuda.get_device_properties(0)
+    # 128 FP32 lanes per SM at no more than 2.2 GHz
+    assert 0.3 * props.multi_processor_count * 128 * 1.0e9 < ops < props.multi_processor_count * 128 * 2.2e9
+    assert ms > 0
+
+
+def test_batched_full_config_sampled_against_oracle():
+    """The batched configuration as timed: 64 windows of 10^4-5*10^5 points
+    (log-uniform, whole 200-sample flights), k drawn from {16, 32, 64}, one
+    persistent launch replayed from its CUDA graph; 512 sampled queries per
+    window against the oracle."""
+    wins = synth.batched_windows(n_windows=64)
+    idxs = [_index(wl, 20) for wl, _ in wins]
+    b = tnn.Batch(idxs, [k for _, k in wins])
+    for _ in range(2):
+        b.run()
+    torch.cuda.synchronize()
+    st = b.stats()
+    assert st["queries"] == sum(wl.n for wl, _ in wins)
+    for w, (wl, k) in enumerate(wins):
+        q = synth.query_sample(wl.n, 512, seed=0x5A00 + w)
+        oi, od = oracle.knn(wl.xyzt, k, SIG, qsel=q)
+        assert_knn_equal(b.idx[w].cpu().numpy()[q], b.d2[w].cpu().numpy()[q], oi, od,
+                         what=f"window {w} ({wl.n} points) k={k}")
+    b.destroy()
+    for ix in idxs:
+        ix.destroy()
+
+
+def test_learned_config_contexts_sampled_against_oracle():
+    """The learned form's contexts at full size: 5,000 flights x 200 samples
+    = 1,000,000 points, k = 32, lag 1800 s, autotuned knobs; 4,096 sampled
+    queries against the oracle."""
+    wl = synth.learned()
+    ix = _index(wl, 20)
+    tune = tnn.tnn_autotune(ix, 32, 1800.0)
+    ti, td, st = tnn.tnn_knn(ix, 32, 1800.0, stats=True, **tune)
+    q = synth.query_sample(wl.n, 4096)
+    oi, od = oracle.knn(wl.xyzt, 32, SIG, lag=1800.0, qsel=q)
+    assert_knn_equal(ti.cpu().numpy()[q], td.cpu().numpy()[q], oi, od, what="learned 1M lag 1800")
+    assert st["queries"] == wl.n

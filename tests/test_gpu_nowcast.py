@@ -367,3 +367,51 @@ def test_gkamlp_gradient_and_adam_steps_match_oracle():
         # Adam normalises each coordinate: compare where the gradient is not tiny
         big = np.abs(gt) > 1e-3 * np.abs(gt).max()
         np.testing.assert_allclose(got[big], wk[big], rtol=0, atol=3e-3)
+
+
+def test_window_average_matches_oracle():
+    """The hour average of Sec. 4.1 ([t - 1 h 30, t - 30 min]) and the day
+    average against the float64 oracle, self-queries and external ones
+    (including windows that hold no point)."""
+    wl = synth.flights(300, 200, seed=77, n_routes=6)  # 60,000 points over 6 h
+    ix = tnn.tnn_build_segments(torch.from_numpy(wl.xyzt).cuda(), wl.traj_off, SIG, 20)
+    wind = torch.from_numpy(wl.wind).cuda()
+    hour = tnn.tnn_window_average(ix, wind).cpu().numpy()
+    sel = synth.query_sample(wl.n, 3000, seed=4)
+    ref = nc.window_average(wl.xyzt, wl.wind, wl.xyzt[sel])
+    nan = np.isnan(ref)
+    assert np.array_equal(np.isnan(hour[sel]), nan)
+    assert nan.any() and not nan.all()
+    np.testing.assert_allclose(hour[sel][~nan], ref[~nan], rtol=1e-6, atol=1e-6)
+    # external queries at other times, and the day average (every point)
+    rng = np.random.default_rng(3)
+    q = wl.xyzt[rng.choice(wl.n, 700, replace=False)].copy()
+    q[:, 3] = rng.uniform(-1000.0, 30000.0, size=700).astype(np.float32)
+    qd = torch.from_numpy(q).cuda()
+    got = tnn.tnn_window_average(ix, wind, 7200.0, 600.0, q=qd).cpu().numpy()
+    ref = nc.window_average(wl.xyzt, wl.wind, q, 7200.0, 600.0)
+    nan = np.isnan(ref)
+    assert np.array_equal(np.isnan(got), nan)
+    np.testing.assert_allclose(got[~nan], ref[~nan], rtol=1e-6, atol=1e-6)
+    day = tnn.tnn_window_average(ix, wind, float("inf"), float("-inf"), q=qd[:5]).cpu().numpy()
+    np.testing.assert_allclose(day, np.repeat(wl.wind.astype(np.float64).mean(axis=0)[None], 5, axis=0),
+                               rtol=1e-6)
+
+
+def test_checkpoint_rejects_other_shapes_and_truncated_files(tmp_path):
+    m = tnn.MLP(64, 64, seed=1)
+    p = tmp_path / "a.bin"
+    m.save(str(p))
+    other = tnn.MLP(64, 128, seed=1)
+    with pytest.raises(tnn.TNNError) as ei:
+        other.load(str(p))
+    assert ei.value.status == 1
+    raw = p.read_bytes()
+    (tmp_path / "cut.bin").write_bytes(raw[:-4])
+    with pytest.raises(tnn.TNNError):
+        m.load(str(tmp_path / "cut.bin"))
+    # the file layout: five little-endian int64, then three float32 blocks
+    hdr = np.frombuffer(raw[:40], dtype="<i8")
+    assert hdr.tolist() == [0x544E4E4D, 1, 64, 64, 0]
+    assert len(raw) == 40 + 3 * 4 * m.n_params
+    np.testing.assert_array_equal(np.frombuffer(raw[40:40 + 4 * m.n_params], dtype="<f4"), m.get_params())

@@ -237,3 +237,25 @@ def test_gkamlp_theta_hand_worked_single_hidden_unit():
     w1 = math.exp(-math.exp(0.8615941559557649))
     w2 = math.exp(-math.exp(-1.3231883119115298))
     np.testing.assert_allclose(out, [[w1 / (w1 + w2), w2 / (w1 + w2)]], rtol=1e-12)
+
+
+def test_hour_average_hand_worked_window():
+    # Hour average of Sec. 4.1: the mean of the points measured in
+    # [t - 1 h 30, t - 30 min].  For a query at t = 6000 s the window is
+    # [600, 4200] s, both ends included.
+    t = np.array([0.0, 599.5, 600.0, 1000.0, 4200.0, 4200.5, 5000.0, 6000.0])
+    u = np.array([100.0, 50.0, 1.0, 2.0, 6.0, 70.0, 80.0, 90.0])
+    v = np.array([-100.0, -50.0, 4.0, 0.0, -1.0, -70.0, -80.0, -90.0])
+    pts = np.column_stack([np.zeros_like(t), np.zeros_like(t), np.full_like(t, 10.0), t]).astype(np.float32)
+    wind = np.column_stack([u, v]).astype(np.float32)
+    q = np.array([[0.0, 0.0, 10.0, 6000.0],   # points at 600, 1000, 4200: u (1+2+6)/3, v (4+0-1)/3
+                  [0.0, 0.0, 10.0, 2000.0],   # window [-3400, 200]: only t = 0
+                  [0.0, 0.0, 10.0, 1000.0]],  # window [-4400, -800]: empty
+                 np.float32)
+    out = nc.window_average(pts, wind, q)
+    np.testing.assert_allclose(out[0], [3.0, 1.0], rtol=1e-15)
+    np.testing.assert_allclose(out[1], [100.0, -100.0], rtol=1e-15)
+    assert np.isnan(out[2]).all()
+    # the day average: every point, whatever the query time
+    day = nc.window_average(pts, wind, q[:1], before_lo=np.inf, before_hi=-np.inf)
+    np.testing.assert_allclose(day[0], [u.mean(), v.mean()], rtol=1e-15)

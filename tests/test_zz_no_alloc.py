@@ -74,3 +74,23 @@ def test_noalloc_rejects_more_queries_than_its_array_holds(lib):
     q = torch.from_numpy(wl.xyzt[-60000:].copy()).cuda()
     ref = tnn.tnn_knn(ix, 8, 0.0, q=q)
     _same(_noalloc(lib, ix, 8, 0.0, q, q.shape[0]), (ref[0].cpu().numpy(), ref[1].cpu().numpy()))
+
+
+def test_noalloc_at_exact_capacity_and_in_sweep_order(lib):
+    """65,536 queries fill the static array to its end (both fallback lists
+    and the handed-over keys); the sweep order runs another kernel over the
+    same scratch.  Both against tnn_knn, twice in a row."""
+    wl = synth.flights(400, 200, seed=11, n_routes=8)  # 80,000 points
+    ix = tnn.tnn_build_segments(torch.from_numpy(wl.xyzt).cuda(), wl.traj_off, SIG, 20)
+    q = torch.from_numpy(wl.xyzt[-65536:].copy()).cuda()
+    ref = tnn.tnn_knn(ix, 32, 0.0, q=q)
+    ref = (ref[0].cpu().numpy(), ref[1].cpu().numpy())
+    for _ in range(2):
+        _same(_noalloc(lib, ix, 32, 0.0, q, 65536), ref)
+    q2 = torch.from_numpy(wl.xyzt[::7].copy()).cuda()
+    ref2 = tnn.tnn_knn(ix, 16, 30.0, q=q2, sweep=True)
+    ref2 = (ref2[0].cpu().numpy(), ref2[1].cpu().numpy())
+    for _ in range(2):
+        _same(_noalloc(lib, ix, 16, 30.0, q2, q2.shape[0], sweep=True), ref2)
+    # nothing the kernels flagged is pending
+    tnn.tnn_sync_status()
