@@ -657,6 +657,32 @@ def _extras(tnn, synth, flush, peaks, steps):
     return out
 
 
+def _tc_tiles(tnn, ix, k, tune, flush, steps, ref_idx, ref_ms):
+    """TNN with the candidate distances formed as tcgen05 TF32 tiles and
+    screened (TNN_FLAG_TC_TILES), timed beside the FP32 member scan on the
+    same workload; identical neighbours required."""
+    import torch
+    kw = {key: tune[key] for key in ("seed_segments", "extra", "defer_cells") if key in tune}
+    ti = torch.empty_like(ref_idx)
+    td = torch.empty(ref_idx.shape, dtype=torch.float32, device=ref_idx.device)
+    tnn.tnn_knn(ix, k, 0.0, out=(ti, td), tc=True, **kw)
+    torch.cuda.synchronize()
+    tnn.tnn_profile_read(reset=True)
+    tnn.tnn_profile_enable(True)
+    with _Range("tnn_tc_tiles"):
+        ms = _timed(lambda: tnn.tnn_knn(ix, k, 0.0, out=(ti, td), tc=True, **kw), steps, flush)
+    tnn.tnn_profile_enable(False)
+    kern, launches = tnn.tnn_profile_read_kernels(reset=True)
+    _, _, st = tnn.tnn_knn(ix, k, 0.0, out=(ti, td), tc=True, stats=True, **kw)
+    tiles = st["segs_scanned"] - 0  # 128 x 128 tiles multiplied (+ seed segments, see note)
+    return {"kernel": "k_tnn_tc", "ms_per_step": ms, "value": ti.shape[0] / (ms / 1e3), "unit": UNIT,
+            "kernel_ms": {"k_tnn_tc": kern[0] / max(launches, 1), "k_tnn_warp": kern[1] / max(launches, 1),
+                          "k_fallback_exact": kern[2] / max(launches, 1)},
+            "vs_fp32_member_scan": ref_ms / ms, "identical_neighbours": bool(torch.equal(ti, ref_idx)),
+            "rescored": st["lb_evals"], "pairs_screened": st["pairs"], "tiles_and_seed_segments": tiles,
+            "warp_queries": st["warp_queries"], "tuning": kw}
+
+
 def _precision(tnn, synth, flush, steps, alu_peak, derived_peak, cpu=True):
     """The precision workload: 20,000 flights x 200 samples = 4,000,000
     points, k = 32, every point a query; FP32 screening with certified
@@ -696,6 +722,7 @@ def _precision(tnn, synth, flush, steps, alu_peak, derived_peak, cpu=True):
     torch.cuda.synchronize()
     cms = _timed(lambda: tnn.tnn_knn_bruteforce(ix, k, 0.0, q=qd, out=(bi, bd)), 2, flush)
     same = bool(torch.equal(bi, idx[torch.from_numpy(qs).cuda()]))
+    tcx = _tc_tiles(tnn, ix, k, tune, flush, steps, idx, ms)
     out = {"workload": "precision-4M: 20,000 synthetic flights x 200 samples = 4,000,000 points, "
                        "self-query of every point, k = 32, 20-point segments",
            "metric": "causal k-NN contexts/s (exact, k=32)", "value": wl.n / (ms / 1e3), "unit": UNIT,
@@ -711,7 +738,7 @@ def _precision(tnn, synth, flush, steps, alu_peak, derived_peak, cpu=True):
                                       "contexts_per_s": qd.shape[0] / (cms / 1e3),
                                       "tnn_speedup": (wl.n / (ms / 1e3)) / (qd.shape[0] / (cms / 1e3)),
                                       "identical_neighbours": same},
-           "stats_per_step": st}
+           "stats_per_step": st, "tc_tiles": tcx}
     if cpu:
         out["cpu_baseline"] = _cpu_baseline(wl, k, 4096, idx, d2)
         out["max_rel_d2_err_vs_fp64"] = out["cpu_baseline"]["parity"]["max_rel_d2_err_vs_fp64"]
@@ -894,6 +921,9 @@ def run_ours(a):
                               "peak_note": "of measured FFMA issue rate"}
             comparator[name] = ent
 
+    # the same search with the candidate distances as tensor-core tiles
+    tc_tiles = _tc_tiles(tnn, ix, k, tune, flush, max(3, min(a.steps, 20)), idx, ms_step)
+
     # end to end through the C ABI on host buffers (tnn_knn_host): pinned
     # host points -> H2D -> index build -> search -> D2H of both result
     # arrays into pinned host memory, the copies overlapped with the search
@@ -940,7 +970,7 @@ def run_ours(a):
                               parallelism=f"replicas x{world}: each rank its own window"),
                "clocks": clocks, "e2e": e2e, "gpu_launches": 3 * a.steps,
                "roofline": roofline, "cpu_baseline": cpu, "comparator": comparator,
-               "stats_per_step": st, "e2e_breakdown": e2e_break}
+               "stats_per_step": st, "e2e_breakdown": e2e_break, "tc_tiles": tc_tiles}
         if extras:
             out.update(extras)
         print(json.dumps(out))

@@ -124,7 +124,15 @@ enum {
     /* tnn_knn_bruteforce only: compute the pair distances on the CUDA cores
        (direct differences) instead of screening them with the tensor-core
        distance matrix.  Same exact result. */
-    TNN_FLAG_FFMA = 4
+    TNN_FLAG_FFMA = 4,
+    /* tnn_knn, grid order: form the distances of the fetched candidate
+       points as 128 x 128 tensor-core tiles (tcgen05, TF32 operands, FP32
+       accumulation) and screen them with a certified margin; points that
+       pass are scored again in FP32 and the ranking settled in FP64 as
+       usual.  128 queries share a traversal.  The first such call builds a
+       grid-key-ordered copy of the points in the index (16 B per point).
+       Same exact result. */
+    TNN_FLAG_TC_TILES = 8
 };
 
 typedef struct {

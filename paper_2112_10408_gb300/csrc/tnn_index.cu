@@ -652,7 +652,8 @@ static void free_index(tnn_index *ix)
     cudaDeviceSynchronize();
     void *arrays[] = {ix->pts,   ix->seg,   ix->segTA, ix->segPM, ix->pts_t,
                       ix->idx_t, ix->g_off, ix->g_ids, ix->g_seg, ix->g_ext,
-                      ix->g_tB,  ix->g_krec, ix->g_bpm, ix->g_ext_max};
+                      ix->g_tB,  ix->g_krec, ix->g_bpm, ix->g_ext_max,
+                      ix->pts_k, ix->idx_k, ix->kp_start};
     for (void *p : arrays)
         tnn_free(p, 0);
     delete ix;
@@ -987,6 +988,128 @@ tnn_status tnn_index_time_order(const tnn_index *cix, cudaStream_t st)
     }
     ix->pts_t = pts_t;
     ix->idx_t = idx_t;
+    return TNN_OK;
+}
+
+// ------------------------------------------------------------- key order
+
+// Padded run length of every key: its segments' member count rounded up to
+// a multiple of 4 (so every run starts on a 16-byte boundary of idx_k).
+__global__ void k_key_runs(const int32_t *__restrict__ off, const float4 *__restrict__ gseg, int nkeys,
+                           int64_t *__restrict__ len)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nkeys)
+        return;
+    int64_t c = 0;
+    for (int i = off[k]; i < off[k + 1]; ++i)
+        c += __float_as_int(gseg[4 * (size_t)i + 3].y);
+    len[k] = (c + 3) & ~3ll;
+}
+
+// Exclusive prefix sum of n int64 values by one block, in place, with the
+// total appended at v[n] (n + 1 entries).
+__global__ void __launch_bounds__(1024) k_scan_i64(int64_t *__restrict__ v, int n)
+{
+    __shared__ int64_t part[1024];
+    const int per = (n + 1023) / 1024;
+    const int lo = min(n, (int)threadIdx.x * per), hi = min(n, lo + per);
+    int64_t s = 0;
+    for (int i = lo; i < hi; ++i)
+        s += v[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int64_t a = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += a;
+        __syncthreads();
+    }
+    int64_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+    for (int i = lo; i < hi; ++i) {
+        const int64_t x = v[i];
+        v[i] = run;
+        run += x;
+    }
+    if (threadIdx.x == 1023)
+        v[n] = part[1023];
+}
+
+// Every key's members into its run, then the padding.
+__global__ void k_key_gather(const int32_t *__restrict__ off, const float4 *__restrict__ gseg,
+                             const int64_t *__restrict__ start, int nkeys, const float4 *__restrict__ pts,
+                             float4 *__restrict__ pk, int32_t *__restrict__ ik, int32_t *__restrict__ ks)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > nkeys)
+        return;
+    ks[k] = (int32_t)start[k];
+    if (k == nkeys)
+        return;
+    int64_t o = start[k];
+    float4 first = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = off[k]; i < off[k + 1]; ++i) {
+        const float4 r = gseg[4 * (size_t)i + 3];
+        const int f = __float_as_int(r.x), c = __float_as_int(r.y);
+        if (i == off[k])
+            first = pts[f];
+        for (int j = 0; j < c; ++j, ++o) {
+            pk[o] = pts[f + j];
+            ik[o] = f + j;
+        }
+    }
+    for (; o < start[k + 1]; ++o) {
+        pk[o] = first;
+        ik[o] = -1;
+    }
+}
+
+static std::mutex g_key_order_mu;
+
+tnn_status tnn_index_key_order(const tnn_index *cix, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(g_key_order_mu);
+    tnn_index *ix = const_cast<tnn_index *>(cix);
+    if (ix->pts_k)
+        return TNN_OK;
+    const int nkeys = ix->grid.nb * ix->grid.ncell, tb = 256;
+    DevBuf len_d;
+    TNN_CUDA_TRY(len_d.alloc(sizeof(int64_t) * (nkeys + 1), st));
+    int64_t *len = (int64_t *)len_d.p;
+    k_key_runs<<<(nkeys + tb - 1) / tb, tb, 0, st>>>(ix->g_off, ix->g_seg, nkeys, len);
+    k_scan_i64<<<1, 1024, 0, st>>>(len, nkeys);
+    int64_t nk = 0;
+    TNN_CUDA_TRY(cudaMemcpyAsync(&nk, len + nkeys, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    TNN_CUDA_TRY(cudaStreamSynchronize(st));
+    if (nk >= (1ll << 31) - 256) {
+        tnn_set_error("the key-ordered copy (%lld points with padding) exceeds 2^31", (long long)nk);
+        return TNN_ERR_UNSUPPORTED;
+    }
+    float4 *pk = nullptr;
+    int32_t *ik = nullptr, *ks = nullptr;
+    cudaError_t e = tnn_alloc((void **)&pk, sizeof(float4) * (size_t)std::max<int64_t>(nk, 1), st);
+    if (e == cudaSuccess)
+        e = tnn_alloc((void **)&ik, sizeof(int32_t) * (size_t)(nk + 4), st);
+    if (e == cudaSuccess)
+        e = tnn_alloc((void **)&ks, sizeof(int32_t) * (size_t)(nkeys + 1), st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(ik + nk, 0xff, 4 * sizeof(int32_t), st);
+    if (e == cudaSuccess) {
+        k_key_gather<<<(nkeys + 1 + tb - 1) / tb, tb, 0, st>>>(ix->g_off, ix->g_seg, len, nkeys, ix->pts, pk,
+                                                             ik, ks);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        tnn_free(pk, st);
+        tnn_free(ik, st);
+        tnn_free(ks, st);
+        tnn_set_error("key order failed: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? TNN_ERR_OOM : TNN_ERR_CUDA;
+    }
+    ix->pts_k = pk;
+    ix->idx_k = ik;
+    ix->kp_start = ks;
+    ix->nk = nk;
     return TNN_OK;
 }
 

@@ -75,6 +75,14 @@ struct tnn_index {
     float4 *pts_t;   // [n] points ordered by (t, index) (linear search; built
                      // by tnn_index_time_order on first use)
     int32_t *idx_t;  // [n + 4] their input index (4 entries of padding)
+    // Points in grid-key order (tensor-core member scan; built by
+    // tnn_index_key_order on first use): the members of every key's segments,
+    // key after key, each key's run padded to a multiple of 4 points with
+    // copies of its first point whose index is -1.
+    float4 *pts_k;   // [nk]
+    int32_t *idx_k;  // [nk + 4] input index, -1 for padding
+    int32_t *kp_start; // [nb * ncell + 1] start of each key's run
+    int64_t nk;
     GridDesc grid;   // views of the arrays below
     int32_t *g_off, *g_ids;
     float4 *g_seg;
@@ -98,6 +106,9 @@ struct KnnWin {
     int64_t m;
     int64_t tile_begin; // first global tile of this window
     GridDesc grid;
+    const float4 *pts_k;      // key-ordered points (tensor-core member scan)
+    const int32_t *idx_k;
+    const int32_t *kp_start;
     float bb_lo[4], bb_hi[4]; // bounding box of the points
     double sigd[4];
     double lag;
@@ -162,6 +173,9 @@ void tnn_free(void *p, cudaStream_t st);
 // Points in (t, index) order for the linear search, built on first use
 // (stream-ordered on `st`).
 tnn_status tnn_index_time_order(const tnn_index *ix, cudaStream_t st);
+// Points in grid-key order for the tensor-core member scan, built on first
+// use (stream-ordered on `st`).
+tnn_status tnn_index_key_order(const tnn_index *ix, cudaStream_t st);
 
 // Launch helpers (tnn_knn.cu).
 tnn_status tnn_fill_window(const tnn_index *ix, const float *d_q, int64_t m,

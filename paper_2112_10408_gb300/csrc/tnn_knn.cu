@@ -62,6 +62,7 @@
 #include "tnn_linear.cuh"
 #include "tnn_fallback.cuh"
 #include "tnn_linear_tc.cuh"
+#include "tnn_tctiles.cuh"
 
 // ------------------------------------------------------ lower-bound export
 
@@ -139,6 +140,7 @@ static tnn_status device_setup()
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_linear_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_tnn_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_fallback_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
+        TNN_CUDA_TRY(cudaFuncSetAttribute(k_tnn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
         attrs[dev] = true;
     }
     return TNN_OK;
@@ -174,6 +176,9 @@ tnn_status tnn_fill_window(const tnn_index *ix, const float *d_q, int64_t m,
     w->segPM = ix->segPM;
     w->pts_t = ix->pts_t;
     w->idx_t = ix->idx_t;
+    w->pts_k = ix->pts_k;
+    w->idx_k = ix->idx_k;
+    w->kp_start = ix->kp_start;
     w->grid = ix->grid;
     for (int i = 0; i < 4; ++i) {
         w->bb_lo[i] = ix->bb_lo[i];
@@ -321,6 +326,31 @@ tnn_status tnn_launch_search(const KnnLaunch &L, bool brute, cudaStream_t st)
         TNN_CUDA_TRY(le);
         return finish_search(L, st, prof, pr);
     }
+    // TNN with tensor-core candidate tiles: one window, 128 queries per CTA,
+    // 256 TMEM columns per CTA; at least 80 KB of shared memory keeps at most
+    // 2 CTAs (512 columns) on an SM
+    if (!brute && !sweep && (L.w0.flags & TNN_FLAG_TC_TILES) && L.nwin <= 1) {
+        const size_t smem = std::max<size_t>(tt_smem_bytes(L.L_max), 80 * 1024);
+        if (smem > (size_t)227 * 1024) {
+            tnn_set_error("tensor-core TNN kernel does not fit on an SM (%zu B shared memory)", smem);
+            return TNN_ERR_UNSUPPORTED;
+        }
+        nb = std::min<int>(2, (int)(g_smem_per_sm / (smem + 1024)));
+        KnnLaunch Lt = L;
+        Lt.total_tiles = (L.w0.m + TT_Q - 1) / TT_Q;
+        long long grid = std::min<long long>(Lt.total_tiles, (long long)std::max(nb, 1) * g_num_sms);
+        if (grid < 1)
+            grid = 1;
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cap);
+        const bool prof = g_prof_on && cap == cudaStreamCaptureStatusNone;
+        ProfEv pr;
+        if (prof)
+            TNN_CUDA_TRY(prof_begin(st, &pr));
+        k_tnn_tc<<<(unsigned)grid, TT_THREADS, smem, st>>>(Lt);
+        TNN_CUDA_TRY(cudaGetLastError());
+        return finish_search(L, st, prof, pr);
+    }
     const size_t smem = smem_per_warp(L.L_max, L.kseg_max,
                                       brute ? SMEM_LINEAR : sweep ? SMEM_SWEEP : SMEM_GRID) *
                         TNN_WARPS_PER_CTA;
@@ -428,6 +458,11 @@ static tnn_status run_single(const tnn_index *ix, const float *d_q, int64_t m,
     tnn_clear_error();
     if (brute && ix) {
         tnn_status ts = tnn_index_time_order(ix, (cudaStream_t)stream);
+        if (ts != TNN_OK)
+            return ts;
+    }
+    if (!brute && ix && p && (p->flags & TNN_FLAG_TC_TILES) && !(p->flags & TNN_FLAG_SWEEP)) {
+        tnn_status ts = tnn_index_key_order(ix, (cudaStream_t)stream);
         if (ts != TNN_OK)
             return ts;
     }
@@ -599,6 +634,8 @@ extern "C" tnn_status tnn_batch_create(const tnn_index *const *indexes,
             return s;
         TNN_ARG_CHECK(m[w] == 0 || (d_idx[w] != nullptr && d_d2[w] != nullptr),
                       "NULL output for window %d", w);
+        TNN_ARG_CHECK((params[w].flags & TNN_FLAG_TC_TILES) == 0,
+                      "TNN_FLAG_TC_TILES is for tnn_knn (window %d)", w);
         wins[w].tile_begin = tiles;
         tiles += (m[w] + TNN_TILE - 1) / TNN_TILE;
         fb += m[w];

@@ -60,6 +60,8 @@ extern "C" tnn_status tnn_knn_noalloc(const tnn_index *index, const float *d_q, 
     if (s != TNN_OK)
         return s;
     TNN_ARG_CHECK(m == 0 || (d_idx != nullptr && d_d2 != nullptr), "NULL output");
+    TNN_ARG_CHECK((params->flags & TNN_FLAG_TC_TILES) == 0,
+                  "TNN_FLAG_TC_TILES is for tnn_knn (its key-ordered copy is allocated on first use)");
     TNN_ARG_CHECK(m <= TNN_NOALLOC_MAX_QUERIES,
                   "tnn_knn_noalloc answers at most %d queries per call, got %lld; "
                   "call it on slices of the queries",

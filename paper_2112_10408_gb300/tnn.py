@@ -61,6 +61,7 @@ class tnn_adamw_params(ctypes.Structure):
 TNN_FLAG_EXACT_D2 = 1
 TNN_FLAG_SWEEP = 2
 TNN_FLAG_FFMA = 4
+TNN_FLAG_TC_TILES = 8
 N_FEAT = 6
 
 # (name, restype, argtypes)
@@ -244,7 +245,7 @@ def tnn_index_export(index: Index):
 
 def make_knn_params(k: int, lag: float = 0.0, seed_segments: int = 0, seed_window: int = 0,
                     extra: int = 0, exact_d2: bool = False, sweep: bool = False,
-                    defer_cells: float = 0.0, ffma: bool = False) -> tnn_knn_params:
+                    defer_cells: float = 0.0, ffma: bool = False, tc: bool = False) -> tnn_knn_params:
     p = tnn_knn_params()
     p.k = int(k)
     p.lag = float(lag)
@@ -252,7 +253,7 @@ def make_knn_params(k: int, lag: float = 0.0, seed_segments: int = 0, seed_windo
     p.seed_window = int(seed_window)
     p.extra = int(extra)
     p.flags = ((TNN_FLAG_EXACT_D2 if exact_d2 else 0) | (TNN_FLAG_SWEEP if sweep else 0)
-               | (TNN_FLAG_FFMA if ffma else 0))
+               | (TNN_FLAG_FFMA if ffma else 0) | (TNN_FLAG_TC_TILES if tc else 0))
     p.defer_cells = float(defer_cells)
     return p
 

@@ -478,3 +478,43 @@ def test_learned_config_contexts_sampled_against_oracle():
     oi, od = oracle.knn(wl.xyzt, 32, SIG, lag=1800.0, qsel=q)
     assert_knn_equal(ti.cpu().numpy()[q], td.cpu().numpy()[q], oi, od, what="learned 1M lag 1800")
     assert st["queries"] == wl.n
+
+
+@pytest.mark.parametrize("k,lag,K", [(1, 0.0, 10), (8, 37.0, 7), (32, 0.0, 20), (64, 120.0, 13)])
+def test_tensor_core_candidate_tiles_match_oracle(k, lag, K):
+    """TNN with the candidate distances as tcgen05 tiles (TNN_FLAG_TC_TILES):
+    the same exact answer as the FP32 member scan and the oracle, on flights,
+    smoothed random walks and random points (several 128-query tiles and a
+    ragged last one)."""
+    for wl in (synth.flights(41, 53, seed=700 + k, n_routes=5),
+               synth.smoothed_random_walks(23, 97, seed=k),
+               synth.random_points(2771, 20, seed=k)):
+        ix = _index(wl, K)
+        ci, cd, st = tnn.tnn_knn(ix, k, lag, tc=True, stats=True)
+        oi, od = oracle.knn(wl.xyzt, k, SIG, lag=lag)
+        assert_knn_equal(ci.cpu().numpy(), cd.cpu().numpy(), oi, od, what=f"tc tiles {wl.name} k={k}")
+        assert st["queries"] == wl.n
+    # external queries, some before every point and some far outside the data
+    wl = synth.flights(40, 64, seed=9, n_routes=5)
+    ix = _index(wl, 10)
+    rng = np.random.default_rng(5)
+    q = wl.xyzt[rng.choice(len(wl.xyzt), 300, replace=False)].copy()
+    q[:50, :2] += rng.normal(0, 500.0, size=(50, 2)).astype(np.float32)
+    q[50:80, 3] = -5.0
+    qd = torch.from_numpy(q).cuda()
+    ci, cd = tnn.tnn_knn(ix, 10, 3.0, q=qd, tc=True)
+    oi, od = oracle.knn(wl.xyzt, 10, SIG, lag=3.0, queries=q)
+    assert_knn_equal(ci.cpu().numpy(), cd.cpu().numpy(), oi, od, what="tc tiles external queries")
+
+
+def test_tensor_core_candidate_tiles_medium_and_precision_sampled():
+    for wl in (synth.medium(), synth.precision()):
+        ix = _index(wl, 20)
+        ci, cd, st = tnn.tnn_knn(ix, 32, 0.0, tc=True, stats=True)
+        q = synth.query_sample(wl.n, 4096)
+        oi, od = oracle.knn(wl.xyzt, 32, SIG, qsel=q)
+        assert_knn_equal(ci.cpu().numpy()[q], cd.cpu().numpy()[q], oi, od, what=f"tc tiles {wl.name}")
+        assert st["queries"] == wl.n and st["segs_scanned"] > 0
+        ti, td = tnn.tnn_knn(ix, 32, 0.0)
+        assert torch.equal(ti, ci)
+        ix.destroy()
