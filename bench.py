@@ -662,9 +662,18 @@ def _tc_tiles(tnn, ix, k, tune, flush, steps, ref_idx, ref_ms):
     screened (TNN_FLAG_TC_TILES), timed beside the FP32 member scan on the
     same workload; identical neighbours required."""
     import torch
-    kw = {key: tune[key] for key in ("seed_segments", "extra", "defer_cells") if key in tune}
     ti = torch.empty_like(ref_idx)
     td = torch.empty(ref_idx.shape, dtype=torch.float32, device=ref_idx.device)
+    # its own knobs: seed count and deferral radius, the fastest of a few
+    tried = {}
+    for F in (1, 2, 3):
+        for dfr in (0.3, 0.6):
+            kw_ = {"seed_segments": F, "extra": tune.get("extra", 4), "defer_cells": dfr}
+            tnn.tnn_knn(ix, k, 0.0, out=(ti, td), tc=True, **kw_)
+            torch.cuda.synchronize()
+            tried[(F, dfr)] = _timed(lambda: tnn.tnn_knn(ix, k, 0.0, out=(ti, td), tc=True, **kw_), 2, flush)
+    F, dfr = min(tried, key=tried.get)
+    kw = {"seed_segments": F, "extra": tune.get("extra", 4), "defer_cells": dfr}
     tnn.tnn_knn(ix, k, 0.0, out=(ti, td), tc=True, **kw)
     torch.cuda.synchronize()
     tnn.tnn_profile_read(reset=True)
@@ -680,7 +689,8 @@ def _tc_tiles(tnn, ix, k, tune, flush, steps, ref_idx, ref_ms):
                           "k_fallback_exact": kern[2] / max(launches, 1)},
             "vs_fp32_member_scan": ref_ms / ms, "identical_neighbours": bool(torch.equal(ti, ref_idx)),
             "rescored": st["lb_evals"], "pairs_screened": st["pairs"], "tiles_and_seed_segments": tiles,
-            "warp_queries": st["warp_queries"], "tuning": kw}
+            "warp_queries": st["warp_queries"], "tuning": kw,
+            "ms_by_knobs": {f"F={a},defer={b}": v for (a, b), v in tried.items()}}
 
 
 def _precision(tnn, synth, flush, steps, alu_peak, derived_peak, cpu=True):

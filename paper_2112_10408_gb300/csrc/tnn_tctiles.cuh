@@ -8,8 +8,8 @@
 //
 // A CTA answers 128 consecutive queries (thread t of warps 0-3 = query t =
 // TMEM lane t).  The index keeps the points in grid-key order (every key's
-// members contiguous, runs padded to a multiple of 4 points), so the keys of
-// one row of cells in one bucket are one contiguous run of points.
+// members contiguous, runs padded to a multiple of 4 points), so keys that
+// follow each other in key order are one contiguous run of points.
 //   seed    every query scans, on its own thread in FP32, the F segments of
 //           smallest cylinder bound among the 3 x 3 cells around the CTA in
 //           the two most recent buckets (Algorithm 2's first fetch); this
@@ -18,7 +18,9 @@
 //           radius goes to the warp-per-query kernel, as in the tile kernel.
 //   main    buckets from the causal end backwards while the temporal bound of
 //           some query's bucket stays within its key (the stop rule); in each
-//           bucket, the rows of cells within reach of the CTA's queries are
+//           bucket, the keys within reach of the CTA whose bound against the
+//           CTA's box (cell rectangle, extent, largest t_B) does not exceed
+//           the largest key of its queries are merged into runs of points and
 //           streamed 128 points at a time (TMA bulk copies into a ring), one
 //           tcgen05.mma per tile, and every query screens its accumulator row.
 //           The threshold in each query's operand row is its key when the
@@ -35,7 +37,7 @@
 #define TT_P 128
 #define TT_S 8         // ring slots
 #define TT_THREADS 160 // 4 screening warps + 1 control warp
-#define TT_RMAX 256    // rows of cells per pass
+#define TT_RMAX 256    // runs of points per pass
 
 #define TT_OFF_A 0                              // [2][128 x 8] TF32
 #define TT_OFF_B (TT_OFF_A + 8192)              // [2][128 x 8] TF32
@@ -43,7 +45,8 @@
 #define TT_OFF_IDX (TT_OFF_RAW + TT_S * 2048)   // [TT_S][128] int32
 #define TT_OFF_BAR (TT_OFF_IDX + TT_S * 512)    // barriers + CTA scalars (512 B)
 #define TT_OFF_SEG (TT_OFF_BAR + 512)           // [128][4] float4 seed records
-#define TT_OFF_ROWS (TT_OFF_SEG + 8192)         // [TT_RMAX] int4 row runs
+#define TT_OFF_TMP (TT_OFF_SEG + 8192)          // [32] int2 runs of one batch of keys
+#define TT_OFF_ROWS (TT_OFF_TMP + 256)          // [TT_RMAX] int4 runs of points
 #define TT_OFF_LIST (TT_OFF_ROWS + TT_RMAX * 16) // [L][128] keys
 
 #define TT_BAR_RAW 0
@@ -99,10 +102,12 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_tnn_tc(const __grid_constant_
     int *s_nrows = (int *)(sc + 16);
     int *s_nch = (int *)(sc + 20);
     float *s_red = (float *)(sc + 32); // [4 warps][16]
-    float4 *segs = (float4 *)(smem + TT_OFF_SEG);
+    float4 *sseg = (float4 *)(smem + TT_OFF_SEG);
+    int *kst = (int *)(smem + TT_OFF_ROWS);      // seed keys: exclusive starts [32]
+    int *klo = (int *)(smem + TT_OFF_ROWS) + 32; //            their first record [32]
+    int2 *tmp = (int2 *)(smem + TT_OFF_TMP);
     int4 *rows = (int4 *)(smem + TT_OFF_ROWS);
-    int *kst = (int *)(smem + TT_OFF_ROWS);       // seed keys: exclusive starts [32]
-    int *klo = (int *)(smem + TT_OFF_ROWS) + 32;  //            their first record [32]
+    int *s_kc = (int *)(sc + 24); // key cursor of the bucket's rectangle
     unsigned long long *K = (unsigned long long *)(smem + TT_OFF_LIST) + tq;
     unsigned long long *cl_d = (unsigned long long *)(smem + TT_OFF_A + (warp & 3) * 3072) + lane;
     int *cl_i = (int *)(smem + TT_OFF_A + (warp & 3) * 3072 + CMAX * 32 * 8) + lane;
@@ -199,7 +204,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_tnn_tc(const __grid_constant_
         const float bx0 = ex[0], bx1 = -ex[1], by0 = ex[2], by1 = -ex[3];
         const float cc[4] = {0.5f * ex[4] - 0.5f * ex[5], 0.5f * ex[6] - 0.5f * ex[7], 0.5f * ex[8] - 0.5f * ex[9],
                              0.5f * ex[10] - 0.5f * ex[11]};
-        const float tmax = -ex[12], dmax = -ex[13];
+        const float tmax = -ex[12], dmax = -ex[13], tqmin = ex[10];
         int bhi = -1;
         {
             const float fb = (tmax - G.t0) * G.inv_dt;
@@ -259,18 +264,18 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_tnn_tc(const __grid_constant_
                     while (j + 1 < 18 && kst[j + 1] <= gidx)
                         ++j;
                     const float4 *r = G.gseg + 4 * (size_t)(klo[j] + (gidx - kst[j]));
-                    segs[4 * tq] = __ldg(r);
-                    segs[4 * tq + 1] = __ldg(r + 1);
-                    segs[4 * tq + 2] = __ldg(r + 2);
-                    segs[4 * tq + 3] = __ldg(r + 3);
+                    sseg[4 * tq] = __ldg(r);
+                    sseg[4 * tq + 1] = __ldg(r + 1);
+                    sseg[4 * tq + 2] = __ldg(r + 2);
+                    sseg[4 * tq + 3] = __ldg(r + 3);
                 }
                 __syncthreads();
                 if (inq) {
                     for (int i = 0; i < cnt; ++i) {
-                        const float lb = seg_lb(c, s3, segs[4 * i], segs[4 * i + 1], segs[4 * i + 2]);
+                        const float lb = seg_lb(c, s3, sseg[4 * i], sseg[4 * i + 1], sseg[4 * i + 2]);
                         if (lb < wF) {
                             float cur = lb;
-                            int cf = __float_as_int(segs[4 * i + 3].x), cn = __float_as_int(segs[4 * i + 3].y);
+                            int cf = __float_as_int(sseg[4 * i + 3].x), cn = __float_as_int(sseg[4 * i + 3].y);
 #pragma unroll
                             for (int f = 0; f < TNN_GMAX_F; ++f) {
                                 if (f < F && cur < bl[f]) {
@@ -368,84 +373,91 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_tnn_tc(const __grid_constant_
                 cy0 = max((int)floorf(fmaxf((by0 - R - G.y0) * G.inv_cell, -1.0f)) - 1, 0);
                 cy1 = min((int)floorf(fminf((by1 + R - G.y0) * G.inv_cell, (float)G.ny)) + 1, G.ny - 1);
             }
-            if (cx0 > cx1) // the reach misses the grid in x (queries far outside it)
+            if (cx0 > cx1 || cy0 > cy1) // the reach misses the grid (queries far outside it)
                 continue;
-            for (int ya = cy0; ya <= cy1; ya += TT_RMAX) {
-                const int yb = min(cy1 + 1, ya + TT_RMAX);
-                // runs of the rows [ya, yb): one contiguous run of points each
+            const int wx = cx1 - cx0 + 1, nkr = (cy1 - cy0 + 1) * wx;
+            if (t == 0)
+                *s_kc = 0;
+            __syncthreads();
+            for (;;) {
+                // runs of the needed keys from the cursor on, at most TT_RMAX
                 if (warp == 0) {
-                    int nr = 0, nc = 0;
-                    for (int yy = ya; yy < yb; yy += 32) {
-                        const int cy = yy + lane;
+                    int kc = *s_kc, nr = 0, nc = 0;
+                    int olo = -1, ohi = -1; // lane 0: the open run
+                    while (kc < nkr && nr < TT_RMAX - 32) {
+                        const int tk = kc + lane;
+                        bool need = false;
                         int p0 = 0, p1 = 0;
-                        if (cy < yb) {
-                            const int k0 = b * G.ncell + cy * G.nx + cx0;
-                            const int k1 = b * G.ncell + cy * G.nx + cx1;
-                            p0 = __ldg(ks + k0);
-                            p1 = __ldg(ks + k1 + 1);
+                        if (tk < nkr) {
+                            const int cy = cy0 + tk / wx, cx = cx0 + tk % wx;
+                            const int key = b * G.ncell + cy * G.nx + cx;
+                            const int4 kr = __ldg(G.krec + key);
+                            if (kr.y > kr.x) {
+                                // bound of the key against the CTA's box
+                                const float rx0 = G.x0 + (float)cx * G.cell, ry0 = G.y0 + (float)cy * G.cell;
+                                const float ddx = fmaxf(fmaxf(rx0 - bx1, bx0 - (rx0 + G.cell)), 0.0f);
+                                const float ddy = fmaxf(fmaxf(ry0 - by1, by0 - (ry0 + G.cell)), 0.0f);
+                                const float a2 = fmaf(ddy, ddy, ddx * ddx);
+                                const float dist = a2 * rsqrtf(fmaxf(a2, 1e-37f));
+                                const float sp = fmaxf(fmaf(dist, 1.0f - 0x1p-20f, -(__int_as_float(kr.z) + dmax)), 0.0f);
+                                const float et = fmaxf(__fsub_rd(tqmin, fminf(__int_as_float(kr.w), tmax)), 0.0f);
+                                const float lb = fmaf(sp, sp, (s3 * et) * et) * (1.0f - 0x1p-19f);
+                                if (lb <= tm) {
+                                    need = true;
+                                    p0 = __ldg(ks + key);
+                                    p1 = __ldg(ks + key + 1);
+                                }
+                            }
                         }
-                        const bool ne = p1 > p0;
-                        const unsigned m = __ballot_sync(FULLMASK, ne);
-                        const int nch = ne ? (p1 - p0 + TT_P - 1) / TT_P : 0;
-                        int inc = nch;
-#pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const int v = __shfl_up_sync(FULLMASK, inc, o);
-                            if (lane >= o)
-                                inc += v;
+                        const unsigned m = __ballot_sync(FULLMASK, need && p1 > p0);
+                        if (need && p1 > p0)
+                            tmp[__popc(m & ((1u << lane) - 1u))] = make_int2(p0, p1);
+                        __syncwarp();
+                        if (lane == 0) {
+                            // consecutive keys are contiguous runs: merge them
+                            const int cnt = __popc(m);
+                            for (int u = 0; u < cnt; ++u) {
+                                const int2 r = tmp[u];
+                                if (r.x == ohi) {
+                                    ohi = r.y;
+                                } else {
+                                    if (olo >= 0) {
+                                        const int nchr = (ohi - olo + TT_P - 1) / TT_P;
+                                        rows[nr++] = make_int4(olo, ohi, nc, 0);
+                                        nc += nchr;
+                                    }
+                                    olo = r.x;
+                                    ohi = r.y;
+                                }
+                            }
                         }
-                        if (ne)
-                            rows[nr + __popc(m & ((1u << lane) - 1u))] = make_int4(p0, p1, nc + inc - nch, 0);
-                        nr += __popc(m);
-                        nc += __shfl_sync(FULLMASK, inc, 31);
+                        __syncwarp();
+                        nr = __shfl_sync(FULLMASK, nr, 0);
+                        nc = __shfl_sync(FULLMASK, nc, 0);
+                        kc += 32;
                     }
                     if (lane == 0) {
+                        if (olo >= 0) {
+                            rows[nr++] = make_int4(olo, ohi, nc, 0);
+                            nc += (ohi - olo + TT_P - 1) / TT_P;
+                        }
                         *s_nrows = nr;
                         *s_nch = nc;
+                        *s_kc = min(kc, nkr);
                     }
                 }
                 __syncthreads();
-                const int nrows = *s_nrows, nch = *s_nch;
+                const int nrows = *s_nrows, nch = *s_nch, kdone = *s_kc;
                 // every thread has read the counts before warp 0 may write
                 // the next pass's
                 __syncthreads();
-                if (nch == 0)
-                    continue;
-
-                if (ctrl) {
-                    // ---- control thread: copies and MMAs
-                    if (lane == 0) {
-                        int curp = 0;
-                        const int pre = min(nch, TT_S - 2);
-                        for (int j = 0; j < pre; ++j) {
-                            const long long gj = g + j;
-                            int lo, hi;
-                            tt_chunk(rows, nrows, j, curp, lo, hi);
-                            tt_load_chunk(pk, ik, lo, hi, su32(raw + (gj % TT_S) * TT_P),
-                                          su32(sidx + (gj % TT_S) * TT_P), BAR(TT_BAR_RAW + gj % TT_S));
-                            issued = gj;
-                        }
-                        for (int i = 0; i < nch; ++i) {
-                            const long long gi = g + i;
-                            const int bb = (int)(gi & 1);
-                            if (!mbar_wait(BAR(TT_BAR_BFULL + bb), (uint32_t)((gi >> 1) & 1), s_err))
-                                break;
-                            if (gi >= 2 && !mbar_wait(BAR(TT_BAR_USED + (gi - 2) % TT_S),
-                                                      (uint32_t)(((gi - 2) / TT_S) & 1), s_err))
-                                break;
-                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                            const uint64_t da = umma_desc(su32(sA + bb * 4096));
-                            const uint64_t db = umma_desc(su32(sB + bb * 4096));
-                            asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-                                         ::"r"(tmem + (uint32_t)(bb * TT_P)), "l"(da), "l"(db), "r"(idesc),
-                                         "r"(0));
-                            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                                         ::"r"(BAR(TT_BAR_ACC + bb))
-                                         : "memory");
-                            mma_last = gi;
-                            const int j = i + TT_S - 2;
-                            if (j < nch) {
+                if (nch > 0) {
+                    if (ctrl) {
+                        // ---- control thread: copies and MMAs
+                        if (lane == 0) {
+                            int curp = 0;
+                            const int pre = min(nch, TT_S - 2);
+                            for (int j = 0; j < pre; ++j) {
                                 const long long gj = g + j;
                                 int lo, hi;
                                 tt_chunk(rows, nrows, j, curp, lo, hi);
@@ -453,126 +465,157 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_tnn_tc(const __grid_constant_
                                               su32(sidx + (gj % TT_S) * TT_P), BAR(TT_BAR_RAW + gj % TT_S));
                                 issued = gj;
                             }
-                        }
-                    }
-                } else {
-                    // ---- screening warps
-                    int curb = 0, curs = 0;
-                    auto build = [&](long long gi, int i) -> bool {
-                        const int s = (int)(gi % TT_S), bb = (int)(gi & 1);
-                        const bool okw = mbar_wait(BAR(TT_BAR_RAW + s), (uint32_t)((gi / TT_S) & 1), s_err);
-                        if (!__all_sync(FULLMASK, okw))
-                            return false;
-                        int lo, hi;
-                        tt_chunk(rows, nrows, i, curb, lo, hi);
-                        float bv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                        if (tq < hi - lo) {
-                            const float4 p = raw[s * TT_P + tq];
-                            if (p.w < tmax) { // a point no query of the CTA may take keeps a zero row
-                                const float e[4] = {q0 * (p.x - cc[0]), q1 * (p.y - cc[1]), q2 * (p.z - cc[2]),
-                                                    q3 * (p.w - cc[3])};
-                                float m2 = 0.f;
-#pragma unroll
-                                for (int d = 0; d < 4; ++d)
-                                    m2 = fmaf(e[d], e[d], m2);
-                                bv[0] = tf32_rna(-2.0f * e[0]);
-                                bv[1] = tf32_rna(-2.0f * e[1]);
-                                bv[2] = tf32_rna(-2.0f * e[2]);
-                                bv[3] = tf32_rna(-2.0f * e[3]);
-                                bv[4] = 1.0f;
-                                bv[5] = tf32_rna((1.0f - TC_EPS) * m2);
-                                bv[6] = tf32_rna(-2.0f * sqrtf(m2));
-                                bv[7] = 1.0f;
+                            for (int i = 0; i < nch; ++i) {
+                                const long long gi = g + i;
+                                const int bb = (int)(gi & 1);
+                                if (!mbar_wait(BAR(TT_BAR_BFULL + bb), (uint32_t)((gi >> 1) & 1), s_err))
+                                    break;
+                                if (gi >= 2 && !mbar_wait(BAR(TT_BAR_USED + (gi - 2) % TT_S),
+                                                          (uint32_t)(((gi - 2) / TT_S) & 1), s_err))
+                                    break;
+                                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                                const uint64_t da = umma_desc(su32(sA + bb * 4096));
+                                const uint64_t db = umma_desc(su32(sB + bb * 4096));
+                                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                                             ::"r"(tmem + (uint32_t)(bb * TT_P)), "l"(da), "l"(db), "r"(idesc),
+                                             "r"(0));
+                                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                             ::"r"(BAR(TT_BAR_ACC + bb))
+                                             : "memory");
+                                mma_last = gi;
+                                const int j = i + TT_S - 2;
+                                if (j < nch) {
+                                    const long long gj = g + j;
+                                    int lo, hi;
+                                    tt_chunk(rows, nrows, j, curp, lo, hi);
+                                    tt_load_chunk(pk, ik, lo, hi, su32(raw + (gj % TT_S) * TT_P),
+                                                  su32(sidx + (gj % TT_S) * TT_P), BAR(TT_BAR_RAW + gj % TT_S));
+                                    issued = gj;
+                                }
                             }
                         }
-                        store_row(sB + bb * 4096, tq, bv);
-                        arow[7] = active ? tc_neg_T(tau) : 0.0f;
-                        store_row(sA + bb * 4096, tq, arow);
-                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        __syncwarp();
-                        if (lane == 0)
-                            mbar_arrive(BAR(TT_BAR_BFULL + bb));
-                        return true;
-                    };
-                    bool ok = build(g, 0);
-                    for (int i = 0; ok && i < nch; ++i) {
-                        const long long gi = g + i;
-                        const int s = (int)(gi % TT_S), bb = (int)(gi & 1);
-                        if (i + 1 < nch && !build(gi + 1, i + 1))
-                            break;
-                        const bool okw = mbar_wait(BAR(TT_BAR_ACC + bb), (uint32_t)((gi >> 1) & 1), s_err);
-                        if (!__all_sync(FULLMASK, okw))
-                            break;
-                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        int lo, hi;
-                        tt_chunk(rows, nrows, i, curs, lo, hi);
-                        const int ncol = hi - lo;
-                        if (active)
-                            st.pairs += ncol;
-                        if (t == 0)
-                            st.segs++; // 128 x 128 tiles multiplied
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            uint32_t v[64];
-                            tmem_ld32_nowait(taddr_row + (uint32_t)(bb * TT_P + h * 64), v);
-                            tmem_ld32_nowait(taddr_row + (uint32_t)(bb * TT_P + h * 64 + 32), v + 32);
-                            tmem_wait_ld();
-                            uint32_t any = 0u;
-#pragma unroll
-                            for (int j = 0; j < 64; ++j)
-                                any |= v[j];
-                            const int lim = ncol - h * 64;
-                            if ((int)any < 0 && lim > 0) {
-                                uint32_t m0 = 0u, m1 = 0u;
-#pragma unroll
-                                for (int j = 0; j < 32; ++j) {
-                                    m0 |= (v[j] >> 31) << j;
-                                    m1 |= (v[32 + j] >> 31) << j;
+                    } else {
+                        // ---- screening warps
+                        int curb = 0, curs = 0;
+                        auto build = [&](long long gi, int i) -> bool {
+                            const int s = (int)(gi % TT_S), bb = (int)(gi & 1);
+                            const bool okw = mbar_wait(BAR(TT_BAR_RAW + s), (uint32_t)((gi / TT_S) & 1), s_err);
+                            if (!__all_sync(FULLMASK, okw))
+                                return false;
+                            int lo, hi;
+                            tt_chunk(rows, nrows, i, curb, lo, hi);
+                            float bv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                            if (tq < hi - lo) {
+                                const float4 p = raw[s * TT_P + tq];
+                                if (p.w < tmax) { // a point no query of the CTA may take keeps a zero row
+                                    const float e[4] = {q0 * (p.x - cc[0]), q1 * (p.y - cc[1]), q2 * (p.z - cc[2]),
+                                                        q3 * (p.w - cc[3])};
+                                    float m2 = 0.f;
+    #pragma unroll
+                                    for (int d = 0; d < 4; ++d)
+                                        m2 = fmaf(e[d], e[d], m2);
+                                    bv[0] = tf32_rna(-2.0f * e[0]);
+                                    bv[1] = tf32_rna(-2.0f * e[1]);
+                                    bv[2] = tf32_rna(-2.0f * e[2]);
+                                    bv[3] = tf32_rna(-2.0f * e[3]);
+                                    bv[4] = 1.0f;
+                                    bv[5] = tf32_rna((1.0f - TC_EPS) * m2);
+                                    bv[6] = tf32_rna(-2.0f * sqrtf(m2));
+                                    bv[7] = 1.0f;
                                 }
-                                if (lim <= 32) {
-                                    m1 = 0u;
-                                    if (lim < 32)
-                                        m0 &= (1u << lim) - 1u;
-                                } else if (lim < 64) {
-                                    m1 &= (1u << (lim - 32)) - 1u;
-                                }
-#pragma unroll
-                                for (int part = 0; part < 2; ++part) {
-                                    uint32_t msk = part ? m1 : m0;
-                                    while (msk) {
-                                        const int col = h * 64 + part * 32 + __ffs(msk) - 1;
-                                        msk &= msk - 1u;
-                                        const int j = sidx[s * TT_P + col];
-                                        if (j < 0)
-                                            continue; // padding
-                                        bool seed = false;
-#pragma unroll
-                                        for (int f = 0; f < TNN_GMAX_F; ++f)
-                                            seed |= f < F && j >= bf[f] && j < bf[f] + bc[f];
-                                        if (seed)
-                                            continue; // scanned in the seed phase
-                                        const float4 p = raw[s * TT_P + col];
-                                        const float d = dist32(c, s0, s1, s2, s3, p);
-                                        st.lb++; // screened points scored again in FP32
-                                        if (p.w < c.T32 && d <= tau) {
-                                            const unsigned long long key = pack_key(d, j);
-                                            if (key < tauk) {
-                                                tauk = list_push<TT_Q>(K, Lw, nv, key);
-                                                tau = key_d(tauk);
+                            }
+                            store_row(sB + bb * 4096, tq, bv);
+                            arow[7] = active ? tc_neg_T(tau) : 0.0f;
+                            store_row(sA + bb * 4096, tq, arow);
+                            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                            __syncwarp();
+                            if (lane == 0)
+                                mbar_arrive(BAR(TT_BAR_BFULL + bb));
+                            return true;
+                        };
+                        bool ok = build(g, 0);
+                        for (int i = 0; ok && i < nch; ++i) {
+                            const long long gi = g + i;
+                            const int s = (int)(gi % TT_S), bb = (int)(gi & 1);
+                            if (i + 1 < nch && !build(gi + 1, i + 1))
+                                break;
+                            const bool okw = mbar_wait(BAR(TT_BAR_ACC + bb), (uint32_t)((gi >> 1) & 1), s_err);
+                            if (!__all_sync(FULLMASK, okw))
+                                break;
+                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                            int lo, hi;
+                            tt_chunk(rows, nrows, i, curs, lo, hi);
+                            const int ncol = hi - lo;
+                            if (active)
+                                st.pairs += ncol;
+                            if (t == 0)
+                                st.segs++; // 128 x 128 tiles multiplied
+    #pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                uint32_t v[64];
+                                tmem_ld32_nowait(taddr_row + (uint32_t)(bb * TT_P + h * 64), v);
+                                tmem_ld32_nowait(taddr_row + (uint32_t)(bb * TT_P + h * 64 + 32), v + 32);
+                                tmem_wait_ld();
+                                uint32_t any = 0u;
+    #pragma unroll
+                                for (int j = 0; j < 64; ++j)
+                                    any |= v[j];
+                                const int lim = ncol - h * 64;
+                                if ((int)any < 0 && lim > 0) {
+                                    uint32_t m0 = 0u, m1 = 0u;
+    #pragma unroll
+                                    for (int j = 0; j < 32; ++j) {
+                                        m0 |= (v[j] >> 31) << j;
+                                        m1 |= (v[32 + j] >> 31) << j;
+                                    }
+                                    if (lim <= 32) {
+                                        m1 = 0u;
+                                        if (lim < 32)
+                                            m0 &= (1u << lim) - 1u;
+                                    } else if (lim < 64) {
+                                        m1 &= (1u << (lim - 32)) - 1u;
+                                    }
+    #pragma unroll
+                                    for (int part = 0; part < 2; ++part) {
+                                        uint32_t msk = part ? m1 : m0;
+                                        while (msk) {
+                                            const int col = h * 64 + part * 32 + __ffs(msk) - 1;
+                                            msk &= msk - 1u;
+                                            const int j = sidx[s * TT_P + col];
+                                            if (j < 0)
+                                                continue; // padding
+                                            bool seed = false;
+    #pragma unroll
+                                            for (int f = 0; f < TNN_GMAX_F; ++f)
+                                                seed |= f < F && j >= bf[f] && j < bf[f] + bc[f];
+                                            if (seed)
+                                                continue; // scanned in the seed phase
+                                            const float4 p = raw[s * TT_P + col];
+                                            const float d = dist32(c, s0, s1, s2, s3, p);
+                                            st.lb++; // screened points scored again in FP32
+                                            if (p.w < c.T32 && d <= tau) {
+                                                const unsigned long long key = pack_key(d, j);
+                                                if (key < tauk) {
+                                                    tauk = list_push<TT_Q>(K, Lw, nv, key);
+                                                    tau = key_d(tauk);
+                                                }
                                             }
                                         }
                                     }
                                 }
                             }
+                            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                            __syncwarp();
+                            if (lane == 0)
+                                mbar_arrive(BAR(TT_BAR_USED + s));
                         }
-                        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                        __syncwarp();
-                        if (lane == 0)
-                            mbar_arrive(BAR(TT_BAR_USED + s));
                     }
+                    g += nch;
                 }
-                g += nch;
                 __syncthreads();
+                if (kdone >= nkr || *s_err)
+                    break;
             }
         }
         __syncthreads();
