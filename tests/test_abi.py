@@ -89,3 +89,32 @@ def test_host_pipeline_and_memory_argument_errors(lib):
     assert st == 1 and b"keep_bytes" in L.tnn_last_error()
     st = L.tnn_memory_reserved(None, None)
     assert st == 1 and b"NULL" in L.tnn_last_error()
+
+
+def test_measurement_and_baseline_entry_points_check_arguments(lib):
+    from paper_2112_10408_gb300 import tnn
+    L = tnn.load_library()
+    ops, ms = ctypes.c_double(), ctypes.c_double()
+    st = L.tnn_probe_fp32(0, ctypes.byref(ops), ctypes.byref(ms), None)
+    assert st == 1 and b"iters" in L.tnn_last_error()
+    st = L.tnn_probe_fp32(64, None, None, None)
+    assert st == 1 and b"NULL" in L.tnn_last_error()
+    st = L.tnn_selftest_bounded_wait(0, None)
+    assert st == 1 and b"limit_us" in L.tnn_last_error()
+    st = L.tnn_selftest_bounded_wait(2000000, None)
+    assert st == 1 and b"limit_us" in L.tnn_last_error()
+    buf = (ctypes.c_float * 8)()
+    st = L.tnn_window_average(None, buf, None, 4, 5400.0, 1800.0, buf, None)
+    assert st == 1 and b"NULL" in L.tnn_last_error()
+    assert L.tnn_mlp_save(None, b"x.bin") == 1 and b"NULL" in L.tnn_last_error()
+    assert L.tnn_mlp_load(None, b"x.bin") == 1 and b"NULL" in L.tnn_last_error()
+    kp = tnn.make_knn_params(8)
+    st = L.tnn_knn_trace(ctypes.c_void_p(8), None, 10, ctypes.byref(kp), buf, buf, None, None, None)
+    assert st == 1 and b"d_path" in L.tnn_last_error()
+    st = L.tnn_knn_work_split(ctypes.c_void_p(8), None, 10, 8, 0.0, buf, None, None, None)
+    assert st == 1 and b"h_work" in L.tnn_last_error()
+    # nothing recorded yet: zero time, zero launches
+    k3 = (ctypes.c_double * 3)()
+    n = ctypes.c_int64(-1)
+    assert L.tnn_profile_read_kernels(k3, ctypes.byref(n), 1) == 0
+    assert n.value == 0 and list(k3) == [0.0, 0.0, 0.0]

@@ -518,3 +518,15 @@ def test_tensor_core_candidate_tiles_medium_and_precision_sampled():
         ti, td = tnn.tnn_knn(ix, 32, 0.0)
         assert torch.equal(ti, ci)
         ix.destroy()
+
+
+def test_tensor_core_tiles_flag_is_for_single_searches():
+    wl = synth.flights(20, 40, seed=3, n_routes=2)
+    ix = _index(wl, 10)
+    with pytest.raises(tnn.TNNError) as ei:
+        tnn.Batch([ix, ix], [8, 8], tunings=[dict(tc=True), {}])
+    assert ei.value.status == 1
+    # the sweep order takes precedence over the tiles and is still exact
+    si, sd = tnn.tnn_knn(ix, 8, 0.0, sweep=True, tc=True)
+    oi, od = oracle.knn(wl.xyzt, 8, SIG)
+    assert_knn_equal(si.cpu().numpy(), sd.cpu().numpy(), oi, od, what="sweep with tc flag")

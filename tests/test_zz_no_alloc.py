@@ -94,3 +94,16 @@ def test_noalloc_at_exact_capacity_and_in_sweep_order(lib):
         _same(_noalloc(lib, ix, 16, 30.0, q2, q2.shape[0], sweep=True), ref2)
     # nothing the kernels flagged is pending
     tnn.tnn_sync_status()
+
+
+def test_noalloc_rejects_the_tensor_core_tiles_flag(lib):
+    # the tiles read a key-ordered copy of the points that the index builds
+    # on first use, i.e. an allocation: this entry point refuses the flag
+    wl = synth.flights(20, 40, seed=4, n_routes=2)
+    ix = tnn.tnn_build_segments(torch.from_numpy(wl.xyzt).cuda(), wl.traj_off, SIG, 10)
+    p = tnn.make_knn_params(8, tc=True)
+    idx = torch.empty((wl.n, 8), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((wl.n, 8), dtype=torch.float32, device="cuda")
+    st = lib.tnn_knn_noalloc(ix.handle, None, wl.n, ctypes.byref(p), tnn._ptr(idx), tnn._ptr(d2),
+                             tnn._stream())
+    assert st == 1 and b"TNN_FLAG_TC_TILES" in lib.tnn_last_error()
