@@ -172,6 +172,19 @@ def _peaks():
         return {}
 
 
+def _cpu_model():
+    """The host CPU's model name (lscpu), for the oracle's timing lines."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
 def _parity(gi, gd, oi, od):
     """Sampled GPU rows against the oracle's: identical neighbour indices
     (ties by index), and the largest relative error of the reported FP32
@@ -199,7 +212,7 @@ def _cpu_baseline(wl, k, n_sample, idx=None, d2=None, lag=0.0, seed=0x5A00):
     oi, od, o64 = oracle.knn(wl.xyzt, k, (1.0, 1.0, 10.0, 0.01), lag=lag, qsel=q, nthreads=cores,
                              want_d64=True)
     dt = time.perf_counter() - t0
-    out = {"value": q.size / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    out = {"value": q.size / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": _cpu_model(),
            "sample": f"{q.size} uniformly sampled self-queries of the same workload "
                      f"(FP64 brute force, {cores} threads, {dt:.2f} s)"}
     if idx is not None:
@@ -279,6 +292,7 @@ def run_reference(a):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": _config(wl, k, K, a.workload), "impl": "reference",
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "cpu": _cpu_model(),
                             "sample": f"each step: {per_step} uniformly sampled self-queries "
                                       f"(FP64 brute-force oracle, {cores} threads)"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
