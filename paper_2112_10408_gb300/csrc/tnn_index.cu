@@ -139,44 +139,49 @@ __global__ void k_segment_fit(const float4 *__restrict__ p,
         AB[i] = (double)ABf[i];
         E[i] = A[i] + AB[i];
     }
-    double ab2 = AB[0] * AB[0] + AB[1] * AB[1] + AB[2] * AB[2];
-    double r2 = 0.0, mag = fabs(A[0]) + fabs(A[1]) + fabs(A[2]) +
-                          fabs(E[0]) + fabs(E[1]) + fabs(E[2]);
+    const double ab2 = AB[0] * AB[0] + AB[1] * AB[1] + AB[2] * AB[2];
+    // Any lam in [0, 1] names a point of the segment, so the distance to it
+    // bounds the distance to the segment from above: lam = dot / |AB|^2 may
+    // take the reciprocal (one division per lane, not one per member).
+    const double inv_ab2 = ab2 > 0.0 ? 1.0 / ab2 : 0.0;
+    // mag only scales the rounding slack below, which is about a thousand
+    // times the FP64 error of the distances; FP32 is ample for it.
+    const float qf[3] = {(float)q0, (float)q1, (float)q2};
+    float mag = fabsf(Af[0]) + fabsf(Af[1]) + fabsf(Af[2]) + fabsf((float)E[0]) +
+                fabsf((float)E[1]) + fabsf((float)E[2]);
+    double r2 = 0.0;
     for (int j = sub; j < (valid ? count : 0); j += 4) {
-        float4 v = p[first + j];
-        double P[3] = {qq[0] * (double)v.x, qq[1] * (double)v.y, qq[2] * (double)v.z};
-        double lam = 0.0;
-        if (ab2 > 0.0) {
-            lam = ((P[0] - A[0]) * AB[0] + (P[1] - A[1]) * AB[1] +
-                   (P[2] - A[2]) * AB[2]) / ab2;
-            lam = fmin(fmax(lam, 0.0), 1.0);
-        }
-        double d2 = 0.0;
-        for (int i = 0; i < 3; ++i) {
-            double e = P[i] - (A[i] + lam * AB[i]);
-            d2 += e * e;
-        }
-        r2 = fmax(r2, d2);
-        mag = fmax(mag, fabs(P[0]) + fabs(P[1]) + fabs(P[2]));
+        const float4 v = p[first + j];
+        const double D0 = qq[0] * (double)v.x - A[0], D1 = qq[1] * (double)v.y - A[1],
+                     D2 = qq[2] * (double)v.z - A[2];
+        const double lam = fmin(fmax((D0 * AB[0] + D1 * AB[1] + D2 * AB[2]) * inv_ab2, 0.0), 1.0);
+        const double e0 = D0 - lam * AB[0], e1 = D1 - lam * AB[1], e2 = D2 - lam * AB[2];
+        r2 = fmax(r2, e0 * e0 + e1 * e1 + e2 * e2);
+        mag = fmaxf(mag, fabsf(qf[0] * v.x) + fabsf(qf[1] * v.y) + fabsf(qf[2] * v.z));
     }
     for (int o = 1; o < 4; o <<= 1) {
         r2 = fmax(r2, __shfl_xor_sync(0xffffffffu, r2, o));
-        mag = fmax(mag, __shfl_xor_sync(0xffffffffu, mag, o));
+        mag = fmaxf(mag, __shfl_xor_sync(0xffffffffu, mag, o));
     }
-    if (!valid || sub != 0)
-        return;
-    for (int i = 0; i < 3; ++i)
-        Uf[i] = ab2 > 1e-30 ? (float)(AB[i] / ab2) : 0.f;
-    // FP64 rounding of the distances above is far below 1e-12 * mag.
-    double r = sqrt(r2) + 1e-12 * (1.0 + mag);
-    float rf = __double2float_ru(r);
-    rec[4 * s + 0] = make_float4(Af[0], Af[1], Af[2], pa.w);
-    rec[4 * s + 1] = make_float4(Uf[0], Uf[1], Uf[2], pb.w);
-    rec[4 * s + 2] = make_float4(ABf[0], ABf[1], ABf[2], rf);
-    rec[4 * s + 3] = make_float4(__int_as_float(first), __int_as_float(count),
-                                 __int_as_float(tr), __int_as_float(s));
-    keys[s] = ((unsigned long long)f2ord(pa.w) << 32) | (unsigned)s;
-    atomicMax(rmax_bits, __float_as_uint(rf));
+    const bool writer = valid && sub == 0;
+    unsigned int rbits = 0u;
+    if (writer) {
+        for (int i = 0; i < 3; ++i)
+            Uf[i] = ab2 > 1e-30 ? (float)(AB[i] / ab2) : 0.f;
+        // FP64 rounding of the distances above is far below 1e-12 * mag.
+        const double r = sqrt(r2) + 1e-12 * (1.0 + (double)mag);
+        const float rf = __double2float_ru(r);
+        rbits = __float_as_uint(rf); // rf >= 0: the bits order like the values
+        rec[4 * s + 0] = make_float4(Af[0], Af[1], Af[2], pa.w);
+        rec[4 * s + 1] = make_float4(Uf[0], Uf[1], Uf[2], pb.w);
+        rec[4 * s + 2] = make_float4(ABf[0], ABf[1], ABf[2], rf);
+        rec[4 * s + 3] = make_float4(__int_as_float(first), __int_as_float(count),
+                                     __int_as_float(tr), __int_as_float(s));
+        keys[s] = ((unsigned long long)f2ord(pa.w) << 32) | (unsigned)s;
+    }
+    rbits = __reduce_max_sync(0xffffffffu, rbits); // one atomic per warp
+    if ((threadIdx.x & 31) == 0 && rbits != 0u)
+        atomicMax(rmax_bits, rbits);
 }
 
 __global__ void k_time_keys(const float4 *__restrict__ p, int n,
@@ -197,8 +202,17 @@ __global__ void k_fill(unsigned long long *keys, int from, int n2)
 }
 
 // ------------------------------------------------------------ bitonic sort
+//
+// Batcher's bitonic network on n2 = 2^p 64-bit keys, ascending.  Step (k, j)
+// compares positions i and i + j (bit j of i clear) and puts the smaller key
+// first when bit k of i is clear, last otherwise.  Every kernel below keeps
+// four consecutive keys per thread in registers: steps j = 1, 2 stay inside a
+// thread, steps 4 <= j <= 64 inside a warp (shuffles, no barrier), steps
+// 128 <= j < block size go through shared memory, and larger steps through
+// distributed shared memory (cluster) or global memory.
 
-#define BS_BLOCK 2048
+#define BS_MIN 2048  // smallest n2 handed out (a cluster of 8 x 256 keys)
+#define BS_BLOCK 4096 // keys per CTA of the multi-launch path (1024 threads)
 
 __device__ __forceinline__ void cmpx(unsigned long long &a,
                                      unsigned long long &b, bool asc)
@@ -210,44 +224,90 @@ __device__ __forceinline__ void cmpx(unsigned long long &a,
     }
 }
 
-// Full bitonic sort of every 2048-element block (direction of each block
-// follows its global position, as the network requires).
-__global__ void k_bitonic_block(unsigned long long *keys)
+__device__ __forceinline__ void bs_load4(unsigned long long (&r)[4], const unsigned long long *p)
 {
-    __shared__ unsigned long long s[BS_BLOCK];
-    const int base = blockIdx.x * BS_BLOCK;
-    s[threadIdx.x] = keys[base + threadIdx.x];
-    s[threadIdx.x + 1024] = keys[base + threadIdx.x + 1024];
-    __syncthreads();
-    for (int k = 2; k <= BS_BLOCK; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            int t = threadIdx.x;
-            int i = ((t & ~(j - 1)) << 1) | (t & (j - 1)); // j is a power of two
-            bool asc = ((base + i) & k) == 0;
-            cmpx(s[i], s[i + j], asc);
-            __syncthreads();
-        }
-    keys[base + threadIdx.x] = s[threadIdx.x];
-    keys[base + threadIdx.x + 1024] = s[threadIdx.x + 1024];
+    const ulonglong2 a = ((const ulonglong2 *)p)[0], b = ((const ulonglong2 *)p)[1];
+    r[0] = a.x;
+    r[1] = a.y;
+    r[2] = b.x;
+    r[3] = b.y;
 }
 
-// Steps j < 2048 of merge stage k, inside each block.
-__global__ void k_bitonic_merge_local(unsigned long long *keys, int k)
+__device__ __forceinline__ void bs_store4(unsigned long long *p, const unsigned long long (&r)[4])
 {
-    __shared__ unsigned long long s[BS_BLOCK];
-    const int base = blockIdx.x * BS_BLOCK;
-    s[threadIdx.x] = keys[base + threadIdx.x];
-    s[threadIdx.x + 1024] = keys[base + threadIdx.x + 1024];
-    __syncthreads();
-    for (int j = BS_BLOCK >> 1; j > 0; j >>= 1) {
-        int t = threadIdx.x;
-        int i = ((t & ~(j - 1)) << 1) | (t & (j - 1)); // j is a power of two
-        bool asc = ((base + i) & k) == 0;
-        cmpx(s[i], s[i + j], asc);
-        __syncthreads();
+    ((ulonglong2 *)p)[0] = make_ulonglong2(r[0], r[1]);
+    ((ulonglong2 *)p)[1] = make_ulonglong2(r[2], r[3]);
+}
+
+// Steps j, j/2, ..., 1 (j <= 64) of stage k on the four keys at global
+// positions g0 .. g0 + 3 (g0 a multiple of 4); the partner of a key at
+// distance j >= 4 sits in lane ^ (j / 4) of the same warp.
+__device__ __forceinline__ void bs_warp_steps(unsigned long long (&r)[4], int g0, int k, int j)
+{
+    for (; j >= 4; j >>= 1) {
+        const int ld = j >> 2;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const unsigned long long w = __shfl_xor_sync(0xffffffffu, r[e], ld);
+            const int g = g0 + e;
+            const bool take_min = ((g & j) == 0) == ((g & k) == 0);
+            const bool w_lt = w < r[e];
+            r[e] = (take_min == w_lt) ? w : r[e];
+        }
     }
-    keys[base + threadIdx.x] = s[threadIdx.x];
-    keys[base + threadIdx.x + 1024] = s[threadIdx.x + 1024];
+    if (j >= 2) { // k >= 4: the four keys share bit k
+        const bool asc = (g0 & k) == 0;
+        cmpx(r[0], r[2], asc);
+        cmpx(r[1], r[3], asc);
+    }
+    cmpx(r[0], r[1], (g0 & k) == 0);
+    cmpx(r[2], r[3], ((g0 + 2) & k) == 0);
+}
+
+// Steps j, j/2, ..., 1 (j < nl) of stage k on a CTA's nl consecutive keys
+// starting at global position gb, held four per thread (nl / 4 threads);
+// s has room for nl keys.
+__device__ __forceinline__ void bs_local_steps(unsigned long long (&r)[4], unsigned long long *s,
+                                               int nl, int gb, int k, int j)
+{
+    const int t = threadIdx.x, nt = nl >> 2;
+    if (j >= 128) {
+        bs_store4(s + 4 * t, r);
+        __syncthreads();
+        for (; j >= 128; j >>= 1) {
+            for (int q = t; q < (nl >> 1); q += nt) {
+                const int i = ((q & ~(j - 1)) << 1) | (q & (j - 1)); // j is a power of two
+                cmpx(s[i], s[i + j], ((gb + i) & k) == 0);
+            }
+            __syncthreads();
+        }
+        bs_load4(r, s + 4 * t); // each thread rereads only its own four slots
+    }
+    bs_warp_steps(r, gb + 4 * t, k, j);
+}
+
+// Stages 2 .. BS_BLOCK, each 4096-key block on its own (the direction of a
+// block follows its global position, as the network requires).
+__global__ void __launch_bounds__(BS_BLOCK / 4) k_bitonic_block(unsigned long long *keys)
+{
+    __shared__ __align__(16) unsigned long long s[BS_BLOCK];
+    const int base = blockIdx.x * BS_BLOCK;
+    unsigned long long r[4];
+    bs_load4(r, keys + base + 4 * threadIdx.x);
+    for (int k = 2; k <= BS_BLOCK; k <<= 1)
+        bs_local_steps(r, s, BS_BLOCK, base, k, k >> 1);
+    bs_store4(keys + base + 4 * threadIdx.x, r);
+}
+
+// Steps j < BS_BLOCK of stage k, inside each block.
+__global__ void __launch_bounds__(BS_BLOCK / 4) k_bitonic_merge_local(unsigned long long *keys, int k)
+{
+    __shared__ __align__(16) unsigned long long s[BS_BLOCK];
+    const int base = blockIdx.x * BS_BLOCK;
+    unsigned long long r[4];
+    bs_load4(r, keys + base + 4 * threadIdx.x);
+    bs_local_steps(r, s, BS_BLOCK, base, k, BS_BLOCK >> 1);
+    bs_store4(keys + base + 4 * threadIdx.x, r);
 }
 
 __global__ void k_bitonic_global(unsigned long long *keys, int j, int k)
@@ -264,72 +324,63 @@ __global__ void k_bitonic_global(unsigned long long *keys, int j, int k)
 
 int tnn_next_pow2_sort(int64_t n)
 {
-    int64_t p = BS_BLOCK;
+    int64_t p = BS_MIN;
     while (p < n)
         p <<= 1;
     return (int)p;
 }
 
-// The whole network for n2 <= 32768 keys in one launch: a cluster of 8 CTAs,
-// each holding n2 / 8 consecutive keys in shared memory.  Steps whose
-// partner lies in the same CTA exchange in shared memory; steps whose
-// partner lies in another CTA (j >= n2 / 8) read it through distributed
-// shared memory between two cluster barriers (all old values read before
-// any is replaced).
+// The whole network for n2 <= 32768 keys in one launch: a cluster of 8 CTAs
+// of n2 / 32 threads, CTA c holding keys c * n2 / 8 .. (c + 1) * n2 / 8 - 1.
+// A step whose partner lies in another CTA (j >= n2 / 8) publishes the keys
+// in shared memory and reads the partner's through distributed shared memory
+// between two cluster barriers: the first makes every key visible, the
+// second keeps a CTA from overwriting (or leaving) its buffer while its
+// partner still reads it.
 #define BS_CLUSTER 8
 #define BS_CLUSTER_MAX (BS_CLUSTER * 4096)
 
 __global__ void __cluster_dims__(BS_CLUSTER, 1, 1) __launch_bounds__(1024)
     k_bitonic_cluster(unsigned long long *keys, int n2)
 {
-    __shared__ unsigned long long s[4096];
+    __shared__ __align__(16) unsigned long long s[4096];
     cg::cluster_group cluster = cg::this_cluster();
     const int c = (int)cluster.block_rank(), nl = n2 / BS_CLUSTER, base = c * nl;
-    for (int e = threadIdx.x; e < nl; e += 1024)
-        s[e] = keys[base + e];
-    __syncthreads();
+    const int g0 = base + 4 * threadIdx.x;
+    unsigned long long r[4];
+    bs_load4(r, keys + g0);
     for (int k = 2; k <= n2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j < nl) {
-                for (int q = threadIdx.x; q < nl / 2; q += 1024) {
-                    const int i = ((q & ~(j - 1)) << 1) | (q & (j - 1)); // j is a power of two
-                    cmpx(s[i], s[i + j], ((base + i) & k) == 0);
-                }
-                __syncthreads();
-            } else {
-                const unsigned long long *peer = cluster.map_shared_rank(s, c ^ (j / nl));
-                unsigned long long nv[4];
-                cluster.sync();
-                for (int e = threadIdx.x, u = 0; e < nl; e += 1024, ++u) {
-                    const int g = base + e;
-                    const unsigned long long v = s[e], w = peer[e];
-                    const bool take_min = ((g & j) == 0) == ((g & k) == 0);
-                    nv[u] = take_min ? (w < v ? w : v) : (w < v ? v : w);
-                }
-                cluster.sync();
-                for (int e = threadIdx.x, u = 0; e < nl; e += 1024, ++u)
-                    s[e] = nv[u];
-                __syncthreads();
+        int j = k >> 1;
+        for (; j >= nl; j >>= 1) {
+            const unsigned long long *peer = cluster.map_shared_rank(s, c ^ (j / nl));
+            bs_store4(s + 4 * threadIdx.x, r);
+            cluster.sync();
+            unsigned long long w[4];
+            bs_load4(w, peer + 4 * threadIdx.x);
+            const bool take_min = ((g0 & j) == 0) == ((g0 & k) == 0); // same for g0 .. g0 + 3
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const bool w_lt = w[e] < r[e];
+                r[e] = (take_min == w_lt) ? w[e] : r[e];
             }
+            cluster.sync();
         }
+        bs_local_steps(r, s, nl, base, k, j);
     }
-    for (int e = threadIdx.x; e < nl; e += 1024)
-        keys[base + e] = s[e];
-    // no CTA may leave while another still reads its shared memory
-    cluster.sync();
+    bs_store4(keys + g0, r);
 }
 
 void tnn_bitonic_sort(unsigned long long *keys, int n2, cudaStream_t st)
 {
     if (n2 <= BS_CLUSTER_MAX) {
-        k_bitonic_cluster<<<BS_CLUSTER, 1024, 0, st>>>(keys, n2);
+        k_bitonic_cluster<<<BS_CLUSTER, n2 / (4 * BS_CLUSTER), 0, st>>>(keys, n2);
         return;
     }
-    k_bitonic_block<<<n2 / BS_BLOCK, 1024, 0, st>>>(keys);
+    k_bitonic_block<<<n2 / BS_BLOCK, BS_BLOCK / 4, 0, st>>>(keys);
     for (int k = 2 * BS_BLOCK; k <= n2; k <<= 1) {
         for (int j = k >> 1; j >= BS_BLOCK; j >>= 1)
             k_bitonic_global<<<(n2 / 2 + 255) / 256, 256, 0, st>>>(keys, j, k);
-        k_bitonic_merge_local<<<n2 / BS_BLOCK, 1024, 0, st>>>(keys, k);
+        k_bitonic_merge_local<<<n2 / BS_BLOCK, BS_BLOCK / 4, 0, st>>>(keys, k);
     }
 }
 
