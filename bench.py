@@ -791,7 +791,8 @@ def _e2e_breakdown(tnn, wl, k, K, sigma, tune, h_x, h_i, h_d, reps=5):
         ev[0].record()
         d_x.copy_(h_x, non_blocking=True)
         ev[1].record()
-        ix = tnn.tnn_build_segments(d_x, wl.traj_off, sigma, K)
+        with _Range("index_build"):
+            ix = tnn.tnn_build_segments(d_x, wl.traj_off, sigma, K)
         ev[2].record()
         tnn.tnn_knn(ix, k, 0.0, out=(idx, d2), **tune)
         ev[3].record()

@@ -704,7 +704,8 @@ static void free_index(tnn_index *ix)
     void *arrays[] = {ix->pts,   ix->seg,   ix->segTA, ix->segPM, ix->pts_t,
                       ix->idx_t, ix->g_off, ix->g_ids, ix->g_seg, ix->g_ext,
                       ix->g_tB,  ix->g_krec, ix->g_bpm, ix->g_ext_max,
-                      ix->pts_k, ix->idx_k, ix->kp_start};
+                      ix->pts_k, ix->idx_k, ix->kp_start, ix->pts_m,
+                      ix->idx_m, ix->code_m};
     for (void *p : arrays)
         tnn_free(p, 0);
     delete ix;
@@ -1039,6 +1040,79 @@ tnn_status tnn_index_time_order(const tnn_index *cix, cudaStream_t st)
     }
     ix->pts_t = pts_t;
     ix->idx_t = idx_t;
+    return TNN_OK;
+}
+
+// ------------------------------------------------------------ space order
+
+__global__ void k_space_keys(const float4 *__restrict__ p, int n, float4 lo, float4 sc,
+                             unsigned long long *__restrict__ keys, int n2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        keys[i] = ((unsigned long long)tnn_morton_xyt(p[i], lo, sc) << 32) | (unsigned)i;
+    else if (i < n2)
+        keys[i] = ~0ull;
+}
+
+__global__ void k_gather_space(const unsigned long long *__restrict__ keys, const float4 *__restrict__ p,
+                               int n, float4 *__restrict__ pm, int32_t *__restrict__ im,
+                               uint32_t *__restrict__ cm)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const unsigned long long k = keys[i];
+        const int j = (int)(k & 0xffffffffull);
+        pm[i] = p[j];
+        im[i] = j;
+        cm[i] = (uint32_t)(k >> 32);
+    }
+}
+
+static std::mutex g_space_order_mu;
+
+tnn_status tnn_index_space_order(const tnn_index *cix, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(g_space_order_mu);
+    tnn_index *ix = const_cast<tnn_index *>(cix);
+    if (ix->pts_m)
+        return TNN_OK;
+    const int n = (int)ix->n, n2 = tnn_next_pow2_sort(n), tb = 256;
+    float4 *pm = nullptr;
+    int32_t *im = nullptr;
+    uint32_t *cm = nullptr;
+    DevBuf keys_d;
+    cudaError_t e = tnn_alloc((void **)&pm, sizeof(float4) * n, st);
+    if (e == cudaSuccess)
+        e = tnn_alloc((void **)&im, sizeof(int32_t) * n, st);
+    if (e == cudaSuccess)
+        e = tnn_alloc((void **)&cm, sizeof(uint32_t) * n, st);
+    if (e == cudaSuccess)
+        e = keys_d.alloc(sizeof(unsigned long long) * n2, st);
+    if (e != cudaSuccess) {
+        tnn_free(pm, st);
+        tnn_free(im, st);
+        tnn_free(cm, st);
+        tnn_set_error("space-order allocation failed: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? TNN_ERR_OOM : TNN_ERR_CUDA;
+    }
+    float4 l4, s4;
+    tnn_morton_frame(ix->bb_lo, ix->bb_hi, &l4, &s4);
+    unsigned long long *keys = (unsigned long long *)keys_d.p;
+    k_space_keys<<<(n2 + tb - 1) / tb, tb, 0, st>>>(ix->pts, n, l4, s4, keys, n2);
+    tnn_bitonic_sort(keys, n2, st);
+    k_gather_space<<<(n + tb - 1) / tb, tb, 0, st>>>(keys, ix->pts, n, pm, im, cm);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        tnn_free(pm, st);
+        tnn_free(im, st);
+        tnn_free(cm, st);
+        tnn_set_error("space order failed: %s", cudaGetErrorString(e));
+        return TNN_ERR_CUDA;
+    }
+    ix->pts_m = pm;
+    ix->idx_m = im;
+    ix->code_m = cm;
     return TNN_OK;
 }
 

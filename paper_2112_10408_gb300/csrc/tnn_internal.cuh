@@ -83,6 +83,11 @@ struct tnn_index {
     int32_t *idx_k;  // [nk + 4] input index, -1 for padding
     int32_t *kp_start; // [nb * ncell + 1] start of each key's run
     int64_t nk;
+    // Points in space-time order (the Morton key of x, y, t below; linear
+    // search thresholds; built by tnn_index_space_order on first use).
+    float4 *pts_m;    // [n]
+    int32_t *idx_m;   // [n] input index
+    uint32_t *code_m; // [n] Morton key, ascending
     GridDesc grid;   // views of the arrays below
     int32_t *g_off, *g_ids;
     float4 *g_seg;
@@ -155,6 +160,9 @@ struct KnnLaunch {
                           // tile kernel handed it over (parallel to fb_list)
     const unsigned long long *qorder; // tensor-core linear search: sorted
                                       // (space-time key << 32 | query row)
+    const float4 *seed_pts;   // linear search: the points in space-time order
+    const int32_t *seed_idx;  // (tnn_index pts_m, idx_m, code_m), or NULL
+    const uint32_t *seed_code;
     uint32_t *dbg_seen;   // tests only (tnn_knn_trace), else NULL: bit j of
                           // row q = point j's distance to query q was taken
     int64_t dbg_words;    // 32-bit words per row of dbg_seen
@@ -173,6 +181,35 @@ void tnn_free(void *p, cudaStream_t st);
 // Points in (t, index) order for the linear search, built on first use
 // (stream-ordered on `st`).
 tnn_status tnn_index_time_order(const tnn_index *ix, cudaStream_t st);
+// Points in space-time (Morton) order, built on first use.
+tnn_status tnn_index_space_order(const tnn_index *ix, cudaStream_t st);
+
+// Morton key of (x, y, t): 10 bits per axis over the points' bounding box
+// (lo, and sc = 1024 / extent, 0 for a flat axis), interleaved x, y, t.
+__device__ __forceinline__ uint32_t tnn_spread3(uint32_t v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+__device__ __forceinline__ uint32_t tnn_morton_xyt(const float4 &v, const float4 &lo, const float4 &sc)
+{
+    const uint32_t ix = (uint32_t)fminf(fmaxf((v.x - lo.x) * sc.x, 0.0f), 1023.0f);
+    const uint32_t iy = (uint32_t)fminf(fmaxf((v.y - lo.y) * sc.y, 0.0f), 1023.0f);
+    const uint32_t it = (uint32_t)fminf(fmaxf((v.w - lo.w) * sc.w, 0.0f), 1023.0f);
+    return tnn_spread3(ix) | (tnn_spread3(iy) << 1) | (tnn_spread3(it) << 2);
+}
+inline void tnn_morton_frame(const float *lo, const float *hi, float4 *l4, float4 *s4)
+{
+    *l4 = make_float4(lo[0], lo[1], lo[2], lo[3]);
+    s4->x = hi[0] > lo[0] ? 1024.0f / (hi[0] - lo[0]) : 0.0f;
+    s4->y = hi[1] > lo[1] ? 1024.0f / (hi[1] - lo[1]) : 0.0f;
+    s4->z = 0.0f;
+    s4->w = hi[3] > lo[3] ? 1024.0f / (hi[3] - lo[3]) : 0.0f;
+}
 // Points in grid-key order for the tensor-core member scan, built on first
 // use (stream-ordered on `st`).
 tnn_status tnn_index_key_order(const tnn_index *ix, cudaStream_t st);

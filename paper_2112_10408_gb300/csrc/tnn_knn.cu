@@ -216,18 +216,8 @@ tnn_status tnn_fill_window(const tnn_index *ix, const float *d_q, int64_t m,
 }
 
 // Space-time order of the queries for the tensor-core linear search: a
-// Morton key of (x, y, t), 10 bits each over the points' bounding box, above
-// the query row; rows [m, n2) are padding that sorts last.
-__device__ __forceinline__ uint32_t spread3(uint32_t v)
-{
-    v &= 0x3ffu;
-    v = (v | (v << 16)) & 0x030000ffu;
-    v = (v | (v << 8)) & 0x0300f00fu;
-    v = (v | (v << 4)) & 0x030c30c3u;
-    v = (v | (v << 2)) & 0x09249249u;
-    return v;
-}
-
+// Morton key of (x, y, t) above the query row; rows [m, n2) are padding that
+// sorts last.
 __global__ void k_query_order_keys(const float4 *__restrict__ q, int64_t m, int64_t n2,
                                    float4 lo, float4 sc, unsigned long long *__restrict__ keys)
 {
@@ -238,12 +228,7 @@ __global__ void k_query_order_keys(const float4 *__restrict__ q, int64_t m, int6
         keys[i] = ~0ull;
         return;
     }
-    const float4 v = q[i];
-    const uint32_t ix = (uint32_t)fminf(fmaxf((v.x - lo.x) * sc.x, 0.0f), 1023.0f);
-    const uint32_t iy = (uint32_t)fminf(fmaxf((v.y - lo.y) * sc.y, 0.0f), 1023.0f);
-    const uint32_t it = (uint32_t)fminf(fmaxf((v.w - lo.w) * sc.w, 0.0f), 1023.0f);
-    const uint32_t code = spread3(ix) | (spread3(iy) << 1) | (spread3(it) << 2);
-    keys[i] = ((unsigned long long)code << 32) | (unsigned long long)i;
+    keys[i] = ((unsigned long long)tnn_morton_xyt(q[i], lo, sc) << 32) | (unsigned long long)i;
 }
 
 // The per-query kernels that finish the tile kernel's deferred and
@@ -308,12 +293,8 @@ tnn_status tnn_launch_search(const KnnLaunch &L, bool brute, cudaStream_t st)
         if (L.w0.m <= (1ll << 29)) {
             const int n2 = tnn_next_pow2_sort(L.w0.m);
             TNN_CUDA_TRY(tnn_alloc((void **)&keys, (size_t)n2 * 8, st));
-            const float *lo = L.w0.bb_lo, *hi = L.w0.bb_hi;
-            float4 l4 = make_float4(lo[0], lo[1], lo[2], lo[3]), s4;
-            s4.x = hi[0] > lo[0] ? 1024.0f / (hi[0] - lo[0]) : 0.0f;
-            s4.y = hi[1] > lo[1] ? 1024.0f / (hi[1] - lo[1]) : 0.0f;
-            s4.z = 0.0f;
-            s4.w = hi[3] > lo[3] ? 1024.0f / (hi[3] - lo[3]) : 0.0f;
+            float4 l4, s4;
+            tnn_morton_frame(L.w0.bb_lo, L.w0.bb_hi, &l4, &s4);
             k_query_order_keys<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(L.w0.q, L.w0.m, n2, l4, s4,
                                                                            keys);
             tnn_bitonic_sort(keys, n2, st);
@@ -458,6 +439,8 @@ static tnn_status run_single(const tnn_index *ix, const float *d_q, int64_t m,
     tnn_clear_error();
     if (brute && ix) {
         tnn_status ts = tnn_index_time_order(ix, (cudaStream_t)stream);
+        if (ts == TNN_OK && !(p && (p->flags & TNN_FLAG_FFMA))) // threshold seeds of the tensor-core form
+            ts = tnn_index_space_order(ix, (cudaStream_t)stream);
         if (ts != TNN_OK)
             return ts;
     }
@@ -482,6 +465,11 @@ static tnn_status run_single(const tnn_index *ix, const float *d_q, int64_t m,
     L.kseg_max = ix->K;
     L.total_tiles = (m + TNN_TILE - 1) / TNN_TILE;
     L.fb_cap = m;
+    if (brute) {
+        L.seed_pts = ix->pts_m;
+        L.seed_idx = ix->idx_m;
+        L.seed_code = ix->code_m;
+    }
     const size_t hdr = 256;
     void *buf = nullptr;
     TNN_CUDA_TRY(tnn_alloc(&buf, hdr + (2 * sizeof(int2) + sizeof(float)) * (size_t)m, st));

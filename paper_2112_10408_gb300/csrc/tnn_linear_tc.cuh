@@ -8,31 +8,42 @@
 // t), so the 128 of a CTA are close together and share a short causal prefix.
 // With c the centre of the CTA's queries, f = sqrt(sigma) (q - c) and
 // e = sqrt(sigma) (p - c), the TF32 operand rows are
-//     a = [f, (1 - eps) |f|^2, 1, eps |f|, -T]
-//     b = [-2 e, 1, (1 - eps) |e|^2, -2 |e|, 1]
-// so that a . b = |f - e|^2 - eps (|f| + |e|)^2 - T: the scaled squared
+//     a = [f, (1 - 2 eps) |f|^2, 1, -T, 0]
+//     b = [-2 e, 1, (1 - 2 eps) |e|^2, 1, 0]
+// so that a . b = |f - e|^2 - 2 eps (|f|^2 + |e|^2) - T: the scaled squared
 // distance, minus an error allowance that scales with the magnitudes that
 // cancel, minus the query's current pruning threshold T.  A point can enter
-// the query's list only where that value is negative.
+// the query's list only where that value is negative.  The fixed part of a
+// is written once per CTA tile; per chunk only its -T entry changes.
 //
 // Roles (warp specialisation, chained by mbarriers):
 //   warp 4, one thread: TMA (cp.async.bulk) of raw 128-point chunks and
 //     their input indices into a ring of TC_S slots, TC_S - 2 chunks ahead; one tcgen05.mma kind::tf32
 //     (M = N = 128, K = 8) per chunk into one of two TMEM accumulators,
 //     committed to an mbarrier;
-//   warps 0-3: write the A and B rows of chunk i + 1 (one row each), then
-//     read their accumulator rows of chunk i (tcgen05.ld), OR the bit
-//     patterns of 64 values at a time to find any negative one, and score
-//     only those points again with the exact FP32 distance of the other
-//     kernels -- so candidate keys, lists and the FP64 settlement are the
-//     same.  The MMA of chunk i + 1 runs while chunk i is screened.
+//   warps 0-3: before the first chunk, score the 1,024 points nearest the
+//     CTA's queries in space-time order (the index's Morton-ordered copy,
+//     around the key of the CTA's middle query) on the CUDA cores; the L-th
+//     smallest of those keys is an upper bound on the query's final L-th key,
+//     so it becomes the admission bound of the list, which starts empty again
+//     (those points come again in the scan).  The screen then works with a
+//     threshold near the final one from the newest chunk on, instead of
+//     letting through most points of the first chunks while the lists fill.
+//   warps 0-3: write the B row and the -T entry of the A row of chunk i + 1
+//     (one row each), then read their accumulator rows of chunk i
+//     (tcgen05.ld), OR the bit patterns of the values in groups of 8 to find
+//     the groups holding a negative one, and score only those points again
+//     with the exact FP32 distance of the other kernels -- so candidate keys,
+//     lists and the FP64 settlement are the same.  The MMA of chunk i + 1
+//     runs while chunk i is screened.
 // Soundness of the screen (a point whose FP32 distance is at most the k-th
-// key must give a negative value): rounding every operand to TF32 changes
-// each product by at most 2^-10 |a_k b_k| and the FP32 sum of the 8 exact
-// products adds ~2^-20 of sum |a_k b_k| <= (|f| + |e|)^2 (1 + eps) + T;
-// centring and scaling in FP32 move |f - e|^2 by < 2^-21 (|f| + |e|)^2 and the
-// FP32 distance is within 2^-21 of the exact one.  eps = 2^-9 covers the
-// distance terms twice over, and T = RNA_tf32(thr (1 + 2^-8) + 2^-100)
+// key must give a negative value): rounding every operand to TF32 (nearest)
+// changes each product by at most 2^-10 |a_k b_k| and the FP32 sum of the 8
+// exact products adds ~2^-20 of sum |a_k b_k| <= 2 (|f|^2 + |e|^2) + T;
+// centring and scaling in FP32 move |f - e|^2 by < 2^-20 (|f|^2 + |e|^2) and
+// the FP32 distance is within 2^-21 of the exact one.  The allowance
+// 2 eps (|f|^2 + |e|^2) with eps = 2^-9 covers the distance terms twice over
+// (it is at least eps (|f| + |e|)^2), and T = RNA_tf32(thr (1 + 2^-8) + 2^-100)
 // exceeds the threshold by more than the error of its own term.
 #pragma once
 #include "tnn_device.cuh"
@@ -43,13 +54,17 @@
 #define TC_S 16         // raw-point ring slots
 #define TC_THREADS 160  // 4 screening warps + 1 control warp
 #define TC_EPS 0x1p-9f
+#ifndef TC_SEED_BATCHES
+#define TC_SEED_BATCHES 8 // threshold seeds per CTA, in batches of 128 points
+#endif
 
 #define TC_OFF_A 0                            // [2][128 rows x 8] TF32, K-major
 #define TC_OFF_B (TC_OFF_A + 8192)            // [2][128 rows x 8]
 #define TC_OFF_RAW (TC_OFF_B + 8192)          // [TC_S][128] float4
 #define TC_OFF_IDX (TC_OFF_RAW + TC_S * 2048) // [TC_S][128] int32 input index
 #define TC_OFF_BAR (TC_OFF_IDX + TC_S * 512)  // mbarriers and CTA scalars (512 B)
-#define TC_OFF_LIST (TC_OFF_BAR + 512)        // [L][128] candidate keys
+#define TC_OFF_SEED (TC_OFF_BAR + 512)        // [128] float4 + [128] int32 threshold seeds
+#define TC_OFF_LIST (TC_OFF_SEED + TC_P * 20) // [L][128] candidate keys
 // the settlement scratch of the 4 warps (4 x 3 KB) reuses A and B once the
 // tile's last MMA has completed
 
@@ -138,6 +153,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const __grid_consta
     int *s_hi = (int *)(sc + 16);
     float *s_wmax = (float *)(sc + 32); // [4]
     float *s_bb = (float *)(sc + 48);   // [4 warps][8]: min, max per axis
+    int *s_seed = (int *)(sc + 176);    // first seed point (space order), -1: none
+    float4 *seedp = (float4 *)(smem + TC_OFF_SEED);
+    int32_t *seedi = (int32_t *)(smem + TC_OFF_SEED + TC_P * 16);
     unsigned long long *K = (unsigned long long *)(smem + TC_OFF_LIST) + tq;
     unsigned long long *cl_d = (unsigned long long *)(smem + TC_OFF_A + (warp & 3) * 3072) + lane;
     int *cl_i = (int *)(smem + TC_OFF_A + (warp & 3) * 3072 + CMAX * 32 * 8) + lane;
@@ -241,6 +259,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const __grid_consta
             }
             *s_hi = lo;
         }
+        if (t == 32) { // warp 1: the seed window, beside thread 0's search
+            int sl = -1;
+            if (L.seed_code && L.qorder) {
+                const int64_t mid = min((int64_t)(tile * TC_Q + TC_Q / 2), (int64_t)(W->m - 1));
+                const uint32_t code = (uint32_t)(L.qorder[mid] >> 32);
+                int lo = 0, hi = W->n;
+                while (lo < hi) {
+                    const int md = (lo + hi) >> 1;
+                    if (L.seed_code[md] < code)
+                        lo = md + 1;
+                    else
+                        hi = md;
+                }
+                sl = min(max(lo - TC_SEED_BATCHES * TC_P / 2, 0), max(W->n - TC_SEED_BATCHES * TC_P, 0));
+            }
+            *s_seed = sl;
+        }
         // causal end of this query: the time-ordered points [0, hq) are the
         // ones with t < T32
         int hq = 0;
@@ -254,7 +289,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const __grid_consta
                     hi2 = mid;
             }
         }
-        // the fixed part of the query row
+        // the fixed part of the query row (entry 6, -T, is written per chunk)
         float arow[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (active) {
             const float f[4] = {q0 * (q.x - cc[0]), q1 * (q.y - cc[1]), q2 * (q.z - cc[2]),
@@ -267,9 +302,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const __grid_consta
             arow[1] = tf32_rna(f[1]);
             arow[2] = tf32_rna(f[2]);
             arow[3] = tf32_rna(f[3]);
-            arow[4] = tf32_rna((1.0f - TC_EPS) * n2);
+            arow[4] = tf32_rna((1.0f - 2.0f * TC_EPS) * n2);
             arow[5] = 1.0f;
-            arow[6] = tf32_rna(TC_EPS * sqrtf(n2));
         }
         if (!ctrl)
             for (int i = 0; i < Lw; ++i)
@@ -279,6 +313,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const __grid_consta
         const int nch = (hi + TC_P - 1) / TC_P;
         int nv = 0;
         unsigned long long tauk = SENT;
+        unsigned long long bound0 = SENT; // no key at or above it can enter the list
         float tau = INFINITY;
 
         if (ctrl) {
@@ -351,19 +386,62 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const __grid_consta
                     bv[2] = tf32_rna(-2.0f * e[2]);
                     bv[3] = tf32_rna(-2.0f * e[3]);
                     bv[4] = 1.0f;
-                    bv[5] = tf32_rna((1.0f - TC_EPS) * m2);
-                    bv[6] = tf32_rna(-2.0f * sqrtf(m2));
-                    bv[7] = 1.0f;
+                    bv[5] = tf32_rna((1.0f - 2.0f * TC_EPS) * m2);
+                    bv[6] = 1.0f;
                 }
                 store_row(sB + b * 4096, tq, bv);
-                arow[7] = active ? tc_neg_T(tau) : 0.0f;
-                store_row(sA + b * 4096, tq, arow);
+                *(float *)(sA + b * 4096 + kmaj_off(tq, 6)) = active ? tc_neg_T(tau) : 0.0f;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0)
                     mbar_arrive(BAR(TC_BAR_BFULL + b));
                 return true;
             };
+            // threshold seeds (see the header): scored on the CUDA cores
+            const int sl = *s_seed;
+            if (sl >= 0) {
+                const int nseed = min(TC_SEED_BATCHES * TC_P, W->n);
+                for (int b0 = 0; b0 < nseed; b0 += TC_P) {
+                    const int ns = min(TC_P, nseed - b0);
+                    if (b0 > 0) // the previous batch has been read
+                        asm volatile("bar.sync 1, %0;" ::"r"(TC_Q) : "memory");
+                    if (tq < ns) {
+                        seedp[tq] = __ldg(L.seed_pts + sl + b0 + tq);
+                        seedi[tq] = __ldg(L.seed_idx + sl + b0 + tq);
+                    }
+                    asm volatile("bar.sync 1, %0;" ::"r"(TC_Q) : "memory"); // the 4 screening warps
+                    if (!active)
+                        continue;
+                    for (int j = 0; j < ns; ++j) {
+                        const float4 p = seedp[j];
+                        if (!(p.w < c.T32))
+                            continue;
+                        const float d = dist32(c, s0, s1, s2, s3, p);
+                        st.lb++;
+                        if (d <= tau) {
+                            const unsigned long long key = pack_key(d, seedi[j]);
+                            if (key < tauk) {
+                                tauk = list_push<TC_Q>(K, Lw, nv, key);
+                                tau = key_d(tauk);
+                            }
+                        }
+                    }
+                }
+                if (active) {
+                    // keys up to the L-th seed key stay admissible (+1: the
+                    // test is strict and keys are unique)
+                    bound0 = nv == Lw ? tauk + 1ull : SENT;
+                    for (int i = 0; i < nv; ++i)
+                        K[i * TC_Q] = SENT;
+                    nv = 0;
+                    tauk = bound0;
+                    tau = key_d(bound0);
+                }
+            }
+            // the fixed part of both A buffers (the settlement scratch of
+            // the previous tile overlaps them)
+            store_row(sA, tq, arow);
+            store_row(sA + 4096, tq, arow);
             bool ok = build(g, 0);
             for (int i = 0; ok && i < nch; ++i) {
                 const long long gi = g + i;
@@ -387,17 +465,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const __grid_consta
                         tmem_ld32_nowait(taddr_row + (uint32_t)(b * TC_P + h * 64), v);
                         tmem_ld32_nowait(taddr_row + (uint32_t)(b * TC_P + h * 64 + 32), v + 32);
                         tmem_wait_ld();
+                        // OR of each group of 8 values: its sign bit says
+                        // whether the group holds a negative one
+                        uint32_t gor[8];
+#pragma unroll
+                        for (int q8 = 0; q8 < 8; ++q8) {
+                            gor[q8] = v[8 * q8];
+#pragma unroll
+                            for (int j = 1; j < 8; ++j)
+                                gor[q8] |= v[8 * q8 + j];
+                        }
                         uint32_t any = 0u;
 #pragma unroll
-                        for (int j = 0; j < 64; ++j)
-                            any |= v[j];
+                        for (int q8 = 0; q8 < 8; ++q8)
+                            any |= gor[q8];
                         const int lim = ncaus - h * 64; // causal columns in this half
                         if ((int)any < 0 && lim > 0) {
+                            // sign bits of the groups that hold a negative value
                             uint32_t m0 = 0u, m1 = 0u;
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                m0 |= (v[j] >> 31) << j;
-                                m1 |= (v[32 + j] >> 31) << j;
+                            for (int q8 = 0; q8 < 8; ++q8) {
+                                if ((int)gor[q8] < 0) {
+                                    uint32_t gm = 0u;
+#pragma unroll
+                                    for (int j = 0; j < 8; ++j)
+                                        gm |= (v[8 * q8 + j] >> 31) << j;
+                                    if (q8 < 4)
+                                        m0 |= gm << (8 * q8);
+                                    else
+                                        m1 |= gm << (8 * (q8 - 4));
+                                }
                             }
                             if (lim <= 32) {
                                 m1 = 0u;
@@ -418,7 +515,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const __grid_consta
                                     if (p.w < c.T32 && d <= tau) {
                                         const unsigned long long key = pack_key(d, sidx[s * TC_P + col]);
                                         if (key < tauk) {
-                                            tauk = list_push<TC_Q>(K, Lw, nv, key);
+                                            const unsigned long long r = list_push<TC_Q>(K, Lw, nv, key);
+                                            tauk = r < bound0 ? r : bound0;
                                             tau = key_d(tauk);
                                         }
                                     }
