@@ -84,8 +84,12 @@ typedef struct {
  *   d_xyzt      [n][4] float, device; copied into the index.
  *   h_traj_off  [n_traj + 1] int64, host; 0 = off[0] <= ... <= off[n_traj] = n.
  * Validates the input on the device (finite, |coordinate| <= 1e15, times
- * sorted within each trajectory) and therefore SYNCHRONISES `stream`.
- * On success *out owns device memory until tnn_index_destroy.
+ * sorted within each trajectory) and therefore SYNCHRONISES `stream` once,
+ * after the validation (the grid's geometry is chosen from the points'
+ * bounding box and durations read back at the same time); the segment fit,
+ * the sorts and the grid are enqueued after it and run on in stream order
+ * after the call returns.  On success *out owns device memory until
+ * tnn_index_destroy.
  */
 tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
                               const int64_t *h_traj_off, int64_t n_traj,
@@ -93,6 +97,8 @@ tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
                               tnn_stream_t stream, tnn_index **out);
 
 void tnn_index_destroy(tnn_index *index);
+/* Sizes of the index.  The first call waits for the build to finish (for
+   max_radius, the segment fit's largest radius). */
 tnn_status tnn_index_get_info(const tnn_index *index, tnn_index_info *out);
 
 /*

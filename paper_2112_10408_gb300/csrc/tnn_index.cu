@@ -79,20 +79,29 @@ __global__ void k_validate_points(const float4 *__restrict__ p, int n,
         atomicMax(cmax_bits, __float_as_uint(m)); // m >= 0: bits are monotone
 }
 
-// Times non-decreasing inside each trajectory (one warp per trajectory).
-__global__ void k_validate_order(const float4 *__restrict__ p,
-                                 const int32_t *__restrict__ traj_off,
-                                 int n_traj, unsigned int *flag)
+// Times non-decreasing inside each trajectory, and the summed duration
+// t_last - t_first of its K-point sets, which sizes the grid's time buckets
+// (one warp per trajectory).
+__global__ void k_validate_traj(const float4 *__restrict__ p,
+                                const int32_t *__restrict__ traj_off,
+                                int n_traj, int K, unsigned int *flag, double *dur_sum)
 {
     const int tr = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (tr >= n_traj)
+    if (tr >= n_traj) // the same for the whole warp
         return;
     const int b = traj_off[tr], e = traj_off[tr + 1];
     bool bad = false;
     for (int i = b + 1 + lane; i < e; i += 32)
         bad |= !(p[i].w >= p[i - 1].w);
+    double dur = 0.0;
+    for (int f = b + lane * K; f < e; f += 32 * K)
+        dur += (double)p[min(f + K - 1, e - 1)].w - (double)p[f].w;
+    for (int o = 16; o > 0; o >>= 1)
+        dur += __shfl_xor_sync(0xffffffffu, dur, o);
     if (__any_sync(0xffffffffu, bad) && lane == 0)
         atomicOr(flag, (unsigned)BAD_ORDER);
+    if (lane == 0 && dur != 0.0)
+        atomicAdd(dur_sum, dur);
 }
 
 // Four lanes per segment (build order).  FP64 throughout, rounded once to
@@ -487,44 +496,6 @@ __device__ __forceinline__ float ord2f(uint32_t u)
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 
-// Extremes of the segment midpoints (scaled x, y) and of t_A, and the sum of
-// the segment durations, for choosing the grid.
-// Warp-level minimum / maximum of ordered values, then one atomic per warp.
-__device__ __forceinline__ void warp_minmax_atomic(unsigned int lo, unsigned int hi,
-                                                   unsigned int *out_lo, unsigned int *out_hi)
-{
-    for (int o = 16; o > 0; o >>= 1) {
-        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicMin(out_lo, lo);
-        atomicMax(out_hi, hi);
-    }
-}
-
-__global__ void k_seg_extremes(const float4 *__restrict__ seg, int S,
-                               unsigned int *ext_ord, double *dur_sum)
-{
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned int o[6] = {0xffffffffu, 0u, 0xffffffffu, 0u, 0xffffffffu, 0u};
-    double dur = 0.0;
-    if (s < S) {
-        const float4 a = seg[4 * s], u = seg[4 * s + 1], b = seg[4 * s + 2];
-        const float mx = fmaf(0.5f, b.x, a.x), my = fmaf(0.5f, b.y, a.y);
-        o[0] = o[1] = f2ord(mx);
-        o[2] = o[3] = f2ord(my);
-        o[4] = o[5] = f2ord(a.w);
-        dur = (double)u.w - (double)a.w;
-    }
-    for (int d = 0; d < 3; ++d)
-        warp_minmax_atomic(o[2 * d], o[2 * d + 1], ext_ord + 2 * d, ext_ord + 2 * d + 1);
-    for (int k = 16; k > 0; k >>= 1)
-        dur += __shfl_xor_sync(0xffffffffu, dur, k);
-    if ((threadIdx.x & 31) == 0)
-        atomicAdd(dur_sum, dur);
-}
-
 // Bounding box of the raw points (x, y, z, t): ordered min/max per axis,
 // reduced over the block (grid-stride) before one atomic per value.
 __global__ void k_point_bbox(const float4 *__restrict__ p, int n, unsigned int *ord)
@@ -708,6 +679,9 @@ static void free_index(tnn_index *ix)
                       ix->idx_m, ix->code_m};
     for (void *p : arrays)
         tnn_free(p, 0);
+    tnn_free(ix->d_rmax, 0);
+    if (ix->built)
+        cudaEventDestroy(ix->built);
     delete ix;
 }
 
@@ -731,62 +705,22 @@ static float host_ord2f(uint32_t u)
     return f;
 }
 
-// Choose the grid from the segment extremes and build it (synchronises).
-// Buckets span about four mean segment durations (at most 4096 of them);
-// cells are square, about two segments per (bucket, cell) on average, at most
-// 65,536 cells and 2^22 keys.
-static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
-                             const unsigned int *d_flag, unsigned int *h_flag,
-                             cudaStream_t st)
+// Grid geometry from the points' bounding box in sqrt(sigma)-scaled x, y
+// (it holds every segment midpoint up to rounding, and keys are clamped to
+// the grid), their time range and the summed segment duration.  Buckets span
+// about four mean segment durations (at most 4096 of them); cells are square,
+// about two segments per (bucket, cell) on average, at most 65,536 cells and
+// 2^22 keys.
+static GridBuild grid_geometry(double xmn, double xmx, double ymn, double ymx, double tmn,
+                               double tmx, double dur, int64_t S)
 {
-    const int S = (int)ix->S, tb = 256;
-    DevBuf sb;
-    TNN_CUDA_TRY(sb.alloc(64, st));
-    unsigned int init[8] = {0xffffffffu, 0u, 0xffffffffu, 0u, 0xffffffffu, 0u, 0u, 0u};
-    TNN_CUDA_TRY(cudaMemcpyAsync(sb.p, init, sizeof(init), cudaMemcpyHostToDevice, st));
-    TNN_CUDA_TRY(cudaMemsetAsync((char *)sb.p + 32, 0, 8, st));
-    k_seg_extremes<<<(S + tb - 1) / tb, tb, 0, st>>>(ix->seg, S, (unsigned int *)sb.p,
-                                                    (double *)((char *)sb.p + 32));
-    DevBuf bb;
-    TNN_CUDA_TRY(bb.alloc(32, st));
-    const unsigned int binit[8] = {0xffffffffu, 0u, 0xffffffffu, 0u, 0xffffffffu, 0u, 0xffffffffu, 0u};
-    TNN_CUDA_TRY(cudaMemcpyAsync(bb.p, binit, sizeof(binit), cudaMemcpyHostToDevice, st));
-    k_point_bbox<<<(int)std::min<int64_t>((ix->n + tb - 1) / tb, 608), tb, 0, st>>>(
-        ix->pts, (int)ix->n, (unsigned int *)bb.p);
-    unsigned int h[8], hb[8];
-    double dur = 0.0;
-    TNN_CUDA_TRY(cudaMemcpyAsync(h, sb.p, sizeof(h), cudaMemcpyDeviceToHost, st));
-    TNN_CUDA_TRY(cudaMemcpyAsync(&dur, (char *)sb.p + 32, 8, cudaMemcpyDeviceToHost, st));
-    TNN_CUDA_TRY(cudaMemcpyAsync(hb, bb.p, sizeof(hb), cudaMemcpyDeviceToHost, st));
-    // the validation flags, the largest coordinate and the largest radius
-    // are complete by now: the build's only synchronisation reads them too
-    TNN_CUDA_TRY(cudaMemcpyAsync(h_flag, d_flag, 3 * sizeof(unsigned int),
-                                 cudaMemcpyDeviceToHost, st));
-    TNN_CUDA_TRY(cudaStreamSynchronize(st));
-    if (h_flag[0] & BAD_VALUE) {
-        tnn_set_error("non-finite or too large (|v| > 1e15) coordinate in input");
-        return TNN_ERR_INVALID_ARG;
-    }
-    if (h_flag[0] & BAD_ORDER) {
-        tnn_set_error("times are not sorted inside a trajectory");
-        return TNN_ERR_INVALID_ARG;
-    }
-    // bounding box of the points (orders the queries of the tensor-core
-    // linear search)
-    for (int d = 0; d < 4; ++d) {
-        ix->bb_lo[d] = (float)host_ord2f(hb[2 * d]);
-        ix->bb_hi[d] = (float)host_ord2f(hb[2 * d + 1]);
-    }
-    const double xmn = host_ord2f(h[0]), xmx = host_ord2f(h[1]);
-    const double ymn = host_ord2f(h[2]), ymx = host_ord2f(h[3]);
-    const double tmn = host_ord2f(h[4]), tmx = host_ord2f(h[5]);
     const double T = tmx - tmn;
     double dt = 4.0 * dur / S;
     if (!(dt > 0.0))
         dt = T > 0.0 ? T / 64.0 : 1.0;
     if (T / dt > 4095.0)
         dt = T / 4095.0;
-    int nb = (int)std::min(4096.0, floor(T / dt) + 1.0);
+    const int nb = (int)std::min(4096.0, floor(T / dt) + 1.0);
     const double Wd = xmx - xmn, Hd = ymx - ymn;
     const double target = std::min(65536.0, std::max(1.0, 2.0 * S / nb));
     double cell = sqrt(std::max(Wd * Hd, 1e-12) / target);
@@ -811,6 +745,16 @@ static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
     g.ny = ny;
     g.ncell = nx * ny;
     g.nb = nb;
+    return g;
+}
+
+// Build the grid over the t_A-ordered segments (stream-ordered, no host
+// synchronisation).
+static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2, const GridBuild &g,
+                             cudaStream_t st)
+{
+    const int S = (int)ix->S, tb = 256;
+    const int nx = g.nx, ny = g.ny, nb = g.nb;
     const int nkeys = nb * g.ncell;
     TNN_CUDA_TRY(tnn_alloc((void **)&ix->g_off, sizeof(int32_t) * (nkeys + 1), st));
     TNN_CUDA_TRY(tnn_alloc((void **)&ix->g_ids, sizeof(int32_t) * S, st));
@@ -824,7 +768,6 @@ static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
     TNN_CUDA_TRY(cudaMemsetAsync(ix->g_ext, 0, sizeof(float) * nkeys, st));
     TNN_CUDA_TRY(cudaMemsetAsync(ix->g_tB, 0, sizeof(float) * nkeys, st));
     TNN_CUDA_TRY(cudaMemsetAsync(ix->g_bpm, 0, sizeof(float) * nb, st));
-    TNN_CUDA_TRY(cudaMemsetAsync((char *)sb.p + 48, 0, 4, st));
     k_fill<<<(s2 - S + tb - 1) / tb + 1, tb, 0, st>>>(keys, S, s2);
     k_grid_keys<<<(S + tb - 1) / tb, tb, 0, st>>>(ix->seg, S, g, keys, (unsigned int *)ix->g_ext,
                                                  (unsigned int *)ix->g_tB,
@@ -838,7 +781,7 @@ static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2,
     k_prefix_max<<<1, 32, 0, st>>>(ix->g_bpm, nb);
     k_key_records<<<(nkeys + tb - 1) / tb, tb, 0, st>>>(ix->g_off, ix->g_ext, ix->g_tB, nkeys,
                                                        ix->g_krec);
-    // largest extent (for the search region), read back with the build's flags
+    // largest extent (for the search region)
     k_max_bits<<<std::min((nkeys + tb - 1) / tb, 1024), tb, 0, st>>>(
         (const unsigned int *)ix->g_ext, nkeys, (unsigned int *)ix->g_ext_max);
     TNN_CUDA_TRY(cudaGetLastError());
@@ -936,12 +879,17 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
     if (e == cudaSuccess)
         e = keys_d.alloc(sizeof(unsigned long long) * s2, st);
     if (e == cudaSuccess)
-        e = flags_d.alloc(sizeof(unsigned int) * 4, st);
+        e = flags_d.alloc(sizeof(unsigned int) * 12, st);
     if (e != cudaSuccess) {
         free_index(ix);
         tnn_set_error("index allocation failed: %s", cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? TNN_ERR_OOM : TNN_ERR_CUDA;
     }
+    // flags_d: [0] validation flags, [1] largest |scaled coordinate| bits,
+    // [2..9] point bounding box (ordered min, max per axis), [10..11] summed
+    // segment duration (double)
+    static const unsigned int meta_init[12] = {0u, 0u, 0xffffffffu, 0u, 0xffffffffu, 0u,
+                                               0xffffffffu, 0u, 0xffffffffu, 0u, 0u, 0u};
     unsigned int *flag = (unsigned int *)flags_d.p;
     unsigned long long *keys = (unsigned long long *)keys_d.p;
     const int tb = 256;
@@ -953,21 +901,63 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
         e = cudaMemcpyAsync(soff_d.p, soff.data(), sizeof(int32_t) * (n_traj + 1),
                             cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(flag, 0, sizeof(unsigned int) * 4, st);
+        e = cudaMemcpyAsync(flag, meta_init, sizeof(meta_init), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = tnn_alloc((void **)&ix->d_rmax, sizeof(unsigned int), st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(ix->d_rmax, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&ix->built, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         free_index(ix);
         tnn_set_error("index upload failed: %s", cudaGetErrorString(e));
         return TNN_ERR_CUDA;
     }
     const int ni = (int)n, Si = (int)S, Ti = (int)n_traj;
+    // ---- validation, and what the grid geometry needs: the build's only
+    // host synchronisation; everything after it is enqueued at once
     k_validate_points<<<(ni + tb - 1) / tb, tb, 0, st>>>(
         ix->pts, ni, ix->ssq_f[0], ix->ssq_f[1], ix->ssq_f[2], flag, flag + 1);
-    k_validate_order<<<(int)(((int64_t)Ti * 32 + tb - 1) / tb), tb, 0, st>>>(
-        ix->pts, (const int32_t *)toff_d.p, Ti, flag);
+    k_validate_traj<<<(int)(((int64_t)Ti * 32 + tb - 1) / tb), tb, 0, st>>>(
+        ix->pts, (const int32_t *)toff_d.p, Ti, K, flag, (double *)(flag + 10));
+    k_point_bbox<<<(int)std::min<int64_t>((ix->n + tb - 1) / tb, 608), tb, 0, st>>>(
+        ix->pts, (int)ix->n, flag + 2);
+    unsigned int hm[12];
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hm, flag, sizeof(hm), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        free_index(ix);
+        tnn_set_error("index validation failed: %s", cudaGetErrorString(e));
+        return TNN_ERR_CUDA;
+    }
+    if (hm[0] & BAD_VALUE) {
+        free_index(ix);
+        tnn_set_error("non-finite or too large (|v| > 1e15) coordinate in input");
+        return TNN_ERR_INVALID_ARG;
+    }
+    if (hm[0] & BAD_ORDER) {
+        free_index(ix);
+        tnn_set_error("times are not sorted inside a trajectory");
+        return TNN_ERR_INVALID_ARG;
+    }
+    memcpy(&ix->coord_max, &hm[1], sizeof(float));
+    for (int d = 0; d < 4; ++d) {
+        ix->bb_lo[d] = host_ord2f(hm[2 + 2 * d]);
+        ix->bb_hi[d] = host_ord2f(hm[3 + 2 * d]);
+    }
+    double dur = 0.0;
+    memcpy(&dur, &hm[10], sizeof(double));
+    const double q0 = sqrt(params->sigma[0]), q1 = sqrt(params->sigma[1]);
+    const GridBuild geo = grid_geometry(q0 * ix->bb_lo[0], q0 * ix->bb_hi[0], q1 * ix->bb_lo[1],
+                                        q1 * ix->bb_hi[1], ix->bb_lo[3], ix->bb_hi[3], dur, S);
+
+    // ---- segments, their t_A order, the running maximum of t_B, the grid
     k_segment_fit<<<(int)(((int64_t)Si * 4 + tb - 1) / tb), tb, 0, st>>>(
         ix->pts, (const int32_t *)toff_d.p, (const int32_t *)soff_d.p, Ti, Si, K,
-        sqrt(params->sigma[0]), sqrt(params->sigma[1]), sqrt(params->sigma[2]),
-        (float4 *)rec_d.p, keys, flag + 2);
+        q0, q1, sqrt(params->sigma[2]), (float4 *)rec_d.p, keys, ix->d_rmax);
     k_fill<<<(s2 - Si + tb - 1) / tb + 1, tb, 0, st>>>(keys, Si, s2);
     tnn_bitonic_sort(keys, s2, st);
     k_gather_segments<<<(Si + tb - 1) / tb, tb, 0, st>>>(keys, (const float4 *)rec_d.p,
@@ -978,24 +968,23 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
         k_pm_block_max<<<nblk, 1024, 0, st>>>(ix->seg, Si, bmax);
         k_pm_apply<<<nblk, 1024, 0, st>>>(ix->seg, Si, bmax, ix->segPM);
     }
-    unsigned int hflag[3] = {0, 0, 0};
     {
-        tnn_status gs = build_grid(ix, keys, s2, flag, hflag, st);
+        tnn_status gs = build_grid(ix, keys, s2, geo, st);
         if (gs != TNN_OK) {
             free_index(ix);
             return gs;
         }
     }
-    // The rest of the build runs on after this call returns (stream order);
-    // a failure there surfaces at the next synchronising call.
-    e = cudaGetLastError();
+    // The build runs on after this call returns (stream order); a failure
+    // there surfaces at the next synchronising call.
+    e = cudaEventRecord(ix->built, st);
+    if (e == cudaSuccess)
+        e = cudaGetLastError();
     if (e != cudaSuccess) {
         free_index(ix);
         tnn_set_error("index build failed: %s", cudaGetErrorString(e));
         return TNN_ERR_CUDA;
     }
-    memcpy(&ix->coord_max, &hflag[1], sizeof(float));
-    memcpy(&ix->max_radius, &hflag[2], sizeof(float));
     *out = ix;
     return TNN_OK;
 }
@@ -1247,6 +1236,22 @@ extern "C" tnn_status tnn_index_get_info(const tnn_index *ix, tnn_index_info *ou
     out->n_segments = ix->S;
     out->seg_len = ix->K;
     out->coord_max = ix->coord_max;
+    if (!ix->rmax_known) {
+        // the segment fit's largest radius: wait for the build to finish
+        static std::mutex mu;
+        std::lock_guard<std::mutex> lk(mu);
+        tnn_index *w = const_cast<tnn_index *>(ix);
+        unsigned int bits = 0u;
+        cudaError_t e = ix->built ? cudaEventSynchronize(ix->built) : cudaSuccess;
+        if (e == cudaSuccess)
+            e = cudaMemcpy(&bits, ix->d_rmax, sizeof(bits), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            tnn_set_error("reading the index radius failed: %s", cudaGetErrorString(e));
+            return TNN_ERR_CUDA;
+        }
+        memcpy(&w->max_radius, &bits, sizeof(float));
+        w->rmax_known = true;
+    }
     out->max_radius = ix->max_radius;
     return TNN_OK;
 }

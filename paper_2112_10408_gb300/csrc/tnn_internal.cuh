@@ -95,6 +95,9 @@ struct tnn_index {
     int4 *g_krec;
     float *g_ext_max; // [1]
     float bb_lo[4], bb_hi[4]; // bounding box of the points (x, y, z, t)
+    unsigned int *d_rmax;     // [1] max_radius bits, written by the segment fit
+    cudaEvent_t built;        // recorded after the build's last kernel
+    bool rmax_known;          // max_radius has been read back
 };
 
 // Parameters of one independent k-NN problem, read by the search kernels.

@@ -191,17 +191,30 @@ def _ptr(t):
 class Index:
     """Owner of a tnn_index*; the points are copied into it."""
 
-    def __init__(self, handle, sigma, seg_len):
+    def __init__(self, handle, sigma, seg_len, n_points, n_traj, n_segments):
         self._h = handle
         self.sigma = tuple(float(s) for s in sigma)
-        info = tnn_index_info()
-        _check(_L().tnn_index_get_info(self._h, ctypes.byref(info)))
-        self.n_points = int(info.n_points)
-        self.n_traj = int(info.n_traj)
-        self.n_segments = int(info.n_segments)
-        self.seg_len = int(info.seg_len)
-        self.coord_max = float(info.coord_max)
-        self.max_radius = float(info.max_radius)
+        self.n_points = int(n_points)
+        self.n_traj = int(n_traj)
+        self.n_segments = int(n_segments)
+        self.seg_len = int(seg_len)
+        self._info = None
+
+    def _get_info(self):
+        # waits for the build to finish (the segment fit's largest radius)
+        if self._info is None:
+            info = tnn_index_info()
+            _check(_L().tnn_index_get_info(self.handle, ctypes.byref(info)))
+            self._info = info
+        return self._info
+
+    @property
+    def coord_max(self) -> float:
+        return float(self._get_info().coord_max)
+
+    @property
+    def max_radius(self) -> float:
+        return float(self._get_info().max_radius)
 
     @property
     def handle(self):
@@ -231,7 +244,8 @@ def tnn_build_segments(xyzt: torch.Tensor, traj_off, sigma, seg_len: int) -> Ind
     h = c_p()
     _check(_L().tnn_build_segments(_ptr(xyzt), xyzt.shape[0], off.ctypes.data_as(c_p),
                                    off.shape[0] - 1, ctypes.byref(p), _stream(), ctypes.byref(h)))
-    return Index(h, sigma, seg_len)
+    n_segments = int(((np.diff(off) + seg_len - 1) // seg_len).sum())
+    return Index(h, sigma, seg_len, xyzt.shape[0], off.shape[0] - 1, n_segments)
 
 
 def tnn_index_export(index: Index):

@@ -39,7 +39,7 @@ def test_pool_reuse_and_trim():
         tnn.tnn_memory_trim(-1)
 
 
-@pytest.mark.parametrize("chunks", [0, 1, 3])
+@pytest.mark.parametrize("chunks", [0, 1, 3, 8])
 def test_host_pipeline_matches_device_path(chunks):
     """tnn_knn_host (host buffers in and out, sliced search with overlapped
     copies) gives exactly the device path's lists."""
