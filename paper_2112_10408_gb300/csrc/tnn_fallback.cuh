@@ -357,10 +357,9 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_WARP_MINB)
                     if (!(time_lb(c, s3, bpm_b) <= tau))
                         break;
                     const float R = sqrtf(tau) * (1.0f + 0x1p-18f) + ext_max + c.delta;
-                    const int cx0 = max((int)floorf(fmaxf((c.sx - R - G.x0) * G.inv_cell, -1.0f)) - 1, 0);
-                    const int cx1 = min((int)floorf(fminf((c.sx + R - G.x0) * G.inv_cell, (float)G.nx)) + 1, G.nx - 1);
-                    const int cy0 = max((int)floorf(fmaxf((c.sy - R - G.y0) * G.inv_cell, -1.0f)) - 1, 0);
-                    const int cy1 = min((int)floorf(fminf((c.sy + R - G.y0) * G.inv_cell, (float)G.ny)) + 1, G.ny - 1);
+                    int cx0, cx1, cy0, cy1;
+                    reach_cells(c.sx, c.sx, R, G.x0, G.inv_cell, G.nx, cx0, cx1);
+                    reach_cells(c.sy, c.sy, R, G.y0, G.inv_cell, G.ny, cy0, cy1);
                     const int wx = cx1 - cx0 + 1, nk = wx * (cy1 - cy0 + 1);
                     const bool bseed = bhi - b <= rs;
                     for (int t0 = 0; t0 < nk; t0 += 32) {

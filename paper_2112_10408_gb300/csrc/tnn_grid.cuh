@@ -36,6 +36,22 @@ __device__ __forceinline__ float cell_lb(const QCtx &c, float st, float rx0, flo
     return fmaf(sp, sp, (st * et) * et) * (1.0f - 0x1p-19f);
 }
 
+// Cells [c0, c1] of one axis (n cells of size 1 / inv_cell from o) whose
+// span can come within R of the interval [s0, s1].  The FP32 evaluation of
+// the indices here and of the cell corners at query time errs by at most
+// 2^-21 ((|s0| + R + 2|o|) inv_cell + n) cells; the slack is twice that plus
+// 2^-10.  (A whole cell of margin on each side would triple the cells
+// examined at the usual cell sizes, and still fall short for coordinates far
+// from the origin.)
+__device__ __forceinline__ void reach_cells(float s0, float s1, float R, float o, float inv_cell, int n,
+                                            int &c0, int &c1)
+{
+    const float slack =
+        fmaf(0x1p-20f, fmaf(fabsf(s0) + fabsf(s1) + R + 2.0f * fabsf(o), inv_cell, (float)n), 0x1p-10f);
+    c0 = max((int)floorf(fmaxf(fmaf(s0 - R - o, inv_cell, -slack), -1.0f)), 0);
+    c1 = min((int)floorf(fminf(fmaf(s1 + R - o, inv_cell, slack), (float)n)), n - 1);
+}
+
 __device__ __forceinline__ float warp_minf(float v)
 {
     for (int o = 16; o > 0; o >>= 1)
@@ -352,10 +368,8 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_GRID_MINB)
             if (tmx < INFINITY) {
                 // any key outside this reach has a bound above every key
                 const float R = sqrtf(tmx) * (1.0f + 0x1p-18f) + ext_max + dmax;
-                cx0 = max((int)floorf(fmaxf((bx0 - R - G.x0) * G.inv_cell, -1.0f)) - 1, 0);
-                cx1 = min((int)floorf(fminf((bx1 + R - G.x0) * G.inv_cell, (float)G.nx)) + 1, G.nx - 1);
-                cy0 = max((int)floorf(fmaxf((by0 - R - G.y0) * G.inv_cell, -1.0f)) - 1, 0);
-                cy1 = min((int)floorf(fminf((by1 + R - G.y0) * G.inv_cell, (float)G.ny)) + 1, G.ny - 1);
+                reach_cells(bx0, bx1, R, G.x0, G.inv_cell, G.nx, cx0, cx1);
+                reach_cells(by0, by1, R, G.y0, G.inv_cell, G.ny, cy0, cy1);
             }
             const int kb = b * G.ncell;
             for (int cy = cy0; cy <= cy1; ++cy) {

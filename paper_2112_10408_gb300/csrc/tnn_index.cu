@@ -711,18 +711,24 @@ static float host_ord2f(uint32_t u)
 // about four mean segment durations (at most 4096 of them); cells are square,
 // about two segments per (bucket, cell) on average, at most 65,536 cells and
 // 2^22 keys.
+#ifndef TNN_BUCKET_SEGS
+#define TNN_BUCKET_SEGS 4.0 // bucket span in mean segment durations
+#endif
+#ifndef TNN_KEY_SEGS
+#define TNN_KEY_SEGS 2.0 // mean segments per (bucket, cell)
+#endif
 static GridBuild grid_geometry(double xmn, double xmx, double ymn, double ymx, double tmn,
                                double tmx, double dur, int64_t S)
 {
     const double T = tmx - tmn;
-    double dt = 4.0 * dur / S;
+    double dt = TNN_BUCKET_SEGS * dur / S;
     if (!(dt > 0.0))
         dt = T > 0.0 ? T / 64.0 : 1.0;
     if (T / dt > 4095.0)
         dt = T / 4095.0;
     const int nb = (int)std::min(4096.0, floor(T / dt) + 1.0);
     const double Wd = xmx - xmn, Hd = ymx - ymn;
-    const double target = std::min(65536.0, std::max(1.0, 2.0 * S / nb));
+    const double target = std::min(65536.0, std::max(1.0, TNN_KEY_SEGS * S / nb));
     double cell = sqrt(std::max(Wd * Hd, 1e-12) / target);
     cell = std::max(cell, std::max(std::max(Wd, Hd) / 1024.0, 1e-6));
     int nx = 1, ny = 1;

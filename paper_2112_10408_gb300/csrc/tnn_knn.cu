@@ -879,10 +879,9 @@ __global__ void k_knn_work(const __grid_constant__ KnnWin W, const float *__rest
             if (!(time_lb(c, W.sig[3], G.bpm[b]) <= dk))
                 break;
             const float R = sqrtf(dk) * (1.0f + 0x1p-18f) + __ldg(G.ext_max) + c.delta;
-            const int cx0 = max((int)floorf(fmaxf((c.sx - R - G.x0) * G.inv_cell, -1.0f)) - 1, 0);
-            const int cx1 = min((int)floorf(fminf((c.sx + R - G.x0) * G.inv_cell, (float)G.nx)) + 1, G.nx - 1);
-            const int cy0 = max((int)floorf(fmaxf((c.sy - R - G.y0) * G.inv_cell, -1.0f)) - 1, 0);
-            const int cy1 = min((int)floorf(fminf((c.sy + R - G.y0) * G.inv_cell, (float)G.ny)) + 1, G.ny - 1);
+            int cx0, cx1, cy0, cy1;
+            reach_cells(c.sx, c.sx, R, G.x0, G.inv_cell, G.nx, cx0, cx1);
+            reach_cells(c.sy, c.sy, R, G.y0, G.inv_cell, G.ny, cy0, cy1);
             for (int cy = cy0; cy <= cy1; ++cy)
                 for (int cx = cx0; cx <= cx1; ++cx) {
                     const int key = b * G.ncell + cy * G.nx + cx;

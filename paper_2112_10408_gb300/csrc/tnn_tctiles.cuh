@@ -368,10 +368,8 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_tnn_tc(const __grid_constant_
             int cx0 = 0, cx1 = G.nx - 1, cy0 = 0, cy1 = G.ny - 1;
             if (tm < INFINITY) {
                 const float R = sqrtf(tm) * (1.0f + 0x1p-18f) + ext_max + dmax;
-                cx0 = max((int)floorf(fmaxf((bx0 - R - G.x0) * G.inv_cell, -1.0f)) - 1, 0);
-                cx1 = min((int)floorf(fminf((bx1 + R - G.x0) * G.inv_cell, (float)G.nx)) + 1, G.nx - 1);
-                cy0 = max((int)floorf(fmaxf((by0 - R - G.y0) * G.inv_cell, -1.0f)) - 1, 0);
-                cy1 = min((int)floorf(fminf((by1 + R - G.y0) * G.inv_cell, (float)G.ny)) + 1, G.ny - 1);
+                reach_cells(bx0, bx1, R, G.x0, G.inv_cell, G.nx, cx0, cx1);
+                reach_cells(by0, by1, R, G.y0, G.inv_cell, G.ny, cy0, cy1);
             }
             if (cx0 > cx1 || cy0 > cy1) // the reach misses the grid (queries far outside it)
                 continue;

@@ -1,6 +1,7 @@
 """Parity of the CUDA search (TNN and the linear-search comparator) with the
 FP64 oracle, through the C ABI: neighbour indices bit-exact (ties by index),
 distances within 1e-5 relative; plus the index and bound invariants."""
+import dataclasses
 import math
 
 import numpy as np
@@ -348,15 +349,33 @@ def test_linear_tensor_core_far_and_large_coordinates():
         assert_knn_equal(bi.cpu().numpy(), bd.cpu().numpy(), oi, od, what=f"far ffma={ffma}")
 
 
+@pytest.mark.parametrize("offset", [(9000.0, -7000.0), (2e5, 1.5e5)])
+def test_grid_search_far_from_the_origin(offset):
+    # The grid's reach (cells within the k-th distance of a query) is taken in
+    # FP32 with a slack that grows with the coordinates: data thousands of km
+    # from the origin must give the oracle's lists, in both search orders.
+    wl = synth.flights(80, 60, seed=17, n_routes=6)
+    xyzt = wl.xyzt + np.array([offset[0], offset[1], 0.0, 0.0], np.float32)
+    ix = tnn.tnn_build_segments(torch.from_numpy(xyzt).cuda(), wl.traj_off, SIG, 10)
+    oi, od = oracle.knn(xyzt, 12, SIG, lag=0.0)
+    for sweep in (False, True):
+        ti, td = tnn.tnn_knn(ix, 12, 0.0, sweep=sweep)
+        assert_knn_equal(ti.cpu().numpy(), td.cpu().numpy(), oi, od, what=f"offset {offset} sweep={sweep}")
+
+
 def test_stop_certificate_every_skipped_segment_is_bounded_out():
     """Algorithm 2's stop rule and exclusion criterion, checked directly: the
     search records which segments it scanned for each query; every causal
     segment it skipped must have a cylinder bound above the query's final
     k-th distance (the bound it skipped against is the (k + extra)-th
     candidate, never below the k-th)."""
+    far = synth.flights(60, 70, seed=43, n_routes=5)
+    far = dataclasses.replace(far, xyzt=far.xyzt + np.array([3e4, -2e4, 0.0, 0.0], np.float32),
+                              name="flights far from the origin")
     for wl, k, lag in ((synth.flights(60, 70, seed=41, n_routes=5), 16, 0.0),
                        (synth.flights(50, 80, seed=42, n_routes=4), 5, 90.0),
-                       (synth.smoothed_random_walks(25, 90, seed=3), 32, 0.0)):
+                       (synth.smoothed_random_walks(25, 90, seed=3), 32, 0.0),
+                       (far, 16, 0.0)):
         ix = _index(wl, 12)
         idx, d2, path, seen = tnn.tnn_knn_trace(ix, k, lag, seen=True)
         lb = tnn.tnn_segment_lower_bounds(ix, lag=lag)
