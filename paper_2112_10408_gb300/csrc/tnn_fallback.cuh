@@ -43,6 +43,19 @@ __host__ __device__ inline size_t fb_exact_smem_per_warp(int k_max)
     return (size_t)k_max * 32 * 12;
 }
 
+// The settlement of the warp-per-query kernel, out of line (lane 0 only,
+// and only for queries with close ranks): bit 0 = settled, the rest the
+// FP64 rechecks made.  Keeps its body out of the kernel's hot loop code.
+static __device__ __noinline__ unsigned finalize_query_ool(const KnnWin *W, float4 q,
+                                                          const unsigned long long *K, int L,
+                                                          unsigned long long *cl_d, int *cl_i,
+                                                          int64_t qrow)
+{
+    LaneStats st = {0, 0, 0, 0, 0};
+    const bool ok = finalize_query(W, q, K, L, cl_d, cl_i, qrow, st, 1);
+    return ((unsigned)st.fp64 << 1) | (ok ? 1u : 0u);
+}
+
 __device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int m)
 {
     return __shfl_xor_sync(FULLMASK, v, m);
@@ -320,72 +333,90 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_WARP_MINB)
             const int hx = min(max((int)floorf((c.sx - G.x0) * G.inv_cell), 0), G.nx - 1);
             const int hy = min(max((int)floorf((c.sy - G.y0) * G.inv_cell), 0), G.ny - 1);
             const int rcover = max(max(max(hx, G.nx - 1 - hx), max(hy, G.ny - 1 - hy)), bhi);
+            const float ext_max = __ldg(G.ext_max);
+            // One loop hands visit_keys the keys of both phases, up to 32 per
+            // round (a single inlined copy of the visit and its merges):
             // ---- seeding: shells of growing radius around the query's key, at
             // most WQ_RSEED of them (a query with fewer than C valid points
             // would otherwise grow the cube over the whole grid; the main
-            // phase visits each causal bucket once instead)
-            int rs = -1;
-            while (wl.nv < wl.C && rs < rcover && rs < WQ_RSEED) {
-                const int r = ++rs;
-                const int side = 2 * r + 1, nk = side * side * (r + 1);
-                for (int t0 = 0; t0 < nk; t0 += 32) {
-                    const int t = t0 + lane;
-                    int klo = 0, khi = 0;
+            // phase visits each causal bucket once instead);
+            // ---- main: buckets backwards, keys within reach, by bound.
+            bool seeding = true;
+            int rs = -1, side = 1, nk = 0, t0 = 0; // shell rs of side x side x (rs + 1) positions
+            int b = bhi + 1, cx0 = 0, cy0 = 0, wx = 1; // main: bucket b, its reach rectangle
+            bool bseed = false;
+            float bpm_next = 0.0f;
+            for (;;) {
+                int klo = 0, khi = 0;
+                if (seeding) {
+                    if (t0 >= nk) {
+                        if (!(wl.nv < wl.C && rs < rcover && rs < WQ_RSEED)) {
+                            seeding = false;
+                            if (rs >= rcover)
+                                break; // the shells covered every causal key
+                            bpm_next = __ldg(G.bpm + bhi); // one bucket ahead
+                            nk = 0;
+                            t0 = 0;
+                            continue;
+                        }
+                        ++rs;
+                        side = 2 * rs + 1;
+                        nk = side * side * (rs + 1);
+                        t0 = 0;
+                    }
+                    const int t = t0 + lane, r = rs;
                     if (t < nk) {
                         const int db = t / (side * side), rem = t % (side * side);
                         const int dy = rem / side - r, dx = rem % side - r;
-                        const int b = bhi - db, cx = hx + dx, cy = hy + dy;
+                        const int bk = bhi - db, cx = hx + dx, cy = hy + dy;
                         const bool shell = max(max(abs(dx), abs(dy)), db) == r;
-                        if (shell && b >= 0 && cx >= 0 && cx < G.nx && cy >= 0 && cy < G.ny) {
-                            const int k2 = b * G.ncell + cy * G.nx + cx;
+                        if (shell && bk >= 0 && cx >= 0 && cx < G.nx && cy >= 0 && cy < G.ny) {
+                            const int k2 = bk * G.ncell + cy * G.nx + cx;
                             klo = __ldg(G.off + k2);
                             khi = __ldg(G.off + k2 + 1);
                         }
                     }
-                    visit_keys(khi > klo, klo, khi);
-                }
-            }
-            // ---- main: buckets backwards, keys within reach, by bound
-            if (rs < rcover) {
-                float bpm_next = __ldg(G.bpm + bhi); // one bucket ahead
-                const float ext_max = __ldg(G.ext_max);
-                for (int b = bhi; b >= 0; --b) {
-                    const float tau = key_d(wl.tauk);
-                    const float bpm_b = bpm_next;
-                    if (b > 0)
-                        bpm_next = __ldg(G.bpm + b - 1);
-                    if (!(time_lb(c, s3, bpm_b) <= tau))
-                        break;
-                    const float R = sqrtf(tau) * (1.0f + 0x1p-18f) + ext_max + c.delta;
-                    int cx0, cx1, cy0, cy1;
-                    reach_cells(c.sx, c.sx, R, G.x0, G.inv_cell, G.nx, cx0, cx1);
-                    reach_cells(c.sy, c.sy, R, G.y0, G.inv_cell, G.ny, cy0, cy1);
-                    const int wx = cx1 - cx0 + 1, nk = wx * (cy1 - cy0 + 1);
-                    const bool bseed = bhi - b <= rs;
-                    for (int t0 = 0; t0 < nk; t0 += 32) {
-                        const int t = t0 + lane;
-                        int klo = 0, khi = 0;
-                        if (t < nk) {
-                            const int cx = cx0 + t % wx, cy = cy0 + t / wx;
-                            const bool seeded = bseed && abs(cx - hx) <= rs && abs(cy - hy) <= rs;
-                            if (!seeded) {
-                                const int k2 = b * G.ncell + cy * G.nx + cx;
-                                const int4 kr = __ldg(G.krec + k2);
-                                const int a0 = kr.x, a1 = kr.y;
-                                if (a1 > a0) {
-                                    const float rx0 = G.x0 + (float)cx * G.cell;
-                                    const float ry0 = G.y0 + (float)cy * G.cell;
-                                    if (cell_lb(c, s3, rx0, rx0 + G.cell, ry0, ry0 + G.cell,
-                                                __int_as_float(kr.z), __int_as_float(kr.w)) <= key_d(wl.tauk)) {
-                                        klo = a0;
-                                        khi = a1;
-                                    }
+                } else {
+                    if (t0 >= nk) {
+                        if (--b < 0)
+                            break;
+                        const float tau = key_d(wl.tauk);
+                        const float bpm_b = bpm_next;
+                        if (b > 0)
+                            bpm_next = __ldg(G.bpm + b - 1);
+                        if (!(time_lb(c, s3, bpm_b) <= tau))
+                            break;
+                        const float R = sqrtf(tau) * (1.0f + 0x1p-18f) + ext_max + c.delta;
+                        int cx1, cy1;
+                        reach_cells(c.sx, c.sx, R, G.x0, G.inv_cell, G.nx, cx0, cx1);
+                        reach_cells(c.sy, c.sy, R, G.y0, G.inv_cell, G.ny, cy0, cy1);
+                        wx = cx1 - cx0 + 1;
+                        nk = wx * (cy1 - cy0 + 1);
+                        bseed = bhi - b <= rs;
+                        t0 = 0;
+                    }
+                    const int t = t0 + lane;
+                    if (t < nk) {
+                        const int cx = cx0 + t % wx, cy = cy0 + t / wx;
+                        const bool seeded = bseed && abs(cx - hx) <= rs && abs(cy - hy) <= rs;
+                        if (!seeded) {
+                            const int k2 = b * G.ncell + cy * G.nx + cx;
+                            const int4 kr = __ldg(G.krec + k2);
+                            const int a0 = kr.x, a1 = kr.y;
+                            if (a1 > a0) {
+                                const float rx0 = G.x0 + (float)cx * G.cell;
+                                const float ry0 = G.y0 + (float)cy * G.cell;
+                                if (cell_lb(c, s3, rx0, rx0 + G.cell, ry0, ry0 + G.cell,
+                                            __int_as_float(kr.z), __int_as_float(kr.w)) <= key_d(wl.tauk)) {
+                                    klo = a0;
+                                    khi = a1;
                                 }
                             }
                         }
-                        visit_keys(khi > klo, klo, khi);
                     }
                 }
+                t0 += 32;
+                visit_keys(khi > klo, klo, khi);
             }
         }
         __syncwarp();
@@ -413,8 +444,11 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_WARP_MINB)
                     od[i] = ki == SENT ? INFINITY : key_d(ki);
                 }
             } else {
-                if (lane == 0)
-                    ok = finalize_query(W, q, wl.L, wl.C, cl_d, cl_i, ent.y, st, 1);
+                if (lane == 0) {
+                    const unsigned r = finalize_query_ool(W, q, wl.L, wl.C, cl_d, cl_i, ent.y);
+                    ok = (r & 1u) != 0;
+                    st.fp64 += r >> 1;
+                }
                 ok = __shfl_sync(FULLMASK, ok, 0);
             }
         }
