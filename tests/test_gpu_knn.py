@@ -213,6 +213,9 @@ def test_index_segments_match_oracle():
     assert (seg[:, 11] >= ref["radius"][bid] - 1e-4).all()
     assert (seg[:, 11] <= ref["radius"][bid] + 1e-3).all()
     np.testing.assert_array_equal(pm, np.maximum.accumulate(seg[:, 7]))
+    # the info call waits for the build and reports the largest radius
+    assert ix.max_radius == float(seg[:, 11].max())
+    assert ix.coord_max >= float(np.abs(wl.xyzt[:, :3] * np.sqrt(np.asarray(SIG[:3]))).max()) * (1 - 1e-6)
     # every member within r of the stored segment [A', A' + AB'] (FP64 check)
     sq = np.sqrt(np.asarray(SIG[:3]))
     for s in range(S):
