@@ -27,7 +27,9 @@
 
 #define FB_EXTRA 32
 #define WQ_CMAX (64 + FB_EXTRA)
-#define WQ_RSEED 3
+#ifndef WQ_RSEED
+#define WQ_RSEED 4 // largest radius of the seeding shells
+#endif
 
 __host__ __device__ inline size_t wq_smem_per_warp()
 {
@@ -134,7 +136,7 @@ __device__ __forceinline__ void wl_merge(WarpList &w, unsigned long long ck, int
 }
 
 #ifndef TNN_WARP_MINB
-#define TNN_WARP_MINB 8 // 8 CTAs (32 warps) per SM: this kernel waits on chains of dependent loads
+#define TNN_WARP_MINB 7 // 7 CTAs (28 warps, 73 registers) per SM: fewer spills than 8 at 64 registers
 #endif
 __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_WARP_MINB)
     k_tnn_warp(const __grid_constant__ KnnLaunch L)
@@ -337,7 +339,7 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_WARP_MINB)
             // One loop hands visit_keys the keys of both phases, up to 32 per
             // round (a single inlined copy of the visit and its merges):
             // ---- seeding: shells of growing radius around the query's key, at
-            // most WQ_RSEED of them (a query with fewer than C valid points
+            // most WQ_RSEED + 1 of them (a query with fewer than C valid points
             // would otherwise grow the cube over the whole grid; the main
             // phase visits each causal bucket once instead);
             // ---- main: buckets backwards, keys within reach, by bound.
