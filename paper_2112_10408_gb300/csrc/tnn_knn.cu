@@ -763,7 +763,7 @@ extern "C" tnn_status tnn_autotune(const tnn_index *ix, tnn_knn_params *params,
     std::vector<Cand> cands;
     for (int F : {2, 3, 4})
         for (int E : {4, 8})
-            for (float dfr : {0.6f, 0.75f, 1.5f, 3.0f, 6.0f})
+            for (float dfr : {0.6f, 0.75f, 1.5f, 2.0f, 3.0f, 6.0f})
                 cands.push_back({F, E, 0, dfr});
     for (int F : {3, 4})
         cands.push_back({F, 4, TNN_FLAG_SWEEP, 0.0f});
