@@ -8,7 +8,7 @@
 // never exceeds the cylinder bound of any member segment, so whole keys are
 // excluded at once by the exclusion criterion of Sec. 3.4.
 //
-//   seeds   the 3 x 3 cells around the warp in the two most recent buckets:
+//   seeds   the 3 x 3 cells around the warp in the three most recent buckets:
 //           every lane keeps its F smallest cylinder bounds there; the union
 //           of those segments is scanned first (Algorithm 2's first fetch).
 //   main    buckets from the causal end backwards; a bucket is visited while
@@ -21,6 +21,9 @@
 #include "tnn_device.cuh"
 
 #define TNN_GMAX_F 6
+#ifndef TNN_SEED_BUCKETS
+#define TNN_SEED_BUCKETS 3 // newest buckets whose 3 x 3 cells seed a tile (at most 3)
+#endif
 
 // Lower bound on the cylinder bound (and so on the FP32 distance of any
 // valid member) of every segment of one key.
@@ -275,11 +278,13 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_GRID_MINB)
         if (bhi >= 0) {
             const int hx = min(max((int)floorf((0.5f * (bx0 + bx1) - G.x0) * G.inv_cell), 0), G.nx - 1);
             const int hy = min(max((int)floorf((0.5f * (by0 + by1) - G.y0) * G.inv_cell), 0), G.ny - 1);
-            // lanes 0..17 hold the 3 x 3 cells of buckets bhi and bhi - 1; the
-            // member segments of all 18 keys are staged 32 at a time
+            // lanes 0..9 TNN_SEED_BUCKETS - 1 hold the 3 x 3 cells of the
+            // newest buckets bhi, bhi - 1, ...; the member segments of all
+            // those keys are staged 32 at a time
             const int bq = bhi - lane / 9, cl = lane % 9;
             const int cx = hx + cl % 3 - 1, cy = hy + cl / 3 - 1;
-            const bool ok = lane < 18 && bq >= 0 && cx >= 0 && cx < G.nx && cy >= 0 && cy < G.ny;
+            const bool ok = lane < 9 * TNN_SEED_BUCKETS && bq >= 0 && cx >= 0 && cx < G.nx && cy >= 0 &&
+                            cy < G.ny;
             int lo = 0, n = 0;
             if (ok) {
                 const int key = bq * G.ncell + cy * G.nx + cx;
@@ -299,7 +304,7 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_GRID_MINB)
                 const int t = base + lane;
                 int src = 0;
 #pragma unroll
-                for (int j = 0; j < 18; ++j) {
+                for (int j = 0; j < 9 * TNN_SEED_BUCKETS; ++j) {
                     const int ij = __shfl_sync(FULLMASK, inc, j);
                     const int rj = __shfl_sync(FULLMASK, rel, j);
                     if (src == 0 && t < ij)
