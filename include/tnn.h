@@ -155,7 +155,7 @@ typedef struct {
     float defer_cells;     /* grid order: a query whose k-th candidate after
                               seeding is farther than defer_cells grid cells
                               (beyond the sigma_t lag^2 every key carries)
-                              leaves its shared 32-query tile and is finished
+                              leaves its shared query tile and is finished
                               by a warp of its own (Algorithm 2 puts finished
                               lines aside; here the slow ones are) -- 0 =
                               default 1.5, < 0 = never                       */
@@ -182,7 +182,11 @@ typedef struct {
  * in FP32 with a certified error bound; ranks the FP32 values cannot
  * separate are settled in FP64 on the GPU.
  *   d_q     [m][4] float queries (device), or NULL for self-query: every
- *           indexed point is a query (m must equal n_points).
+ *           indexed point is a query (m must equal n_points).  Self-queries
+ *           are taken in tiles of consecutive samples of one trajectory;
+ *           queries the caller passes, in tiles of 32 in the given order
+ *           (queries near one another in space-time and next to one
+ *           another in the array share work best).
  *   d_idx   [m][k] int32 out, d_d2 [m][k] float out (device).
  *   h_stats optional; when non-NULL the call SYNCHRONISES `stream`, fills
  *           the counters and reports what the kernels flagged (see

@@ -304,6 +304,23 @@ __device__ __forceinline__ void dbg_mark_seen(const KnnLaunch &L, int64_t row, i
         atomicOr(r + (j >> 5), 1u << (j & 31));
 }
 
+// The query row of this lane in global tile `tile` of window W, and whether
+// the lane has one: a run of consecutive rows of one trajectory for
+// self-queries (W->tile_rows), else 32 consecutive queries.
+__device__ __forceinline__ bool tile_query(const KnnWin *W, long long tile, int lane, int64_t &qrow)
+{
+    const int64_t t = tile - W->tile_begin;
+    if (W->tile_rows) {
+        const int64_t gt = W->tile_first + t;
+        const int64_t a = max((int64_t)__ldg(W->tile_rows + gt), W->row0);
+        const int64_t b = min((int64_t)__ldg(W->tile_rows + gt + 1), W->row0 + W->m);
+        qrow = a - W->row0 + lane;
+        return a + lane < b;
+    }
+    qrow = t * 32 + lane;
+    return qrow < W->m;
+}
+
 struct LaneStats {
     unsigned long long q, lb, pairs, segs, fp64;
 };

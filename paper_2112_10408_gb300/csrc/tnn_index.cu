@@ -680,6 +680,8 @@ static void free_index(tnn_index *ix)
     for (void *p : arrays)
         tnn_free(p, 0);
     tnn_free(ix->d_rmax, 0);
+    tnn_free(ix->d_tiles, 0);
+    free(ix->h_tiles);
     if (ix->built)
         cudaEventDestroy(ix->built);
     delete ix;
@@ -908,6 +910,29 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
                             cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(flag, meta_init, sizeof(meta_init), cudaMemcpyHostToDevice, st);
+    // query tiles of the self-queries: runs of up to 32 points of one trajectory
+    {
+        int64_t nt = 0;
+        for (int64_t t = 0; t < n_traj; ++t)
+            nt += (h_traj_off[t + 1] - h_traj_off[t] + 31) / 32;
+        ix->n_tiles = nt;
+        ix->h_tiles = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nt + 1));
+        if (!ix->h_tiles) {
+            free_index(ix);
+            tnn_set_error("index allocation failed (host tile table)");
+            return TNN_ERR_OOM;
+        }
+        int64_t j = 0;
+        for (int64_t t = 0; t < n_traj; ++t)
+            for (int64_t r = h_traj_off[t]; r < h_traj_off[t + 1]; r += 32)
+                ix->h_tiles[j++] = (int32_t)r;
+        ix->h_tiles[nt] = (int32_t)n;
+    }
+    if (e == cudaSuccess)
+        e = tnn_alloc((void **)&ix->d_tiles, sizeof(int32_t) * (size_t)(ix->n_tiles + 1), st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ix->d_tiles, ix->h_tiles, sizeof(int32_t) * (size_t)(ix->n_tiles + 1),
+                            cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = tnn_alloc((void **)&ix->d_rmax, sizeof(unsigned int), st);
     if (e == cudaSuccess)

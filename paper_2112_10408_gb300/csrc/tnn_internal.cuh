@@ -95,6 +95,12 @@ struct tnn_index {
     int4 *g_krec;
     float *g_ext_max; // [1]
     float bb_lo[4], bb_hi[4]; // bounding box of the points (x, y, z, t)
+    // Query tiles of the self-queries: every trajectory cut into runs of up
+    // to 32 consecutive points (a tile never spans two trajectories, whose
+    // regions may lie far apart); [n_tiles + 1] starts, the last is n.
+    int32_t *d_tiles;
+    int32_t *h_tiles;
+    int64_t n_tiles;
     unsigned int *d_rmax;     // [1] max_radius bits, written by the segment fit
     cudaEvent_t built;        // recorded after the build's last kernel
     bool rmax_known;          // max_radius has been read back
@@ -113,6 +119,12 @@ struct KnnWin {
     float *out_d2;
     int64_t m;
     int64_t tile_begin; // first global tile of this window
+    // Self-queries over the index's rows [row0, row0 + m): tile t of the
+    // window is the index tile tile_first + t clipped to that range (see
+    // tnn_index::d_tiles); NULL: tiles of 32 consecutive queries.
+    const int32_t *tile_rows;
+    int64_t row0;
+    int64_t tile_first;
     GridDesc grid;
     const float4 *pts_k;      // key-ordered points (tensor-core member scan)
     const int32_t *idx_k;
@@ -184,6 +196,10 @@ void tnn_free(void *p, cudaStream_t st);
 // Points in (t, index) order for the linear search, built on first use
 // (stream-ordered on `st`).
 tnn_status tnn_index_time_order(const tnn_index *ix, cudaStream_t st);
+// Sets the window's tiles (self-queries: per-trajectory tiles of the index;
+// otherwise 32 consecutive queries) and returns how many there are.
+int64_t tnn_window_tiles(const tnn_index *ix, KnnWin *w);
+
 // Points in space-time (Morton) order, built on first use.
 tnn_status tnn_index_space_order(const tnn_index *ix, cudaStream_t st);
 

@@ -185,6 +185,15 @@ tnn_status tnn_fill_window(const tnn_index *ix, const float *d_q, int64_t m,
         w->bb_hi[i] = ix->bb_hi[i];
     }
     w->q = d_q ? (const float4 *)d_q : ix->pts;
+    // self-queries (all points, or a run of them as tnn_knn_host passes):
+    // per-trajectory tiles
+    {
+        const float4 *q4 = w->q;
+        const bool self = q4 >= ix->pts && q4 < ix->pts + ix->n && m <= (ix->pts + ix->n) - q4;
+        w->tile_rows = self && ix->d_tiles ? ix->d_tiles : nullptr;
+        w->row0 = self ? (int64_t)(q4 - ix->pts) : 0;
+        w->tile_first = 0;
+    }
     w->out_idx = d_idx;
     w->out_d2 = d_d2;
     w->m = m;
@@ -229,6 +238,20 @@ __global__ void k_query_order_keys(const float4 *__restrict__ q, int64_t m, int6
         return;
     }
     keys[i] = ((unsigned long long)tnn_morton_xyt(q[i], lo, sc) << 32) | (unsigned long long)i;
+}
+
+int64_t tnn_window_tiles(const tnn_index *ix, KnnWin *w)
+{
+    if (w->m <= 0)
+        return 0;
+    if (!w->tile_rows)
+        return (w->m + TNN_TILE - 1) / TNN_TILE;
+    // the index tiles holding the first and the last row of the range
+    const int32_t *b = ix->h_tiles, *e = ix->h_tiles + ix->n_tiles;
+    const int64_t t0 = (std::upper_bound(b, e, (int32_t)w->row0) - b) - 1;
+    const int64_t t1 = (std::upper_bound(b, e, (int32_t)(w->row0 + w->m - 1)) - b) - 1;
+    w->tile_first = t0;
+    return t1 - t0 + 1;
 }
 
 // The per-query kernels that finish the tile kernel's deferred and
@@ -463,7 +486,7 @@ static tnn_status run_single(const tnn_index *ix, const float *d_q, int64_t m,
     L.nwin = 1;
     L.L_max = L.w0.L;
     L.kseg_max = ix->K;
-    L.total_tiles = (m + TNN_TILE - 1) / TNN_TILE;
+    L.total_tiles = tnn_window_tiles(ix, &L.w0);
     L.fb_cap = m;
     if (brute) {
         L.seed_pts = ix->pts_m;
@@ -625,7 +648,7 @@ extern "C" tnn_status tnn_batch_create(const tnn_index *const *indexes,
         TNN_ARG_CHECK((params[w].flags & TNN_FLAG_TC_TILES) == 0,
                       "TNN_FLAG_TC_TILES is for tnn_knn (window %d)", w);
         wins[w].tile_begin = tiles;
-        tiles += (m[w] + TNN_TILE - 1) / TNN_TILE;
+        tiles += tnn_window_tiles(indexes[w], &wins[w]);
         fb += m[w];
         L_max = std::max(L_max, wins[w].L);
         kseg = std::max(kseg, (int)indexes[w]->K);

@@ -30,8 +30,8 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32)
         if (tile >= L.total_tiles)
             break;
         const KnnWin *W = find_window(L, tile);
-        const int64_t qrow = (tile - W->tile_begin) * 32 + lane;
-        const bool active = qrow < W->m;
+        int64_t qrow;
+        const bool active = tile_query(W, tile, lane, qrow);
         const float4 q = active ? W->q[qrow] : make_float4(0.f, 0.f, 0.f, 0.f);
         const QCtx c = make_qctx(W, q, active);
         const float s0 = W->sig[0], s1 = W->sig[1], s2 = W->sig[2], s3 = W->sig[3];

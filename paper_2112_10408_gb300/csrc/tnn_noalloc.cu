@@ -76,7 +76,7 @@ extern "C" tnn_status tnn_knn_noalloc(const tnn_index *index, const float *d_q, 
     L.nwin = 1;
     L.L_max = L.w0.L;
     L.kseg_max = index->K;
-    L.total_tiles = (m + TNN_TILE - 1) / TNN_TILE;
+    L.total_tiles = tnn_window_tiles(index, &L.w0);
     L.fb_cap = m;
     L.scr = (KnnScratch *)scr;
     L.fb_list = (int2 *)((char *)scr + TNN_NOALLOC_HEADER);
