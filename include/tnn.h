@@ -425,10 +425,11 @@ void tnn_batch_destroy(tnn_batch *batch);
 /*
  * Choose the segment order (TNN_FLAG_SWEEP), seed_segments, extra and
  * defer_cells for one index and k by timing
- * the search on a sample of self-queries spread over the index (CUDA
- * events): max(m_sample, 262,144) of them, at most all n, so that the
- * sample fills the GPU.  Writes the best into *params (k, lag, flags
- * untouched).
+ * the search on a sample of self-queries (CUDA events): one run of
+ * max(m_sample, 262,144) consecutive indexed points (at most all n) from
+ * the middle of the index, so that the sample fills the GPU and takes the
+ * per-trajectory tiles of a self-query.  Writes the best into *params (k,
+ * lag, flags untouched).
  * Synchronises `stream`.
  */
 tnn_status tnn_autotune(const tnn_index *index, tnn_knn_params *params,

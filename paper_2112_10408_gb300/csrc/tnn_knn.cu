@@ -747,26 +747,19 @@ extern "C" tnn_status tnn_autotune(const tnn_index *ix, tnn_knn_params *params,
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = ix->n;
     // A sample too small to fill the GPU times the slowest warp, not the
-    // throughput: at least 262,144 queries (or all of them).
+    // throughput: at least 262,144 queries (or all of them).  The sample is
+    // one run of the index's own rows from its middle, searched as
+    // self-queries, so that it takes the same per-trajectory tiles as a
+    // self-query of every point.
     m_sample = std::max<int64_t>(m_sample, 262144);
-    int64_t nblk = std::max<int64_t>(1, std::min<int64_t>(m_sample / 32, n / 32));
-    if (n < 32)
-        nblk = 1;
-    const int64_t rows = std::min<int64_t>(32, n);
-    const int64_t m = nblk * rows;
-    const int64_t step = nblk > 1 ? (n - rows) / (nblk - 1) : 0;
-    float4 *dq = nullptr;
+    const int64_t m = std::min<int64_t>(m_sample, n);
+    const int64_t r0 = (n - m) / 2;
+    const float4 *dq = ix->pts + r0;
     int32_t *di = nullptr;
     float *dd = nullptr;
-    cudaError_t e = cudaMalloc(&dq, sizeof(float4) * m);
-    if (e == cudaSuccess)
-        e = cudaMalloc(&di, sizeof(int32_t) * m * params->k);
+    cudaError_t e = cudaMalloc(&di, sizeof(int32_t) * m * params->k);
     if (e == cudaSuccess)
         e = cudaMalloc(&dd, sizeof(float) * m * params->k);
-    if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(dq, rows * sizeof(float4), ix->pts,
-                              (step > 0 ? step : rows) * sizeof(float4),
-                              rows * sizeof(float4), nblk, cudaMemcpyDeviceToDevice, st);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess)
         e = cudaEventCreate(&e0);
@@ -786,7 +779,7 @@ extern "C" tnn_status tnn_autotune(const tnn_index *ix, tnn_knn_params *params,
     std::vector<Cand> cands;
     for (int F : {2, 3, 4})
         for (int E : {4, 8})
-            for (float dfr : {0.6f, 0.75f, 1.5f, 2.0f, 3.0f, 6.0f})
+            for (float dfr : {0.6f, 0.75f, 1.0f, 1.5f, 2.0f, 3.0f, 6.0f})
                 cands.push_back({F, E, 0, dfr});
     for (int F : {3, 4})
         cands.push_back({F, 4, TNN_FLAG_SWEEP, 0.0f});
@@ -822,7 +815,6 @@ extern "C" tnn_status tnn_autotune(const tnn_index *ix, tnn_knn_params *params,
         cudaEventDestroy(e0);
     if (e1)
         cudaEventDestroy(e1);
-    cudaFree(dq);
     cudaFree(di);
     cudaFree(dd);
     if (s == TNN_OK)
