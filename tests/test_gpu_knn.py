@@ -352,6 +352,38 @@ def test_linear_tensor_core_far_and_large_coordinates():
         assert_knn_equal(bi.cpu().numpy(), bd.cpu().numpy(), oi, od, what=f"far ffma={ffma}")
 
 
+def test_trajectory_tiles_give_the_same_lists_as_query_order_tiles():
+    """Self-queries are answered in tiles of one trajectory's consecutive
+    samples, passed queries in tiles of 32 in array order: the lists must be
+    bit-identical, also for ragged trajectories (1 to 70 samples, some empty),
+    a run of rows starting inside a trajectory, and against the oracle."""
+    rng = np.random.default_rng(71)
+    wl = synth.flights(90, 70, seed=72, n_routes=6)
+    # ragged trajectories: cut every flight to a random length (some to 0)
+    lens = rng.integers(0, 71, size=wl.n_traj)
+    lens[::17] = 0
+    lens[1::13] = 1
+    keep = np.concatenate([np.arange(wl.traj_off[f], wl.traj_off[f] + lens[f]) for f in range(wl.n_traj)])
+    xyzt = np.ascontiguousarray(wl.xyzt[keep])
+    off = np.zeros(wl.n_traj + 1, dtype=np.int64)
+    off[1:] = np.cumsum(lens)
+    x = torch.from_numpy(xyzt).cuda()
+    ix = tnn.tnn_build_segments(x, off, SIG, 10)
+    si, sd = tnn.tnn_knn(ix, 12, 0.0)
+    for kw in ({}, {"defer_cells": 0.3}, {"sweep": True}):
+        ki, kd = tnn.tnn_knn(ix, 12, 0.0, **kw)
+        qi, qd = tnn.tnn_knn(ix, 12, 0.0, q=x.clone(), **kw)
+        torch.cuda.synchronize()
+        assert torch.equal(ki, qi) and torch.equal(kd, qd), kw
+        assert torch.equal(ki, si) and torch.equal(kd, sd), kw
+    oi, od = oracle.knn(xyzt, 12, SIG, lag=0.0)
+    assert_knn_equal(si.cpu().numpy(), sd.cpu().numpy(), oi, od, what="ragged trajectories")
+    # a run of rows that starts and ends inside trajectories (tnn_knn_host's
+    # slices): the host pipeline against the device path
+    hi, hd = tnn.tnn_knn_host(xyzt, off, SIG, 10, 12, 0.0, chunks=5)
+    assert torch.equal(hi, si.cpu()) and torch.equal(hd, sd.cpu())
+
+
 @pytest.mark.parametrize("offset", [(9000.0, -7000.0), (2e5, 1.5e5)])
 def test_grid_search_far_from_the_origin(offset):
     # The grid's reach (cells within the k-th distance of a query) is taken in
