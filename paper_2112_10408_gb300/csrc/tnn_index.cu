@@ -104,12 +104,15 @@ __global__ void k_validate_traj(const float4 *__restrict__ p,
         atomicAdd(dur_sum, dur);
 }
 
-// Four lanes per segment (build order).  FP64 throughout, rounded once to
+// SF_LANES lanes per segment (build order).  FP64 throughout, rounded once to
 // the stored FP32 record:
 //   A' = fl(sqrt(s) A),  AB' = fl(sqrt(s) B - A'),  U' = fl(AB' / |AB'|^2)
 // The stored segment is [A', A' + AB'] (both exactly representable);
 // r bounds, with upward rounding, the distance of every member's scaled
 // position sqrt(s) p_j to it (Sec. 3.4 E_app, in the cylinder reading).
+#ifndef SF_LANES
+#define SF_LANES 4 // a power of two, at most 32
+#endif
 __global__ void k_segment_fit(const float4 *__restrict__ p,
                               const int32_t *__restrict__ traj_off,
                               const int32_t *__restrict__ seg_off, int n_traj,
@@ -118,10 +121,10 @@ __global__ void k_segment_fit(const float4 *__restrict__ p,
                               unsigned long long *__restrict__ keys,
                               unsigned int *rmax_bits)
 {
-    // four lanes per segment, splitting its members (FP64 is scarce: the
-    // per-segment set-up is repeated by each of the four)
-    const int s_raw = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2);
-    const int sub = threadIdx.x & 3;
+    // SF_LANES lanes per segment, splitting its members (FP64 is scarce:
+    // the per-segment set-up is repeated by each of them)
+    const int s_raw = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / SF_LANES);
+    const int sub = threadIdx.x % SF_LANES;
     const bool valid = s_raw < S;
     const int s = valid ? s_raw : S - 1;
     // trajectory of segment s: largest tr with seg_off[tr] <= s
@@ -159,7 +162,7 @@ __global__ void k_segment_fit(const float4 *__restrict__ p,
     float mag = fabsf(Af[0]) + fabsf(Af[1]) + fabsf(Af[2]) + fabsf((float)E[0]) +
                 fabsf((float)E[1]) + fabsf((float)E[2]);
     double r2 = 0.0;
-    for (int j = sub; j < (valid ? count : 0); j += 4) {
+    for (int j = sub; j < (valid ? count : 0); j += SF_LANES) {
         const float4 v = p[first + j];
         const double D0 = qq[0] * (double)v.x - A[0], D1 = qq[1] * (double)v.y - A[1],
                      D2 = qq[2] * (double)v.z - A[2];
@@ -168,7 +171,7 @@ __global__ void k_segment_fit(const float4 *__restrict__ p,
         r2 = fmax(r2, e0 * e0 + e1 * e1 + e2 * e2);
         mag = fmaxf(mag, fabsf(qf[0] * v.x) + fabsf(qf[1] * v.y) + fabsf(qf[2] * v.z));
     }
-    for (int o = 1; o < 4; o <<= 1) {
+    for (int o = 1; o < SF_LANES; o <<= 1) {
         r2 = fmax(r2, __shfl_xor_sync(0xffffffffu, r2, o));
         mag = fmaxf(mag, __shfl_xor_sync(0xffffffffu, mag, o));
     }
@@ -986,7 +989,7 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
                                         q1 * ix->bb_hi[1], ix->bb_lo[3], ix->bb_hi[3], dur, S);
 
     // ---- segments, their t_A order, the running maximum of t_B, the grid
-    k_segment_fit<<<(int)(((int64_t)Si * 4 + tb - 1) / tb), tb, 0, st>>>(
+    k_segment_fit<<<(int)(((int64_t)Si * SF_LANES + tb - 1) / tb), tb, 0, st>>>(
         ix->pts, (const int32_t *)toff_d.p, (const int32_t *)soff_d.p, Ti, Si, K,
         q0, q1, sqrt(params->sigma[2]), (float4 *)rec_d.p, keys, ix->d_rmax);
     k_fill<<<(s2 - Si + tb - 1) / tb + 1, tb, 0, st>>>(keys, Si, s2);
