@@ -20,7 +20,9 @@
 #pragma once
 #include "tnn_device.cuh"
 
+#ifndef TNN_GMAX_F
 #define TNN_GMAX_F 6
+#endif
 #ifndef TNN_SEED_BUCKETS
 #define TNN_SEED_BUCKETS 3 // newest buckets whose 3 x 3 cells seed a tile (at most 3)
 #endif
