@@ -486,6 +486,8 @@ static tnn_status run_single(const tnn_index *ix, const float *d_q, int64_t m,
     L.nwin = 1;
     L.L_max = L.w0.L;
     L.kseg_max = ix->K;
+    if (brute)
+        L.w0.tile_rows = nullptr; // the linear search gains nothing from trajectory tiles
     L.total_tiles = tnn_window_tiles(ix, &L.w0);
     L.fb_cap = m;
     if (brute) {
