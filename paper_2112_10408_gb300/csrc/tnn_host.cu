@@ -11,6 +11,9 @@
 #include "tnn_internal.cuh"
 
 #define TNN_HOST_MAX_DEVICES 64
+#ifndef TNN_SLICE_RATIO
+#define TNN_SLICE_RATIO (2.0 / 3.0) // size of a slice over the one before it
+#endif
 
 // One copy stream per device, created on first use (non-blocking: it does
 // not serialise with the legacy default stream).
@@ -79,12 +82,12 @@ extern "C" tnn_status tnn_knn_host(const float *h_xyzt, int64_t n, const int64_t
     int64_t bound[65];
     {
         double wsum = 0.0, w = 1.0;
-        for (int c = 0; c < nc; ++c, w *= 2.0 / 3.0)
+        for (int c = 0; c < nc; ++c, w *= TNN_SLICE_RATIO)
             wsum += w;
         double acc = 0.0;
         w = 1.0;
         bound[0] = 0;
-        for (int c = 0; c < nc; ++c, w *= 2.0 / 3.0) {
+        for (int c = 0; c < nc; ++c, w *= TNN_SLICE_RATIO) {
             acc += w;
             bound[c + 1] = c + 1 == nc ? n : std::min<int64_t>(n, (int64_t)(n * (acc / wsum)));
         }
