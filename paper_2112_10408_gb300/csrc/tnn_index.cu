@@ -401,12 +401,13 @@ void tnn_bitonic_sort(unsigned long long *keys, int n2, cudaStream_t st)
 __global__ void k_gather_segments(const unsigned long long *__restrict__ keys,
                                   const float4 *__restrict__ rec, int S,
                                   float4 *__restrict__ out,
-                                  float *__restrict__ tA)
+                                  float *__restrict__ tA, int32_t *__restrict__ pos)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= S)
         return;
     int s = (int)(keys[i] & 0xffffffffu);
+    pos[s] = i;
     float4 a = rec[4 * s];
     out[4 * i + 0] = a;
     out[4 * i + 1] = rec[4 * s + 1];
@@ -543,16 +544,18 @@ struct GridBuild {
     int nx, ny, ncell, nb;
 };
 
-// Key of every segment (t_A order position p) and the per-key aggregates:
-// the extent (FP64, rounded up) of the member cylinders around the key's cell
-// rectangle and the largest t_B; the per-bucket largest t_B.
+// Key of every segment (records in build order; the key's low half is the
+// build id, so the keys sort without the t_A order and the two sorts run
+// side by side) and the per-key aggregates: the extent (FP64, rounded up) of
+// the member cylinders around the key's cell rectangle and the largest t_B;
+// the per-bucket largest t_B.
 __global__ void k_grid_keys(const float4 *__restrict__ seg, int S, GridBuild g,
                             unsigned long long *__restrict__ keys,
                             unsigned int *__restrict__ ext_bits,
                             unsigned int *__restrict__ tB_ord,
                             unsigned int *__restrict__ bmax_ord)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x; // build id
     if (p >= S)
         return;
     const float4 a = seg[4 * p], u = seg[4 * p + 1], b = seg[4 * p + 2];
@@ -598,12 +601,13 @@ __global__ void k_grid_offsets(const unsigned long long *__restrict__ keys, int 
     off[k] = lo;
 }
 
+// t_A position of the segment of every sorted grid key (keys hold build ids).
 __global__ void k_grid_ids(const unsigned long long *__restrict__ keys, int S,
-                           int32_t *__restrict__ ids)
+                           const int32_t *__restrict__ pos, int32_t *__restrict__ ids)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < S)
-        ids[i] = (int32_t)(keys[i] & 0xffffffffu);
+        ids[i] = pos[(int)(keys[i] & 0xffffffffu)];
 }
 
 // Segment records in grid-key order (record 3's trajectory field replaced by
@@ -690,6 +694,30 @@ static void free_index(tnn_index *ix)
     delete ix;
 }
 
+// The build's second stream per device (non-blocking, created on first
+// use): the grid keys and their sort run there beside the t_A sort.
+#define TNN_BUILD_MAX_DEVICES 64
+static std::mutex g_side_mu;
+static cudaStream_t g_side_stream[TNN_BUILD_MAX_DEVICES];
+
+static cudaError_t side_stream(cudaStream_t *out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev < 0 || dev >= TNN_BUILD_MAX_DEVICES)
+        return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_side_mu);
+    if (!g_side_stream[dev]) {
+        e = cudaStreamCreateWithFlags(&g_side_stream[dev], cudaStreamNonBlocking);
+        if (e != cudaSuccess)
+            return e;
+    }
+    *out = g_side_stream[dev];
+    return cudaSuccess;
+}
+
 // Build-time scratch, returned to the pool in stream order.
 struct DevBuf {
     void *p = nullptr;
@@ -759,14 +787,10 @@ static GridBuild grid_geometry(double xmn, double xmx, double ymn, double ymx, d
     return g;
 }
 
-// Build the grid over the t_A-ordered segments (stream-ordered, no host
-// synchronisation).
-static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2, const GridBuild &g,
-                             cudaStream_t st)
+// The grid's arrays, zeroed where the key kernel takes maxima.
+static tnn_status grid_alloc(tnn_index *ix, const GridBuild &g, cudaStream_t st)
 {
-    const int S = (int)ix->S, tb = 256;
-    const int nx = g.nx, ny = g.ny, nb = g.nb;
-    const int nkeys = nb * g.ncell;
+    const int S = (int)ix->S, nb = g.nb, nkeys = nb * g.ncell;
     TNN_CUDA_TRY(tnn_alloc((void **)&ix->g_off, sizeof(int32_t) * (nkeys + 1), st));
     TNN_CUDA_TRY(tnn_alloc((void **)&ix->g_ids, sizeof(int32_t) * S, st));
     TNN_CUDA_TRY(tnn_alloc((void **)&ix->g_seg, sizeof(float4) * 4 * (size_t)S, st));
@@ -779,13 +803,18 @@ static tnn_status build_grid(tnn_index *ix, unsigned long long *keys, int s2, co
     TNN_CUDA_TRY(cudaMemsetAsync(ix->g_ext, 0, sizeof(float) * nkeys, st));
     TNN_CUDA_TRY(cudaMemsetAsync(ix->g_tB, 0, sizeof(float) * nkeys, st));
     TNN_CUDA_TRY(cudaMemsetAsync(ix->g_bpm, 0, sizeof(float) * nb, st));
-    k_fill<<<(s2 - S + tb - 1) / tb + 1, tb, 0, st>>>(keys, S, s2);
-    k_grid_keys<<<(S + tb - 1) / tb, tb, 0, st>>>(ix->seg, S, g, keys, (unsigned int *)ix->g_ext,
-                                                 (unsigned int *)ix->g_tB,
-                                                 (unsigned int *)ix->g_bpm);
-    tnn_bitonic_sort(keys, s2, st);
+    return TNN_OK;
+}
+
+// The grid from its sorted keys (build ids; pos = t_A position of each).
+static tnn_status build_grid(tnn_index *ix, const unsigned long long *keys, const int32_t *pos,
+                             const GridBuild &g, cudaStream_t st)
+{
+    const int S = (int)ix->S, tb = 256;
+    const int nx = g.nx, ny = g.ny, nb = g.nb;
+    const int nkeys = nb * g.ncell;
     k_grid_offsets<<<(nkeys + 1 + tb - 1) / tb, tb, 0, st>>>(keys, S, nkeys, ix->g_off);
-    k_grid_ids<<<(S + tb - 1) / tb, tb, 0, st>>>(keys, S, ix->g_ids);
+    k_grid_ids<<<(S + tb - 1) / tb, tb, 0, st>>>(keys, S, pos, ix->g_ids);
     k_grid_records<<<(S + tb - 1) / tb, tb, 0, st>>>(ix->seg, ix->g_ids, S, ix->g_seg);
     k_decode_ord<<<(nkeys + tb - 1) / tb, tb, 0, st>>>((unsigned int *)ix->g_tB, nkeys);
     k_decode_ord<<<(nb + tb - 1) / tb, tb, 0, st>>>((unsigned int *)ix->g_bpm, nb);
@@ -988,23 +1017,66 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
     const GridBuild geo = grid_geometry(q0 * ix->bb_lo[0], q0 * ix->bb_hi[0], q1 * ix->bb_lo[1],
                                         q1 * ix->bb_hi[1], ix->bb_lo[3], ix->bb_hi[3], dur, S);
 
-    // ---- segments, their t_A order, the running maximum of t_B, the grid
-    k_segment_fit<<<(int)(((int64_t)Si * SF_LANES + tb - 1) / tb), tb, 0, st>>>(
-        ix->pts, (const int32_t *)toff_d.p, (const int32_t *)soff_d.p, Ti, Si, K,
-        q0, q1, sqrt(params->sigma[2]), (float4 *)rec_d.p, keys, ix->d_rmax);
-    k_fill<<<(s2 - Si + tb - 1) / tb + 1, tb, 0, st>>>(keys, Si, s2);
-    tnn_bitonic_sort(keys, s2, st);
-    k_gather_segments<<<(Si + tb - 1) / tb, tb, 0, st>>>(keys, (const float4 *)rec_d.p,
-                                                         Si, ix->seg, ix->segTA);
+    // ---- segments, their t_A order, the running maximum of t_B, the grid.
+    // The grid keys come from the build-order records, so their sort runs on
+    // a second stream beside the t_A sort; the two join before the grid's
+    // offsets and records.
     {
+        DevBuf keys2_d, pos_d, bmax_d;
+        cudaStream_t st2 = nullptr;
+        cudaEvent_t ev_fit = nullptr, ev_keys = nullptr;
         const int nblk = (Si + 1023) / 1024;
-        float *bmax = (float *)((char *)rec_d.p); // the unsorted records are no longer read
-        k_pm_block_max<<<nblk, 1024, 0, st>>>(ix->seg, Si, bmax);
-        k_pm_apply<<<nblk, 1024, 0, st>>>(ix->seg, Si, bmax, ix->segPM);
-    }
-    {
-        tnn_status gs = build_grid(ix, keys, s2, geo, st);
+        e = side_stream(&st2);
+        if (e == cudaSuccess)
+            e = keys2_d.alloc(sizeof(unsigned long long) * s2, st);
+        if (e == cudaSuccess)
+            e = pos_d.alloc(sizeof(int32_t) * (size_t)Si, st);
+        if (e == cudaSuccess)
+            e = bmax_d.alloc(sizeof(float) * (size_t)nblk, st);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&ev_fit, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&ev_keys, cudaEventDisableTiming);
+        tnn_status gs = e == cudaSuccess ? grid_alloc(ix, geo, st) : TNN_ERR_CUDA;
+        if (gs == TNN_OK) {
+            unsigned long long *keys2 = (unsigned long long *)keys2_d.p;
+            k_segment_fit<<<(int)(((int64_t)Si * SF_LANES + tb - 1) / tb), tb, 0, st>>>(
+                ix->pts, (const int32_t *)toff_d.p, (const int32_t *)soff_d.p, Ti, Si, K,
+                q0, q1, sqrt(params->sigma[2]), (float4 *)rec_d.p, keys, ix->d_rmax);
+            e = cudaEventRecord(ev_fit, st);
+            if (e == cudaSuccess)
+                e = cudaStreamWaitEvent(st2, ev_fit, 0);
+            if (e == cudaSuccess) {
+                // second stream: grid keys of the build-order records, sorted
+                k_fill<<<(s2 - Si + tb - 1) / tb + 1, tb, 0, st2>>>(keys2, Si, s2);
+                k_grid_keys<<<(Si + tb - 1) / tb, tb, 0, st2>>>(
+                    (const float4 *)rec_d.p, Si, geo, keys2, (unsigned int *)ix->g_ext,
+                    (unsigned int *)ix->g_tB, (unsigned int *)ix->g_bpm);
+                tnn_bitonic_sort(keys2, s2, st2);
+                e = cudaEventRecord(ev_keys, st2);
+            }
+            // this stream: the t_A order and the running maximum of t_B
+            k_fill<<<(s2 - Si + tb - 1) / tb + 1, tb, 0, st>>>(keys, Si, s2);
+            tnn_bitonic_sort(keys, s2, st);
+            k_gather_segments<<<(Si + tb - 1) / tb, tb, 0, st>>>(keys, (const float4 *)rec_d.p, Si,
+                                                                 ix->seg, ix->segTA, (int32_t *)pos_d.p);
+            k_pm_block_max<<<nblk, 1024, 0, st>>>(ix->seg, Si, (float *)bmax_d.p);
+            k_pm_apply<<<nblk, 1024, 0, st>>>(ix->seg, Si, (const float *)bmax_d.p, ix->segPM);
+            if (e == cudaSuccess)
+                e = cudaStreamWaitEvent(st, ev_keys, 0);
+            if (e == cudaSuccess)
+                gs = build_grid(ix, keys2, (const int32_t *)pos_d.p, geo, st);
+            else
+                gs = TNN_ERR_CUDA;
+        }
+        if (ev_fit)
+            cudaEventDestroy(ev_fit);
+        if (ev_keys)
+            cudaEventDestroy(ev_keys);
         if (gs != TNN_OK) {
+            if (e != cudaSuccess)
+                tnn_set_error("index build failed: %s", cudaGetErrorString(e));
+            cudaStreamSynchronize(st2);
             free_index(ix);
             return gs;
         }
