@@ -358,7 +358,8 @@ tnn_status tnn_selftest_bounded_wait(int32_t limit_us, tnn_stream_t stream);
  * copied in, indexed (as tnn_build_segments with *bp) and every point is
  * answered as its own query (as tnn_knn with d_q = NULL and *kp); the
  * neighbour lists land in host memory.  The queries are answered in `chunks`
- * consecutive slices of rows (0 = the library's choice, 2; at most 64),
+ * consecutive slices of rows (0 = the library's choice: 2, or 3 from 2^20
+ * points; at most 64),
  * shrinking by 2/3 from one to the next: a second stream copies a slice's
  * lists out while the search works on the next slice.
  *   h_xyzt [n][4] float, h_traj_off [n_traj + 1]: as tnn_build_segments,

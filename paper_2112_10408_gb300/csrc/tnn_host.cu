@@ -49,7 +49,9 @@ extern "C" tnn_status tnn_knn_host(const float *h_xyzt, int64_t n, const int64_t
                   (long long)n);
     TNN_ARG_CHECK(kp->k >= 1 && kp->k <= 64, "k must be in [1, 64], got %d", kp->k);
     TNN_ARG_CHECK(chunks >= 0 && chunks <= 64, "chunks must be in [0, 64]");
-    const int nc = (int)std::min<int64_t>(chunks == 0 ? 2 : chunks, n);
+    // the library's choice: 2 slices, 3 from 2^20 queries (the fixed costs of
+    // a slice weigh less against a longer search)
+    const int nc = (int)std::min<int64_t>(chunks == 0 ? (n >= (1 << 20) ? 3 : 2) : chunks, n);
     const int64_t k = kp->k;
     cudaStream_t st = (cudaStream_t)stream, cs = nullptr;
     TNN_CUDA_TRY(copy_stream(&cs));
