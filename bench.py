@@ -345,12 +345,13 @@ def _extras(tnn, synth, flush, peaks, steps):
     idxs = [tnn.tnn_build_segments(torch.from_numpy(wl.xyzt).cuda(), wl.traj_off, sigma, 20)
             for wl, _ in wins]
     # two tunings of the same launch: the library defaults, and every window
-    # autotuned on its own (tnn_autotune: segment order, seed count, list
-    # width, deferral radius for that window's size and k); the faster one is
-    # the batched figure
+    # autotuned on its own (tnn_autotune: seed count, list width, deferral
+    # radius for that window's size and k); the faster one is the batched
+    # figure.  A batch runs one segment order for all its windows, so the
+    # per-window tunings keep the grid order.
     ks = [k for _, k in wins]
     t0 = time.perf_counter()
-    tuned = [tnn.tnn_autotune(ix, k, 0.0) for ix, k in zip(idxs, ks)]
+    tuned = [dict(tnn.tnn_autotune(ix, k, 0.0), sweep=False) for ix, k in zip(idxs, ks)]
     tune_s = time.perf_counter() - t0
     timing = {}
     for name, tunings in (("library_defaults", [{}] * len(wins)), ("autotuned_per_window", tuned)):

@@ -405,7 +405,9 @@ typedef struct tnn_batch tnn_batch;
  * the end of the batch") done by letting finished warps take new work.
  *   indexes[w], d_q[w] (NULL = self-query), m[w], params[w], d_idx[w],
  *   d_d2[w]: as tnn_knn, per window.  The arrays are read at creation; the
- *   device buffers must stay valid while the batch is run.
+ *   device buffers must stay valid while the batch is run.  All windows
+ *   take the same segment order (TNN_FLAG_SWEEP set in all or in none;
+ *   otherwise TNN_ERR_INVALID_ARG); TNN_FLAG_TC_TILES is not accepted.
  * The launch is captured once into a CUDA graph; tnn_batch_run replays it.
  * This is the batched k-NN call of the library (create once, run many
  * times).

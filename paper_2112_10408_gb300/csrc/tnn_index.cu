@@ -741,14 +741,14 @@ static float host_ord2f(uint32_t u)
 // Grid geometry from the points' bounding box in sqrt(sigma)-scaled x, y
 // (it holds every segment midpoint up to rounding, and keys are clamped to
 // the grid), their time range and the summed segment duration.  Buckets span
-// about four mean segment durations (at most 4096 of them); cells are square,
-// about two segments per (bucket, cell) on average, at most 65,536 cells and
+// about five mean segment durations (at most 4096 of them); cells are square,
+// about one segment per (bucket, cell) on average, at most 65,536 cells and
 // 2^22 keys.
 #ifndef TNN_BUCKET_SEGS
-#define TNN_BUCKET_SEGS 4.0 // bucket span in mean segment durations
+#define TNN_BUCKET_SEGS 5.0 // bucket span in mean segment durations
 #endif
 #ifndef TNN_KEY_SEGS
-#define TNN_KEY_SEGS 2.0 // mean segments per (bucket, cell)
+#define TNN_KEY_SEGS 1.0 // mean segments per (bucket, cell)
 #endif
 static GridBuild grid_geometry(double xmn, double xmx, double ymn, double ymx, double tmn,
                                double tmx, double dur, int64_t S)

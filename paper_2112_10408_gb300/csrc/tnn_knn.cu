@@ -649,6 +649,9 @@ extern "C" tnn_status tnn_batch_create(const tnn_index *const *indexes,
                       "NULL output for window %d", w);
         TNN_ARG_CHECK((params[w].flags & TNN_FLAG_TC_TILES) == 0,
                       "TNN_FLAG_TC_TILES is for tnn_knn (window %d)", w);
+        TNN_ARG_CHECK((params[w].flags & TNN_FLAG_SWEEP) == (params[0].flags & TNN_FLAG_SWEEP),
+                      "all windows of a batch take the same segment order (TNN_FLAG_SWEEP; window %d "
+                      "differs from window 0)", w);
         wins[w].tile_begin = tiles;
         tiles += tnn_window_tiles(indexes[w], &wins[w]);
         fb += m[w];

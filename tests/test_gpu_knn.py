@@ -302,6 +302,9 @@ def test_batched_windows_match_oracle():
         oi, od = oracle.knn(wl.xyzt, k, SIG, qsel=q)
         assert_knn_equal(b.idx[w].cpu().numpy()[q], b.d2[w].cpu().numpy()[q], oi, od,
                          what=f"window {w} k={k}")
+    # one segment order per batch: mixing the sweep and the grid is refused
+    with pytest.raises(tnn.TNNError):
+        tnn.Batch(idxs[:2], ks[:2], tunings=[{"sweep": True}, {}])
 
 
 def test_autotune_returns_valid_knobs():
