@@ -985,17 +985,40 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
         ix->pts, (const int32_t *)toff_d.p, Ti, K, flag, (double *)(flag + 10));
     k_point_bbox<<<(int)std::min<int64_t>((ix->n + tb - 1) / tb, 608), tb, 0, st>>>(
         ix->pts, (int)ix->n, flag + 2);
+    // The values come back through a page-locked buffer of this host thread
+    // and an event: the segment fit (which needs neither the geometry nor
+    // the verdict) is enqueued before the host waits, so it runs while the
+    // host chooses the geometry and enqueues the rest.  Invalid input is
+    // still reported here; the fit's output is then dropped.
+    static thread_local unsigned int *t_meta = nullptr;
     unsigned int hm[12];
+    cudaEvent_t ev_meta = nullptr;
     e = cudaGetLastError();
+    if (e == cudaSuccess && !t_meta)
+        e = cudaHostAlloc((void **)&t_meta, sizeof(hm), cudaHostAllocPortable);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(hm, flag, sizeof(hm), cudaMemcpyDeviceToHost, st);
+        e = cudaEventCreateWithFlags(&ev_meta, cudaEventDisableTiming);
     if (e == cudaSuccess)
-        e = cudaStreamSynchronize(st);
+        e = cudaMemcpyAsync(t_meta, flag, sizeof(hm), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(ev_meta, st);
+    const double q0 = sqrt(params->sigma[0]), q1 = sqrt(params->sigma[1]);
+    if (e == cudaSuccess) {
+        k_segment_fit<<<(int)(((int64_t)Si * SF_LANES + tb - 1) / tb), tb, 0, st>>>(
+            ix->pts, (const int32_t *)toff_d.p, (const int32_t *)soff_d.p, Ti, Si, K,
+            q0, q1, sqrt(params->sigma[2]), (float4 *)rec_d.p, keys, ix->d_rmax);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaEventSynchronize(ev_meta);
+    if (ev_meta)
+        cudaEventDestroy(ev_meta);
     if (e != cudaSuccess) {
         free_index(ix);
         tnn_set_error("index validation failed: %s", cudaGetErrorString(e));
         return TNN_ERR_CUDA;
     }
+    memcpy(hm, t_meta, sizeof(hm));
     if (hm[0] & BAD_VALUE) {
         free_index(ix);
         tnn_set_error("non-finite or too large (|v| > 1e15) coordinate in input");
@@ -1013,7 +1036,6 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
     }
     double dur = 0.0;
     memcpy(&dur, &hm[10], sizeof(double));
-    const double q0 = sqrt(params->sigma[0]), q1 = sqrt(params->sigma[1]);
     const GridBuild geo = grid_geometry(q0 * ix->bb_lo[0], q0 * ix->bb_hi[0], q1 * ix->bb_lo[1],
                                         q1 * ix->bb_hi[1], ix->bb_lo[3], ix->bb_hi[3], dur, S);
 
@@ -1040,10 +1062,7 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
         tnn_status gs = e == cudaSuccess ? grid_alloc(ix, geo, st) : TNN_ERR_CUDA;
         if (gs == TNN_OK) {
             unsigned long long *keys2 = (unsigned long long *)keys2_d.p;
-            k_segment_fit<<<(int)(((int64_t)Si * SF_LANES + tb - 1) / tb), tb, 0, st>>>(
-                ix->pts, (const int32_t *)toff_d.p, (const int32_t *)soff_d.p, Ti, Si, K,
-                q0, q1, sqrt(params->sigma[2]), (float4 *)rec_d.p, keys, ix->d_rmax);
-            e = cudaEventRecord(ev_fit, st);
+            e = cudaEventRecord(ev_fit, st); // the fit (enqueued above) and the grid's zeroing
             if (e == cudaSuccess)
                 e = cudaStreamWaitEvent(st2, ev_fit, 0);
             if (e == cudaSuccess) {
