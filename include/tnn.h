@@ -138,7 +138,18 @@ enum {
        usual.  128 queries share a traversal.  The first such call builds a
        grid-key-ordered copy of the points in the index (16 B per point).
        Same exact result. */
-    TNN_FLAG_TC_TILES = 8
+    TNN_FLAG_TC_TILES = 8,
+    /* tnn_knn_host only (other calls ignore it): h_idx and h_d2 are
+       page-locked host memory mapped into the device's address space over
+       their whole extent (cudaHostAlloc, or cudaHostRegister of the whole
+       range).  The shared-tile kernel then writes each finished tile's rows
+       into them itself (coalesced stores), so the transfer runs under the
+       search, and a kernel writes the few rows finished later (queries
+       handed to a warp of their own, or settled exactly).  The call checks
+       the first and the last element of each (TNN_ERR_INVALID_ARG when
+       they are not mapped); the caller vouches for the rest.  Ignored
+       together with TNN_FLAG_TC_TILES. */
+    TNN_FLAG_MAPPED_OUT = 16
 };
 
 typedef struct {
@@ -358,10 +369,11 @@ tnn_status tnn_selftest_bounded_wait(int32_t limit_us, tnn_stream_t stream);
  * copied in, indexed (as tnn_build_segments with *bp) and every point is
  * answered as its own query (as tnn_knn with d_q = NULL and *kp); the
  * neighbour lists land in host memory.  The queries are answered in `chunks`
- * consecutive slices of rows (0 = the library's choice: 2, or 3 from 2^20
- * points; at most 64),
- * shrinking by 2/3 from one to the next: a second stream copies a slice's
- * lists out while the search works on the next slice.
+ * consecutive slices of rows (at most 64), shrinking by 2/3 from one to the
+ * next: a second stream copies a slice's lists out while the search works
+ * on the next slice.  0 = the library's choice: 2 slices, 3 from 2^20
+ * points.  With TNN_FLAG_MAPPED_OUT there are no slices (`chunks` is
+ * ignored): the search kernels write the lists into host memory as they go.
  *   h_xyzt [n][4] float, h_traj_off [n_traj + 1]: as tnn_build_segments,
  *     host memory (page-locked memory is copied faster).
  *   h_idx [n][k] int32, h_d2 [n][k] float: host outputs, layout as tnn_knn.

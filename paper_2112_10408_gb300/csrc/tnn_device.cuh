@@ -321,6 +321,50 @@ __device__ __forceinline__ bool tile_query(const KnnWin *W, long long tile, int 
     return qrow < W->m;
 }
 
+// Copy rows [row0, row0 + cnt) of a finished tile from the window's lists
+// (just written by this warp) to the mirror lists (KnnLaunch::mirror_idx):
+// consecutive words across the lanes, so every store instruction writes
+// contiguous bytes (16 per lane when KnnLaunch::mirror_vec, else 4); two
+// words of each list in flight per lane before their stores (more would
+// take registers from the search loops).
+template <typename T>
+__device__ __forceinline__ void mirror_words(const T *__restrict__ si, const T *__restrict__ sd,
+                                             T *__restrict__ di, T *__restrict__ dd, int64_t nw, int lane)
+{
+    for (int64_t j0 = 0; j0 < nw; j0 += 2 * 32) {
+        T vi[2], vd[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t j = j0 + u * 32 + lane;
+            if (j < nw) {
+                vi[u] = __ldcg(si + j);
+                vd[u] = __ldcg(sd + j);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t j = j0 + u * 32 + lane;
+            if (j < nw) {
+                di[j] = vi[u];
+                dd[j] = vd[u];
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void mirror_tile(const KnnLaunch &L, const KnnWin *W, int64_t row0, int cnt,
+                                            int lane)
+{
+    __syncwarp();
+    const int64_t o = row0 * W->k, nw = (int64_t)cnt * W->k;
+    if (L.mirror_vec) // k % 4 == 0 and 16-byte aligned lists: whole int4 words
+        mirror_words((const int4 *)(W->out_idx + o), (const int4 *)(W->out_d2 + o),
+                     (int4 *)(L.mirror_idx + o), (int4 *)(L.mirror_d2 + o), nw / 4, lane);
+    else
+        mirror_words((const int *)(W->out_idx + o), (const int *)(W->out_d2 + o), (int *)(L.mirror_idx + o),
+                     (int *)(L.mirror_d2 + o), nw, lane);
+}
+
 struct LaneStats {
     unsigned long long q, lb, pairs, segs, fp64;
 };

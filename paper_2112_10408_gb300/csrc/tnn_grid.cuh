@@ -74,6 +74,10 @@ __device__ __forceinline__ float warp_maxf(float v)
 #define TNN_GRID_MINB 4
 #endif
 
+// MIRROR: also copy each finished tile's rows to KnnLaunch::mirror_idx /
+// mirror_d2 (a separate instantiation, so that the plain search compiles
+// without that code).
+template <bool MIRROR>
 __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_GRID_MINB)
     k_tnn_grid_search(const __grid_constant__ KnnLaunch L)
 {
@@ -424,6 +428,11 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_GRID_MINB)
             }
         }
         __syncwarp();
+        if (MIRROR) {
+            const int cnt = __popc(__ballot_sync(FULLMASK, active));
+            if (cnt > 0)
+                mirror_tile(L, W, __shfl_sync(FULLMASK, qrow, 0), cnt, lane);
+        }
     }
     flush_stats(L.scr, st);
 }

@@ -674,24 +674,36 @@ __global__ void k_prefix_max(float *__restrict__ v, int n)
 
 // The index may still be read by work queued on any stream: wait for the
 // device (as cudaFree would), then return the arrays to the pool.
-static void free_index(tnn_index *ix)
+// Arrays back to the pool in the order of `st`, host parts freed.
+static void release_index(tnn_index *ix, cudaStream_t st)
 {
-    if (!ix)
-        return;
-    cudaDeviceSynchronize();
     void *arrays[] = {ix->pts,   ix->seg,   ix->segTA, ix->segPM, ix->pts_t,
                       ix->idx_t, ix->g_off, ix->g_ids, ix->g_seg, ix->g_ext,
                       ix->g_tB,  ix->g_krec, ix->g_bpm, ix->g_ext_max,
                       ix->pts_k, ix->idx_k, ix->kp_start, ix->pts_m,
                       ix->idx_m, ix->code_m};
     for (void *p : arrays)
-        tnn_free(p, 0);
-    tnn_free(ix->d_rmax, 0);
-    tnn_free(ix->d_tiles, 0);
+        tnn_free(p, st);
+    tnn_free(ix->d_rmax, st);
+    tnn_free(ix->d_tiles, st);
     free(ix->h_tiles);
     if (ix->built)
         cudaEventDestroy(ix->built);
     delete ix;
+}
+
+static void free_index(tnn_index *ix)
+{
+    if (!ix)
+        return;
+    cudaDeviceSynchronize();
+    release_index(ix, 0);
+}
+
+void tnn_index_release(tnn_index *ix, cudaStream_t st)
+{
+    if (ix)
+        release_index(ix, st);
 }
 
 // The build's second stream per device (non-blocking, created on first

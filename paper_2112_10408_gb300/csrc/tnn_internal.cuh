@@ -181,6 +181,14 @@ struct KnnLaunch {
     uint32_t *dbg_seen;   // tests only (tnn_knn_trace), else NULL: bit j of
                           // row q = point j's distance to query q was taken
     int64_t dbg_words;    // 32-bit words per row of dbg_seen
+    // When set (one window), a grid or sweep tile kernel copies the rows of
+    // each finished tile, handed-over rows included as they stand, from
+    // out_idx / out_d2 to the same rows of these: mapped page-locked host
+    // lists, written with coalesced stores.
+    int32_t *mirror_idx;
+    float *mirror_d2;
+    int32_t mirror_vec; // k % 4 == 0 and all four lists 16-byte aligned
+    int32_t pad2_;
 };
 
 // Ascending sort of n2 (a power of two, >= 2048) 64-bit keys in place
@@ -239,11 +247,22 @@ tnn_status tnn_fill_window(const tnn_index *ix, const float *d_q, int64_t m,
                            float *d_d2, KnnWin *w);
 tnn_status tnn_launch_search(const KnnLaunch &L, bool brute,
                              cudaStream_t stream);
+// The two halves of a grid- or sweep-order search: the tile kernel alone,
+// and the warp-per-query and exact kernels over what it handed over.
+tnn_status tnn_launch_tiles(const KnnLaunch &L, cudaStream_t stream);
+tnn_status tnn_launch_finish(const KnnLaunch &L, cudaStream_t stream);
 size_t tnn_search_smem_per_warp(int L_max, int kseg_max, int mode);
 
 // Search faults flagged on the device since the last report: synchronise
 // `st`, then read and clear the device's fault word (tnn_knn.cu).
 tnn_status tnn_take_search_faults(cudaStream_t st);
+// Enqueue on `st` a copy of the device's fault word into page-locked *h_word
+// (nonzero: tnn_take_search_faults has something to report).
+cudaError_t tnn_fault_word_async(unsigned int *h_word, cudaStream_t st);
+// Free an index whose every use is ordered before the end of `st`: the
+// arrays go back to the pool in stream order, with no synchronisation
+// (tnn_index.cu).
+void tnn_index_release(tnn_index *ix, cudaStream_t st);
 
 #define TNN_WARPS_PER_CTA 4
 #define TNN_TILE 32

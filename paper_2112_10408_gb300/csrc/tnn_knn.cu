@@ -134,8 +134,10 @@ static tnn_status device_setup()
     std::lock_guard<std::mutex> lk(mu);
     if (!attrs[dev]) {
         const int maxs = 227 * 1024;
-        TNN_CUDA_TRY(cudaFuncSetAttribute(k_tnn_search, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
-        TNN_CUDA_TRY(cudaFuncSetAttribute(k_tnn_grid_search, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
+        TNN_CUDA_TRY(cudaFuncSetAttribute(k_tnn_search<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
+        TNN_CUDA_TRY(cudaFuncSetAttribute(k_tnn_search<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
+        TNN_CUDA_TRY(cudaFuncSetAttribute(k_tnn_grid_search<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
+        TNN_CUDA_TRY(cudaFuncSetAttribute(k_tnn_grid_search<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_linear_search, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_linear_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
         TNN_CUDA_TRY(cudaFuncSetAttribute(k_tnn_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
@@ -279,6 +281,37 @@ static tnn_status finish_search(const KnnLaunch &L, cudaStream_t st, bool prof, 
     return TNN_OK;
 }
 
+// The grid- or sweep-order tile kernel.
+static tnn_status launch_tiles(const KnnLaunch &L, cudaStream_t st)
+{
+    const bool sweep = (L.w0.flags & TNN_FLAG_SWEEP) != 0;
+    const size_t smem = smem_per_warp(L.L_max, L.kseg_max, sweep ? SMEM_SWEEP : SMEM_GRID) *
+                        TNN_WARPS_PER_CTA;
+    const bool mirror = L.mirror_idx != nullptr;
+    const void *kern = sweep ? (mirror ? (const void *)k_tnn_search<true> : (const void *)k_tnn_search<false>)
+                             : (mirror ? (const void *)k_tnn_grid_search<true> : (const void *)k_tnn_grid_search<false>);
+    int nb = 0;
+    TNN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, TNN_WARPS_PER_CTA * 32, smem));
+    if (nb < 1) {
+        tnn_set_error("search kernel does not fit on an SM (%zu B shared memory)", smem);
+        return TNN_ERR_UNSUPPORTED;
+    }
+    const long long need = (L.total_tiles + TNN_WARPS_PER_CTA - 1) / TNN_WARPS_PER_CTA;
+    long long grid = std::min<long long>(need, (long long)nb * g_num_sms);
+    if (grid < 1)
+        grid = 1;
+    if (sweep && mirror)
+        k_tnn_search<true><<<(unsigned)grid, TNN_WARPS_PER_CTA * 32, smem, st>>>(L);
+    else if (sweep)
+        k_tnn_search<false><<<(unsigned)grid, TNN_WARPS_PER_CTA * 32, smem, st>>>(L);
+    else if (mirror)
+        k_tnn_grid_search<true><<<(unsigned)grid, TNN_WARPS_PER_CTA * 32, smem, st>>>(L);
+    else
+        k_tnn_grid_search<false><<<(unsigned)grid, TNN_WARPS_PER_CTA * 32, smem, st>>>(L);
+    TNN_CUDA_TRY(cudaGetLastError());
+    return TNN_OK;
+}
+
 tnn_status tnn_launch_search(const KnnLaunch &L, bool brute, cudaStream_t st)
 {
     tnn_status s = device_setup();
@@ -355,12 +388,23 @@ tnn_status tnn_launch_search(const KnnLaunch &L, bool brute, cudaStream_t st)
         TNN_CUDA_TRY(cudaGetLastError());
         return finish_search(L, st, prof, pr);
     }
-    const size_t smem = smem_per_warp(L.L_max, L.kseg_max,
-                                      brute ? SMEM_LINEAR : sweep ? SMEM_SWEEP : SMEM_GRID) *
-                        TNN_WARPS_PER_CTA;
-    const void *kern = brute ? (const void *)k_linear_search
-                             : sweep ? (const void *)k_tnn_search : (const void *)k_tnn_grid_search;
-    TNN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, TNN_WARPS_PER_CTA * 32, smem));
+    if (!brute) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cap);
+        const bool prof = g_prof_on && cap == cudaStreamCaptureStatusNone;
+        ProfEv pr;
+        if (prof)
+            TNN_CUDA_TRY(prof_begin(st, &pr));
+        s = launch_tiles(L, st);
+        if (s != TNN_OK) {
+            if (prof)
+                g_prof_pool.push_back(pr);
+            return s;
+        }
+        return finish_search(L, st, prof, pr);
+    }
+    const size_t smem = smem_per_warp(L.L_max, L.kseg_max, SMEM_LINEAR) * TNN_WARPS_PER_CTA;
+    TNN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_linear_search, TNN_WARPS_PER_CTA * 32, smem));
     if (nb < 1) {
         tnn_set_error("search kernel does not fit on an SM (%zu B shared memory)", smem);
         return TNN_ERR_UNSUPPORTED;
@@ -375,14 +419,23 @@ tnn_status tnn_launch_search(const KnnLaunch &L, bool brute, cudaStream_t st)
     ProfEv pr;
     if (prof)
         TNN_CUDA_TRY(prof_begin(st, &pr));
-    if (brute)
-        k_linear_search<<<(unsigned)grid, TNN_WARPS_PER_CTA * 32, smem, st>>>(L);
-    else if (sweep)
-        k_tnn_search<<<(unsigned)grid, TNN_WARPS_PER_CTA * 32, smem, st>>>(L);
-    else
-        k_tnn_grid_search<<<(unsigned)grid, TNN_WARPS_PER_CTA * 32, smem, st>>>(L);
+    k_linear_search<<<(unsigned)grid, TNN_WARPS_PER_CTA * 32, smem, st>>>(L);
     TNN_CUDA_TRY(cudaGetLastError());
     return finish_search(L, st, prof, pr);
+}
+
+tnn_status tnn_launch_tiles(const KnnLaunch &L, cudaStream_t st)
+{
+    tnn_status s = device_setup();
+    if (s != TNN_OK)
+        return s;
+    return launch_tiles(L, st);
+}
+
+tnn_status tnn_launch_finish(const KnnLaunch &L, cudaStream_t st)
+{
+    ProfEv pr;
+    return finish_search(L, st, false, pr);
 }
 
 // ------------------------------------------------------------- faults
@@ -402,6 +455,12 @@ tnn_status tnn_take_search_faults(cudaStream_t st)
     }
     tnn_set_error("a search overflowed an internal list (flags %u); its outputs are incomplete", f);
     return TNN_ERR_CUDA;
+}
+
+cudaError_t tnn_fault_word_async(unsigned int *h_word, cudaStream_t st)
+{
+    return cudaMemcpyFromSymbolAsync(h_word, g_search_fault, sizeof(unsigned int), 0,
+                                     cudaMemcpyDeviceToHost, st);
 }
 
 extern "C" tnn_status tnn_sync_status(tnn_stream_t stream)

@@ -62,6 +62,7 @@ TNN_FLAG_EXACT_D2 = 1
 TNN_FLAG_SWEEP = 2
 TNN_FLAG_FFMA = 4
 TNN_FLAG_TC_TILES = 8
+TNN_FLAG_MAPPED_OUT = 16
 N_FEAT = 6
 
 # (name, restype, argtypes)
@@ -410,12 +411,14 @@ def _host(t, dtype, shape_tail, name):
 
 
 def tnn_knn_host(xyzt, traj_off, sigma, seg_len: int, k: int, lag: float = 0.0, chunks: int = 0,
-                 out=None, **kw):
+                 out=None, mapped=None, **kw):
     """The whole pipeline on host buffers (C ABI tnn_knn_host): points in,
     index, every point's causal k-NN, neighbour lists out.  ``xyzt`` is a
     host float32 [n, 4] array (numpy or CPU tensor; page-locked tensors copy
     faster); returns host (idx int32 [n, k], d2 float32 [n, k]), written
-    into ``out`` when given."""
+    into ``out`` when given.  ``mapped`` sets TNN_FLAG_MAPPED_OUT; by
+    default it is set when both outputs are page-locked tensors (each one
+    block of mapped page-locked memory)."""
     x = _host(xyzt, torch.float32, (4,), "xyzt")
     n = x.shape[0]
     off = np.ascontiguousarray(np.asarray(traj_off, dtype=np.int64))
@@ -432,6 +435,10 @@ def tnn_knn_host(xyzt, traj_off, sigma, seg_len: int, k: int, lag: float = 0.0, 
         d2 = _host(out[1], torch.float32, (k,), "d2")
         if idx.shape[0] != n or d2.shape[0] != n:
             raise ValueError("outputs must have n rows")
+    if mapped is None:
+        mapped = idx.is_pinned() and d2.is_pinned()
+    if mapped:
+        kp.flags |= TNN_FLAG_MAPPED_OUT
     _check(_L().tnn_knn_host(_ptr(x), n, off.ctypes.data_as(c_p), off.shape[0] - 1, ctypes.byref(bp),
                              ctypes.byref(kp), int(chunks), _ptr(idx), _ptr(d2), _stream()))
     return idx, d2

@@ -355,14 +355,10 @@ def test_linear_tensor_core_far_and_large_coordinates():
         assert_knn_equal(bi.cpu().numpy(), bd.cpu().numpy(), oi, od, what=f"far ffma={ffma}")
 
 
-def test_trajectory_tiles_give_the_same_lists_as_query_order_tiles():
-    """Self-queries are answered in tiles of one trajectory's consecutive
-    samples, passed queries in tiles of 32 in array order: the lists must be
-    bit-identical, also for ragged trajectories (1 to 70 samples, some empty),
-    a run of rows starting inside a trajectory, and against the oracle."""
-    rng = np.random.default_rng(71)
-    wl = synth.flights(90, 70, seed=72, n_routes=6)
-    # ragged trajectories: cut every flight to a random length (some to 0)
+def _ragged_flights(seed=71):
+    # flights cut to random lengths of 0 to 70 samples (some empty, some 1)
+    rng = np.random.default_rng(seed)
+    wl = synth.flights(90, 70, seed=seed + 1, n_routes=6)
     lens = rng.integers(0, 71, size=wl.n_traj)
     lens[::17] = 0
     lens[1::13] = 1
@@ -370,6 +366,15 @@ def test_trajectory_tiles_give_the_same_lists_as_query_order_tiles():
     xyzt = np.ascontiguousarray(wl.xyzt[keep])
     off = np.zeros(wl.n_traj + 1, dtype=np.int64)
     off[1:] = np.cumsum(lens)
+    return xyzt, off
+
+
+def test_trajectory_tiles_give_the_same_lists_as_query_order_tiles():
+    """Self-queries are answered in tiles of one trajectory's consecutive
+    samples, passed queries in tiles of 32 in array order: the lists must be
+    bit-identical, also for ragged trajectories (1 to 70 samples, some empty),
+    a run of rows starting inside a trajectory, and against the oracle."""
+    xyzt, off = _ragged_flights()
     x = torch.from_numpy(xyzt).cuda()
     ix = tnn.tnn_build_segments(x, off, SIG, 10)
     si, sd = tnn.tnn_knn(ix, 12, 0.0)
@@ -385,6 +390,51 @@ def test_trajectory_tiles_give_the_same_lists_as_query_order_tiles():
     # slices): the host pipeline against the device path
     hi, hd = tnn.tnn_knn_host(xyzt, off, SIG, 10, 12, 0.0, chunks=5)
     assert torch.equal(hi, si.cpu()) and torch.equal(hd, sd.cpu())
+
+
+@pytest.mark.parametrize("chunks,k,lag,kw", [(0, 12, 0.0, {}),
+                                             (1, 12, 0.0, {"defer_cells": 0.3}),
+                                             (3, 64, 0.0, {"exact_d2": True, "defer_cells": 0.3}),
+                                             (7, 12, 60.0, {"sweep": True}),
+                                             (64, 33, 0.0, {"defer_cells": 0.3})])
+def test_mapped_host_outputs_match_the_device_path(chunks, k, lag, kw):
+    """TNN_FLAG_MAPPED_OUT: the shared-tile kernel writes each finished
+    tile's rows into the page-locked outputs itself, and the rows the
+    per-query kernels finish afterwards are written by a kernel at the end.
+    The lists must equal the device path's on ragged trajectories (tiles of
+    1 to 32 rows), with many queries handed over, k above 32, and outputs
+    that are a view into a larger page-locked block; `chunks` only matters
+    to the copied path, which must agree too."""
+    xyzt, off = _ragged_flights()
+    n = xyzt.shape[0]
+    ix = tnn.tnn_build_segments(torch.from_numpy(xyzt).cuda(), off, SIG, 10)
+    di, dd, st = tnn.tnn_knn(ix, k, lag, stats=True, **kw)
+    if "defer_cells" in kw:
+        assert st["warp_queries"] > 100
+    bi = torch.full((n + 9, k), -7, dtype=torch.int32).pin_memory()
+    bd = torch.full((n + 9, k), -7.0, dtype=torch.float32).pin_memory()
+    hi, hd = bi[4:4 + n], bd[4:4 + n]
+    assert hi.is_pinned() and hi.is_contiguous()
+    tnn.tnn_knn_host(xyzt, off, SIG, 10, k, lag, chunks=chunks, out=(hi, hd), **kw)
+    assert torch.equal(hi, di.cpu()) and torch.equal(hd, dd.cpu())
+    # rows outside the outputs are untouched
+    assert (bi[:4] == -7).all() and (bi[4 + n:] == -7).all() and (bd[4 + n:] == -7.0).all()
+    # the same call with the flag off copies every row after its slice ends
+    pi, pd = tnn.tnn_knn_host(xyzt, off, SIG, 10, k, lag, chunks=chunks, mapped=False, **kw)
+    assert torch.equal(pi, hi) and torch.equal(pd, hd)
+
+
+def test_mapped_host_outputs_refuse_unmapped_memory():
+    """TNN_FLAG_MAPPED_OUT with outputs that are not page-locked is an
+    argument error, found before any device work."""
+    xyzt, off = _ragged_flights()
+    n = xyzt.shape[0]
+    pinned = torch.empty((n, 8), dtype=torch.float32).pin_memory()
+    for out in ((np.empty((n, 8), np.int32), np.empty((n, 8), np.float32)),
+                (torch.empty((n, 8), dtype=torch.int32).pin_memory(), np.empty((n, 8), np.float32)),
+                (np.empty((n, 8), np.int32), pinned)):
+        with pytest.raises(tnn.TNNError, match="MAPPED_OUT"):
+            tnn.tnn_knn_host(xyzt, off, SIG, 10, 8, 0.0, out=out, mapped=True)
 
 
 @pytest.mark.parametrize("offset", [(9000.0, -7000.0), (2e5, 1.5e5)])
