@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_MINB)
         float wF = INFINITY;
         int nw = 0;          // segments recorded (may exceed TNN_WCAP)
         bool complete = true; // pass 1 was not cut by the seed window
+        int p1_end = -1;      // this lane's bounds were taken down to here
         {
             int pos_hi = hi, seen = 0;
             if (pos_hi > 0)
@@ -186,6 +187,8 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_MINB)
                 const int c0 = pos_hi > 32 ? pos_hi - 32 : 0;
                 const int cnt = pos_hi - c0;
                 const bool done = !active || !(time_lb(c, s3, __ldg(segPM + pos_hi - 1)) <= wF);
+                if (done && p1_end < 0)
+                    p1_end = pos_hi; // stays done: segPM only falls below
                 if (__all_sync(FULLMASK, done))
                     break;
                 __syncwarp();
@@ -243,6 +246,8 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_MINB)
                 seen += cnt;
                 pos_hi = c0;
             }
+            if (p1_end < 0)
+                p1_end = pos_hi;
         }
 
         // ---- pass 2: scan the union of the seeds, highest position first
@@ -281,8 +286,18 @@ __global__ void __launch_bounds__(TNN_WARPS_PER_CTA * 32, TNN_MINB)
         __syncwarp();
 
         // ---- pass 3: exclusion criterion and stop rule
+        // The list suffices when every segment it lacks is excluded for
+        // every lane: those pass 1 bounded for the lane and did not record
+        // have a bound above RHO times the lane's final F-th smallest (so
+        // above its key when the key is at most that), and those below where
+        // the lane's pass ended have a temporal bound at least that of the
+        // running maximum of t_B there, which must then exceed the key as
+        // well (the pass ended when it exceeded the F-th smallest bound,
+        // which the key can pass when every bound shares a large temporal
+        // part, e.g. under a long lag).
+        const bool beyond = p1_end == 0 || !(time_lb(c, s3, __ldg(segPM + p1_end - 1)) <= tau);
         const bool list_mode = complete && nw <= TNN_WCAP &&
-                               __all_sync(FULLMASK, !active || tau <= TNN_RHO * wF);
+                               __all_sync(FULLMASK, !active || (tau <= TNN_RHO * wF && beyond));
         if (list_mode) {
             int up = 0;
             if (nw > 0)

@@ -437,6 +437,25 @@ def test_mapped_host_outputs_refuse_unmapped_memory():
             tnn.tnn_knn_host(xyzt, off, SIG, 10, 8, 0.0, out=out, mapped=True)
 
 
+def test_sweep_order_under_a_long_lag_matches_grid_order():
+    """Under a long lag every bound carries the same large temporal part
+    (sigma_t lag^2), so a query's k-th distance can exceed the F-th smallest
+    segment bound at which the sweep's first pass stops.  The sweep may then
+    skip the walk of the t_A table only if the temporal bound where that
+    pass stopped also exceeds the key: with that check its lists equal the
+    grid order's on all 200,000 rows (without it about one row in two
+    thousand lost a neighbour), and a sample equals the oracle."""
+    wl = synth.flights(1000, 200, 91)
+    ix = _index(wl, 20)
+    si, sd = tnn.tnn_knn(ix, 32, 1800.0, seed_segments=3, extra=4, sweep=True)
+    gi, gd = tnn.tnn_knn(ix, 32, 1800.0, seed_segments=3, extra=4)
+    torch.cuda.synchronize()
+    assert torch.equal(si, gi) and torch.equal(sd, gd)
+    q = synth.query_sample(wl.n, 512)
+    oi, od = oracle.knn(wl.xyzt, 32, SIG, lag=1800.0, qsel=q)
+    assert_knn_equal(si.cpu().numpy()[q], sd.cpu().numpy()[q], oi, od, what="sweep, lag 1800 s")
+
+
 @pytest.mark.parametrize("offset", [(9000.0, -7000.0), (2e5, 1.5e5)])
 def test_grid_search_far_from_the_origin(offset):
     # The grid's reach (cells within the k-th distance of a query) is taken in
