@@ -43,7 +43,7 @@ SEARCH_TRAFFIC = {"bytes": {"k_tnn_grid_search": 10436864 + 47383808, "k_tnn_war
                   "workload": "medium",
                   "sources": ['tnn_device.cuh', 'tnn_grid.cuh', 'tnn_fallback.cuh', 'tnn_internal.cuh', 'tnn_knn.cu', 'tnn_index.cu'],
                   "tuning": {"seed_segments": 3, "extra": 4, "defer_cells": 1.0},
-                  "sha256_16": "fbecc666ccfce5f9"}
+                  "sha256_16": "df2e349dfcd0b0a4"}
 
 
 def _search_traffic(workload, kernel):

@@ -999,7 +999,7 @@ extern "C" tnn_status tnn_build_segments(const float *d_xyzt, int64_t n,
         ix->pts, (int)ix->n, flag + 2);
     // The values come back through a page-locked buffer of this host thread
     // and an event: the segment fit (which needs neither the geometry nor
-    // the verdict) is enqueued before the host waits, so it runs while the
+    // the validation result) is enqueued before the host waits, so it runs while the
     // host chooses the geometry and enqueues the rest.  Invalid input is
     // still reported here; the fit's output is then dropped.
     static thread_local unsigned int *t_meta = nullptr;
